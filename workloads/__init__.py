@@ -1,0 +1,194 @@
+"""Synthetic workload definitions shared by the tests, the benchmark and the oracle.
+
+This module holds inputs only: lattice unit cells (primitive vectors, basis sites, bonds),
+spin-model couplings and run configurations (frequency range, truncation range, cutoff
+range).  It contains none of the flow-equation arithmetic; the CUDA path and the CPU oracle
+each turn these inputs into meshes, vertex tables and flows on their own.
+
+Unit cells and models follow the paper's resource-file format (arXiv:2109.13317, Sec. 5.3
+"Definition of lattice graphs" and Sec. 5.4 "Definition of spin interactions"): a site is
+(n0, n1, n2, b) = n0 a0 + n1 a1 + n2 a2 + basis[b]; a bond joins basis site `from` of one
+cell to basis site `to` of the cell shifted by (da0, da1, da2); an interaction couples
+S_from . M . S_to with a 3x3 matrix M.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import List, Sequence, Tuple
+
+import numpy as np
+
+S3 = math.sqrt(3.0)
+
+
+@dataclass
+class UnitCell:
+    name: str
+    prim: np.ndarray            # 3 x 3, row i = a_i
+    basis: np.ndarray           # nb x 3
+    bonds: List[Tuple[int, int, int, int, int]]  # (from, to, da0, da1, da2)
+
+    @property
+    def n_basis(self) -> int:
+        return self.basis.shape[0]
+
+
+@dataclass
+class Coupling:
+    frm: Tuple[int, int, int, int]   # (n0, n1, n2, b)
+    to: Tuple[int, int, int, int]
+    M: np.ndarray                    # 3 x 3, already multiplied by the coupling constant
+
+
+@dataclass
+class Model:
+    cell: UnitCell
+    couplings: List[Coupling]
+    backend: str = "SU2"             # "SU2" or "XYZ"
+
+
+def _cell(name, prim, basis, bonds) -> UnitCell:
+    return UnitCell(name, np.asarray(prim, dtype=np.float64), np.asarray(basis, dtype=np.float64),
+                    [tuple(int(v) for v in b) for b in bonds])
+
+
+# --- unit cells (paper Sec. 5.3 listings; pyrochlore and diamond from crystal geometry) ---
+
+def square() -> UnitCell:
+    return _cell("square", [[1, 0, 0], [0, 1, 0], [0, 0, 1]], [[0, 0, 0]],
+                 [(0, 0, 1, 0, 0), (0, 0, 0, 1, 0)])
+
+
+def honeycomb() -> UnitCell:
+    return _cell("honeycomb", [[1.5, S3 / 2, 0], [1.5, -S3 / 2, 0], [0, 0, 1]],
+                 [[0, 0, 0], [1, 0, 0]],
+                 [(0, 1, 0, 0, 0), (1, 0, 1, 0, 0), (1, 0, 0, 1, 0)])
+
+
+def kagome() -> UnitCell:
+    return _cell("kagome", [[2, 0, 0], [1, S3, 0], [0, 0, 1]],
+                 [[0, 0, 0], [1, 0, 0], [0.5, S3 / 2, 0]],
+                 [(0, 1, 0, 0, 0), (0, 2, 0, 0, 0), (1, 2, 0, 0, 0),
+                  (1, 0, 1, 0, 0), (2, 0, 0, 1, 0), (2, 1, -1, 1, 0)])
+
+
+def cubic() -> UnitCell:
+    return _cell("cubic", [[1, 0, 0], [0, 1, 0], [0, 0, 1]], [[0, 0, 0]],
+                 [(0, 0, 1, 0, 0), (0, 0, 0, 1, 0), (0, 0, 0, 0, 1)])
+
+
+def diamond() -> UnitCell:
+    """FCC primitives (conventional cube of edge 1) with a two-site basis."""
+    return _cell("diamond", [[0, 0.5, 0.5], [0.5, 0, 0.5], [0.5, 0.5, 0]],
+                 [[0, 0, 0], [0.25, 0.25, 0.25]],
+                 [(0, 1, 0, 0, 0), (0, 1, -1, 0, 0), (0, 1, 0, -1, 0), (0, 1, 0, 0, -1)])
+
+
+def pyrochlore() -> UnitCell:
+    """FCC primitives with a four-site tetrahedral basis; 6 'up' and 6 'down' bonds per cell."""
+    return _cell("pyrochlore", [[0, 0.5, 0.5], [0.5, 0, 0.5], [0.5, 0.5, 0]],
+                 [[0, 0, 0], [0, 0.25, 0.25], [0.25, 0, 0.25], [0.25, 0.25, 0]],
+                 [(0, 1, 0, 0, 0), (0, 2, 0, 0, 0), (0, 3, 0, 0, 0),
+                  (1, 2, 0, 0, 0), (1, 3, 0, 0, 0), (2, 3, 0, 0, 0),
+                  (0, 1, -1, 0, 0), (0, 2, 0, -1, 0), (0, 3, 0, 0, -1),
+                  (1, 2, 1, -1, 0), (1, 3, 1, 0, -1), (2, 3, 0, 1, -1)])
+
+
+CELLS = {f.__name__: f for f in (square, honeycomb, kagome, cubic, diamond, pyrochlore)}
+
+I3 = np.eye(3)
+
+
+def _diag(i):
+    m = np.zeros((3, 3))
+    m[i, i] = 1.0
+    return m
+
+
+def nn_heisenberg(cell: UnitCell, J: float = 1.0) -> Model:
+    """Heisenberg coupling J on every bond of the unit cell."""
+    cps = [Coupling((0, 0, 0, f), (d0, d1, d2, t), J * I3) for (f, t, d0, d1, d2) in cell.bonds]
+    return Model(cell, cps, "SU2")
+
+
+def square_j1j2(J1: float = 1.0, J2: float = 0.5) -> Model:
+    m = nn_heisenberg(square(), J1)
+    if J2 != 0.0:
+        m.couplings += [Coupling((0, 0, 0, 0), (1, 1, 0, 0), J2 * I3),
+                        Coupling((0, 0, 0, 0), (1, -1, 0, 0), J2 * I3)]
+    return m
+
+
+def honeycomb_kitaev(J: float = 0.2, K: float = -1.0) -> Model:
+    """Heisenberg-Kitaev model of the paper's model listing: Heisenberg J on the three bonds,
+    Kitaev K as xx, yy, zz on the three bond directions."""
+    c = honeycomb()
+    to = [(0, 0, 0, 1), (0, -1, 0, 1), (-1, 0, 0, 1)]
+    cps = [Coupling((0, 0, 0, 0), t, J * I3 + K * _diag(i)) for i, t in enumerate(to)]
+    return Model(c, cps, "XYZ")
+
+
+@dataclass
+class FlowConfig:
+    """One run configuration: model, truncation range, frequency mesh and cutoff range."""
+    name: str
+    model: Model
+    L: int
+    n_freq: int
+    w_min: float
+    w_max: float
+    lam_max: float
+    lam_min: float
+    n_steps: int                 # log-spaced steps (Euler); for adaptive runs the output grid
+    method: str = "euler"        # "euler" or "rk"
+    rtol: float = 1e-6
+    atol: float = 1e-10
+
+
+def config(name: str) -> FlowConfig:
+    """The five workload configurations, by short name."""
+    if name == "square_j1_L3":
+        return FlowConfig(name, nn_heisenberg(square(), 1.0), 3, 16, 0.005, 50.0, 50.0, 0.05, 100)
+    if name == "square_j1j2_L7":
+        return FlowConfig(name, square_j1j2(1.0, 0.5), 7, 48, 0.001, 100.0, 100.0, 0.01, 100,
+                          method="rk", rtol=1e-6, atol=1e-10)
+    if name == "pyrochlore_L6":
+        return FlowConfig(name, nn_heisenberg(pyrochlore(), 1.0), 6, 64, 0.001, 100.0, 100.0, 0.01, 400)
+    if name == "honeycomb_hk_L5":
+        return FlowConfig(name, honeycomb_kitaev(0.2, -1.0), 5, 32, 0.005, 50.0, 50.0, 0.05, 200)
+    raise KeyError(name)
+
+
+def batched_instances(seed: int = 0, n: int = 64):
+    """The batched coupling sweep: square J1-J2 (J2/J1 ~ U[0,1], range 5..9) and kagome J1
+    (range 4..8), 32..64 frequencies each.  Seeded; returns a list of FlowConfig."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        nw = int(rng.integers(32, 65))
+        if i < (3 * n) // 4:
+            j2 = float(rng.uniform(0.0, 1.0))
+            L = int(rng.integers(5, 10))
+            out.append(FlowConfig(f"sq{i}", square_j1j2(1.0, j2), L, nw, 0.005, 50.0, 50.0, 0.05, 100))
+        else:
+            L = int(rng.integers(4, 9))
+            out.append(FlowConfig(f"kg{i}", nn_heisenberg(kagome(), 1.0), L, nw, 0.005, 50.0, 50.0, 0.05, 100))
+    return out
+
+
+def lambda_list(lam_max: float, lam_min: float, n_steps: int) -> np.ndarray:
+    """n_steps log steps from lam_max to lam_min: n_steps + 1 points, endpoints exact."""
+    x = lam_max * (lam_min / lam_max) ** (np.arange(n_steps + 1) / n_steps)
+    x[0], x[-1] = lam_max, lam_min
+    return x
+
+
+def flatten_model(model: Model):
+    """Plain arrays of a model, in the order both implementations take them."""
+    cell = model.cell
+    bonds = np.asarray(cell.bonds, dtype=np.int32).reshape(-1, 5)
+    frm = np.asarray([c.frm for c in model.couplings], dtype=np.int32).reshape(-1, 4)
+    to = np.asarray([c.to for c in model.couplings], dtype=np.int32).reshape(-1, 4)
+    M = np.asarray([c.M for c in model.couplings], dtype=np.float64).reshape(-1, 3, 3)
+    return (np.ascontiguousarray(cell.prim), np.ascontiguousarray(cell.basis), bonds, frm, to, M)
