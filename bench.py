@@ -1,0 +1,414 @@
+"""Benchmark of the pf-FRG flow step on GB300.
+
+Workload: square-lattice J1-J2 Heisenberg model (J1 = 1, J2 = 0.5), truncation range 7
+bonds (N_s = 20 irreducible sites, N_tot = 113), 48 log-spaced frequencies 0.001..100,
+SU(2) core; 2,257,920 stored vertex entries.  One step = one full pass of the hot path:
+self-energy flow, integration nodes, vertex flow (s, t, u channels with the lattice sum),
+Euler update and the susceptibility chi(k) on a 64 x 64 momentum grid.  The flow is first
+advanced (untimed) from Lambda = 100 to mid-flow (Lambda ~ 1) so every step carries the
+full regular (Katanin) integration work.
+
+Metric: RHS vertex entries per second (stored Gamma entries x right-hand-side evaluations
+/ time).  ``--impl reference`` times the CPU oracle on the machine's host cores on a bounded
+sample of entries of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+WORKLOAD = "square_j1j2_L7"
+METRIC = "RHS vertex entries/s"
+UNIT = "entries/s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-mixed side measurement")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.idx), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _algorithmic_flops(counts: np.ndarray, N: int, Ns: int, nc: int, P: int) -> float:
+    """Floating-point operations of one vertex-flow launch as the algorithm is laid out:
+    per integration node and stored triple, trilinear interpolation (8 FMA = 16 flop per
+    interpolated value) of two vertex rows over all irreducible sites and components for the
+    s and u channels and two rows plus two on-site rows for the t channel; the projected
+    products (s / u: 14 flop per site for SU2, 36 for XYZ); the lattice sum (3 flop per table
+    entry and component); the t-channel on-site terms (9 flop per site and component)."""
+    row = Ns * nc
+    prod = 14 if nc == 2 else 36
+    per_s = 2 * row * 16 + Ns * prod
+    per_u = per_s
+    per_t = (2 * row + 2 * nc) * 16 + 3 * P * nc + 9 * row
+    ns, nt, nu = counts[0].astype(np.float64), counts[1].astype(np.float64), counts[2].astype(np.float64)
+    # triples: s_i >= u_i, any t_i
+    tot = 0.0
+    cs = np.cumsum(np.ones(N))  # number of u_i <= s_i
+    tot += N * float(np.sum(ns * cs)) * per_s                # s channel: depends on s_i
+    tot += (N * (N + 1) / 2) * float(np.sum(nt)) * per_t     # t channel: depends on t_i
+    tot += N * float(np.sum(nu * (N - np.arange(N)))) * per_u  # u channel: depends on u_i
+    return tot
+
+
+def _kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("flow.cu", "kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_2109_13317_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(precision: str):
+    """DRAM bytes per vertex-flow launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "gamma_rhs_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d.get(precision)
+        if e and e.get("kernel_hash") == _kernel_hash():
+            return e.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+def _kgrid(n=64):
+    ks = np.linspace(-2 * math.pi, 2 * math.pi, n)
+    kx, ky = np.meshgrid(ks, ks, indexing="ij")
+    return np.stack([kx.ravel(), ky.ravel(), np.zeros(n * n)], axis=1)
+
+
+def _cpu_baseline(cfg, target_s: float = 12.0):
+    """The oracle as it stands, on the host's cores, on a bounded random sample of stored
+    entries of the same workload (synthetic symmetric state at Lambda = 0.9)."""
+    from oracle import oracle as O
+    from tests.helpers import synthetic_state
+    mesh = O.mesh_exponential(cfg.n_freq, cfg.w_min, cfg.w_max)
+    of = O.OracleFlow(cfg.model, cfg.L, mesh)
+    gam, G = synthetic_state(of, cfg.model, seed=3)
+    of.set_state(gam, G)
+    rng = np.random.default_rng(5)
+    N = cfg.n_freq
+
+    def sample(m):
+        ent = []
+        for _ in range(m):
+            si = int(rng.integers(0, N))
+            ui = int(rng.integers(0, si + 1))
+            ti = int(rng.integers(0, N))
+            k = int(rng.integers(0, of.nsite[0]))
+            ent.append((0, k, si, ti, ui))
+        return np.array(ent, dtype=np.int32)
+    of.rhs_entries(0.9, sample(8))
+    t0 = time.perf_counter()
+    n0 = 64
+    of.rhs_entries(0.9, sample(n0))
+    dt = time.perf_counter() - t0
+    m = max(n0, int(n0 * target_s / max(dt, 1e-3)))
+    ent = sample(m)
+    t0 = time.perf_counter()
+    of.rhs_entries(0.9, ent)
+    dt = time.perf_counter() - t0
+    # the oracle evaluates every symmetry-equivalent pair; a stored entry of the oracle's
+    # translation-only vertex is one equation, as for the GPU's reduced vertex
+    return {"value": m / dt, "unit": UNIT, "cores": O.OracleFlow.threads(), "kind": "oracle",
+            "sample": f"{m} random stored vertex entries (RHS of each, incl. self-energy flow) of the "
+                      f"{WORKLOAD} workload at Lambda=0.9 on a synthetic symmetric state; {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    cfg = W.config(WORKLOAD)
+    from oracle import oracle as O
+    from tests.helpers import synthetic_state
+    mesh = O.mesh_exponential(cfg.n_freq, cfg.w_min, cfg.w_max)
+    of = O.OracleFlow(cfg.model, cfg.L, mesh)
+    gam, G = synthetic_state(of, cfg.model, seed=3)
+    of.set_state(gam, G)
+    rng = np.random.default_rng(7)
+    N = cfg.n_freq
+    m = 256
+
+    def sample():
+        ent = []
+        for _ in range(m):
+            si = int(rng.integers(0, N))
+            ent.append((0, int(rng.integers(0, of.nsite[0])), si, int(rng.integers(0, N)), int(rng.integers(0, si + 1))))
+        return np.array(ent, dtype=np.int32)
+    for _ in range(args.warmup):
+        of.rhs_entries(0.9, sample())
+    times = []
+    for _ in range(args.steps):
+        e = sample()
+        t0 = time.perf_counter()
+        of.rhs_entries(0.9, e)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    val = m * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_entries_per_step": m, "lambda": 0.9},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": O.OracleFlow.threads(), "kind": "oracle",
+                             "sample": f"{m} random stored entries per step of {WORKLOAD} at Lambda=0.9"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _measure_precision(sr, torch, cfg, lat, mesh, prec, steps, warmup, lams, flush, kgrid, sampler=None):
+    """Advance to mid-flow, warm up, then time `steps` Euler steps (+ chi) with CUDA events."""
+    fl = sr.Flow(lat, mesh, lams[0], prec)
+    i = 0
+    # untimed advance to mid-flow
+    while lams[i] > 1.0:
+        fl.step(lams[i + 1], sr.SR_EULER)
+        i += 1
+    for _ in range(warmup):
+        fl.step(lams[i + 1], sr.SR_EULER)
+        fl.measure(kgrid, want_ij=False)
+        i += 1
+    stream = torch.cuda.current_stream()
+    fl.profile_enable(True)
+    ev = []
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    lam_start = lams[i]
+    for _ in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fl.step(lams[i + 1], sr.SR_EULER)
+        fl.measure(kgrid, want_ij=False)
+        b.record(stream)
+        ev.append((a, b))
+        i += 1
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    kms, kn = fl.profile_read()
+    counts = fl.node_counts()
+    fl.profile_enable(False)
+    return fl, ms, kms, kn, counts, (lam_start, lams[i]), i
+
+
+def run_ours(args):
+    import torch
+    import paper_2109_13317_gb300 as sr
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    cfg = W.config(WORKLOAD)
+    mesh = sr.sr_frequency_mesh_exponential(cfg.n_freq, cfg.w_min, cfg.w_max)
+    lat = sr.Lattice.from_model(cfg.model, cfg.L)
+    lams = W.lambda_list(cfg.lam_max, cfg.lam_min, cfg.n_steps)
+    while len(lams) < 200:
+        lams = W.lambda_list(cfg.lam_max, cfg.lam_min, 2 * (len(lams) - 1))
+    kgrid = _kgrid(64)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    prec = sr.SR_FP64 if args.precision == "fp64" else sr.SR_FP32_MIXED
+    sampler = ClockSampler(local) if rank == 0 else None
+
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    fl, ms, kms, kn, counts, lam_rng, i_end = _measure_precision(sr, torch, cfg, lat, mesh, prec, args.steps,
+                                                                 args.warmup, lams, flush, kgrid, sampler)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_step = sum(ms) / len(ms)  # ms
+    if ws > 1:
+        t = torch.tensor([t_step], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(t.item())
+    n_ent = fl.n_gamma
+    value = n_ent * ws / (t_step * 1e-3)
+
+    # roofline of the dominant kernel (vertex flow)
+    flops = _algorithmic_flops(counts, fl.N, lat.N_s, fl.n_comp, lat.P)
+    k_ms = kms[2] / max(kn[2], 1)
+    achieved = flops / (k_ms * 1e-3) / 1e12
+    peak_fp64_nominal = 1.25     # TFLOP/s, recipe table
+    peak_fp32_units = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+    peak = peak_fp64_nominal if prec == sr.SR_FP64 else peak_fp32_units
+    measured_peak = sr.sr_peak_fma(prec) / 1e12
+
+    # end to end through the public API: state in from pinned host memory, step, state out
+    g_h = torch.empty(fl.N, dtype=torch.float64).pin_memory()
+    G_h = torch.empty(fl.n_gamma, dtype=torch.float64).pin_memory()
+    g_d, G_d = fl.get_state()
+    g_h.copy_(g_d)
+    G_h.copy_(G_d)
+    torch.cuda.synchronize()
+    lam = fl.lam
+    e2e_t = []
+    for k in range(max(3, min(args.steps, 5))):
+        t0 = time.perf_counter()
+        g_dev = g_h.to("cuda", non_blocking=True)
+        G_dev = G_h.to("cuda", non_blocking=True)
+        fl.set_state(lam, g_dev, G_dev)
+        fl.step(lam * 0.95, sr.SR_EULER)
+        g_o, G_o = fl.get_state()
+        G_h.copy_(G_o, non_blocking=True)
+        g_h.copy_(g_o, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+        lam = lam * 0.95
+    e2e_val = n_ent * ws / statistics.median(e2e_t)
+    bytes_state = 8 * (fl.N + fl.n_gamma)
+
+    extra = {}
+    if not args.no_fp32 and prec == sr.SR_FP64:
+        fl2, ms2, kms2, kn2, counts2, _, _ = _measure_precision(sr, torch, cfg, lat, mesh, sr.SR_FP32_MIXED,
+                                                                 args.steps, args.warmup, lams, flush, kgrid)
+        # accuracy of the mixed flow at the same cutoff: chi and Gamma against the FP64 flow
+        ck64, _ = fl.measure(kgrid, want_ij=False) if abs(fl.lam - fl2.lam) < 1e-12 else (None, None)
+        ck32, _ = fl2.measure(kgrid, want_ij=False)
+        extra["fp32_mixed"] = {"value": n_ent * ws / (sum(ms2) / len(ms2) * 1e-3), "unit": UNIT,
+                               "ms_per_step": sum(ms2) / len(ms2),
+                               "gamma_rhs_ms": kms2[2] / max(kn2[2], 1),
+                               "chi_rel_err_vs_fp64": (float(np.abs(ck32 - ck64).max() / np.abs(ck64).max())
+                                                       if ck64 is not None else None)}
+        fl2.close()
+
+    clocks = sampler.summary() if sampler else None
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        try:
+            cpu = _cpu_baseline(cfg)
+        except Exception as e:  # the oracle is a baseline, never the product path
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {e}"}
+
+    launches_per_step = 5 + 1 + (1 if prec == sr.SR_FP32_MIXED else 0)  # sigma, nodes, gamma, 2 axpy, chi (+1 shadow)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if prec == sr.SR_FP64 else "f32-mixed", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": "square J1=1 J2=0.5", "range_L": cfg.L,
+                       "N_s": lat.N_s, "N_tot": lat.N_tot, "P": lat.P, "n_freq": cfg.n_freq,
+                       "freq_range": [cfg.w_min, cfg.w_max], "entries": n_ent, "core": "SU2",
+                       "step": "Euler step (self-energy + vertex flow + update) + chi(k) on 64x64 k-grid",
+                       "lambda_range_timed": [float(lam_rng[0]), float(lam_rng[1])],
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "roofline": {"bound": "alu", "kernel": "k_gamma_rhs", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak,
+                         "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe table)" if prec == sr.SR_FP64 else
+                         "FP32 from unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz",
+                         "peak_measured_fma": measured_peak, "frac_of_measured_fma": achieved / measured_peak,
+                         "algorithmic_flop_per_launch": flops, "launch_ms": k_ms,
+                         "traffic": _traffic(args.precision)},
+            "kernels_ms_per_step": {"sigma_rhs": kms[0] / max(kn[0], 1), "channel_nodes": kms[1] / max(kn[1], 1),
+                                    "gamma_rhs": k_ms},
+            "clocks": clocks,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_state,
+                    "d2h_bytes_per_step": bytes_state},
+            "gpu_launches": launches_per_step * args.steps,
+            "cpu_baseline": cpu,
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    fl.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

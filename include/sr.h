@@ -1,0 +1,187 @@
+/*
+ * sr.h -- C ABI of the GB300 pf-FRG flow library (libsr.so).
+ *
+ * The library integrates the pseudofermion functional renormalization group flow of
+ * Buessen, arXiv:2109.13317 ("The SpinParser software for pseudofermion functional
+ * renormalization group calculations on quantum magnets") on one GPU: the flow of the
+ * self-energy Sigma(w) and of the two-particle vertex Gamma^{mu nu}_{i1 i2}(s, t, u)
+ * (Sec. 3, Eqs. frg:flowexplicit:1particle / frg:flowexplicit:2particle) in the cutoff
+ * Lambda, with symmetry-reduced lattice storage (Sec. 4.1), frequency interpolation and
+ * trapezoidal integration (Sec. 4.2), Euler stepping (Sec. 4.3) and the spin correlation
+ * chi(k) (Sec. 3, Eqs. frg:correlation and frg:structurefactor).
+ *
+ * Conventions
+ *   - Every function returns an sr_status; SR_OK = 0.  On error, sr_last_error() returns a
+ *     thread-local message.  No C++ exception crosses this boundary.
+ *   - Host arrays passed in are caller-owned and only read during the call.
+ *   - Device pointers (marked "device") are borrowed for the call; they must be valid
+ *     allocations on the current device, ordered on the flow's stream.
+ *   - The library owns all its internal device memory (sr_flow_destroy releases it).
+ *   - An sr_flow is not thread-safe; use one per host thread.
+ *
+ * Readings of points the paper leaves open are fixed identically here and in the test
+ * oracle: Sigma = -i gamma with gamma real and odd (so G(w) = 1/(i(w + gamma(w))));
+ * theta(0) = 1 in the delta-point terms of the single-scale propagator; trapezoid nodes at
+ * {+-w_n} plus the propagator break points, clipped to [-w_max, w_max]; interpolation
+ * corners below the s = u diagonal read through the s <-> u relation.
+ *
+ * State layout (device, FP64), as in Sec. 4.4 of the paper with the site index fastest:
+ *   sigma: gamma(w_n), n = 0..N-1 (Sigma(w_n) = -i gamma(w_n)).
+ *   gamma: index ((pair(s_i, u_i) * N + t_i) * n_c + c) * N_s + r
+ *          with pair(s, u) = s (s + 1) / 2 + u for s >= u (the stored octant),
+ *          c = spin component (SU2: 0 = density Gamma^00, 1 = spin Gamma^zz;
+ *          XYZ: 0 = Gamma^00, 1..3 = Gamma^xx, Gamma^yy, Gamma^zz),
+ *          r = symmetry-irreducible site (r = 0 is the reference site itself).
+ *   N_entries = N (N + 1) / 2 * N * n_c * N_s.
+ */
+#ifndef SR_H_
+#define SR_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SR_OK = 0,
+    SR_EINVAL = 1,        /* invalid argument (checked on the host before any launch) */
+    SR_ENOMEM = 2,        /* host or device allocation failed */
+    SR_ECUDA = 3,         /* a CUDA runtime call failed */
+    SR_ESYMMETRY = 4,     /* not all lattice sites are equivalent under the model's symmetries */
+    SR_ENONFINITE = 5,    /* the flow produced NaN / Inf */
+    SR_ETIMEOUT = 6,      /* a bounded device-side wait gave up */
+    SR_EUNSUPPORTED = 7   /* valid request that this build does not implement (e.g. TRI core) */
+} sr_status;
+
+typedef enum { SR_SU2 = 0, SR_XYZ = 1, SR_TRI = 2 } sr_backend;
+typedef enum { SR_FP64 = 0, SR_FP32_MIXED = 1 } sr_precision;
+typedef enum {
+    SR_EULER = 0,         /* one Euler step to lambda_next (Sec. 4.3) */
+    SR_RK_ADAPTIVE = 1,   /* embedded Dormand-Prince 5(4) steps with error control to lambda_next */
+    SR_RK_FIXED = 2       /* exactly one Dormand-Prince 5(4) step of size lambda_next - lambda */
+} sr_method;
+
+/* Lattice bond (Sec. 5.3): basis site `from_basis` of a cell to basis site `to_basis` of
+ * the cell shifted by da[0] a0 + da[1] a1 + da[2] a2. */
+typedef struct { int from_basis, to_basis; int da[3]; } sr_bond;
+
+/* Spin interaction (Sec. 5.4): S_from . M . S_to between sites given as (n0, n1, n2, basis);
+ * M is row-major and already multiplied by the coupling constant. */
+typedef struct { int from[4]; int to[4]; double M[3][3]; } sr_coupling;
+
+typedef struct {
+    double prim[3][3];             /* prim[i] = Cartesian lattice vector a_i */
+    int n_basis;
+    const double* basis_xyz;       /* host, n_basis x 3 Cartesian basis positions */
+    int n_bonds;
+    const sr_bond* bonds;          /* host */
+    int n_couplings;
+    const sr_coupling* couplings;  /* host */
+    int range_L;                   /* truncation range in bonds (Sec. 4.1) */
+    sr_backend backend;            /* SR_SU2 or SR_XYZ (SR_TRI -> SR_EUNSUPPORTED) */
+    double eps;                    /* real-space precision of the symmetry search; <= 0 means 1e-5 */
+} sr_lattice_desc;
+
+typedef struct sr_lattice sr_lattice;
+typedef struct sr_flow sr_flow;
+
+/* Build the truncated lattice and its symmetry tables on the host (Sec. 4.1): the sites
+ * within bond distance L of the reference site (basis site 0 of cell 0), the lattice and
+ * spin-permutation symmetries of the model, the irreducible site set, the site-exchange
+ * map, and the lattice-sum table of sum_j Gamma_{i1 j} Gamma_{j i2}.  No GPU is touched.
+ * Errors: SR_EINVAL (bad desc), SR_ESYMMETRY (sites not all equivalent),
+ * SR_EUNSUPPORTED (SR_TRI, or a coupling the chosen core cannot represent). */
+sr_status sr_lattice_create(const sr_lattice_desc* desc, sr_lattice** out);
+
+/* N_s irreducible sites, N_tot sites within range, basis size, P lattice-sum table length. */
+sr_status sr_lattice_info(const sr_lattice* lat, int* N_s, int* N_tot, int* N_basis, long* P);
+
+/* Representative site (n0, n1, n2, basis) of each irreducible site: host out, N_s x 4. */
+sr_status sr_lattice_representatives(const sr_lattice* lat, int* rep);
+
+/* Map an arbitrary site pair (i1, i2) (each n0, n1, n2, basis) to the stored vertex:
+ * *r = irreducible site or -1 if beyond range, perm[c] = stored component holding
+ * component c of the pair (perm has 4 entries; for SU2 only c = 0, 1 are meaningful). */
+sr_status sr_lattice_map_pair(const sr_lattice* lat, const int* i1, const int* i2, int* r, int* perm);
+
+sr_status sr_lattice_destroy(sr_lattice* lat);
+
+/* Logarithmic frequency mesh w_n = w_min (w_max / w_min)^(n / (n_freq - 1)) (Sec. 5.2). */
+sr_status sr_frequency_mesh_exponential(int n_freq, double w_min, double w_max, double* out);
+
+/* Create a flow on the current CUDA device and the given stream (cudaStream_t, NULL =
+ * default stream): initial condition Sigma = 0, Gamma^{mu nu} = J^{mu nu}/4 at
+ * lambda_init (Sec. 3, Eq. frg:parametrizationInitial).  freq_pos: host, n_freq >= 2
+ * strictly ascending positive frequencies.  Uploads the lattice tables. */
+sr_status sr_flow_init(const sr_lattice* lat, int n_freq, const double* freq_pos, double lambda_init,
+                       sr_precision precision, void* cuda_stream, sr_flow** out);
+
+/* Number of stored Gamma entries and of frequencies. */
+sr_status sr_flow_sizes(const sr_flow* flow, long* n_gamma, int* n_freq, int* n_comp);
+
+/* Right-hand side of the flow at cutoff lambda for the current state: dgamma/dLambda
+ * (device, N doubles) and dGamma/dLambda (device, N_entries doubles, state layout).
+ * Either pointer may be NULL.  Asynchronous on the flow's stream. */
+sr_status sr_flow_rhs(sr_flow* flow, double lambda, double* d_dsigma, double* d_dgamma);
+
+/* Advance the state from the current cutoff toward lambda_next (< current) with the given
+ * method; rtol / atol are the error-control tolerances of SR_RK_ADAPTIVE.  Writes the
+ * cutoff reached to *lambda_reached (host; may be NULL).  Synchronises the stream once
+ * per accepted or rejected step to read the error norm and the non-finite flag.
+ * Errors: SR_EINVAL, SR_ENONFINITE (state untouched beyond the failing step). */
+sr_status sr_flow_step(sr_flow* flow, double lambda_next, int method, double rtol, double atol,
+                       double* lambda_reached);
+
+/* Error norm of the last Dormand-Prince step (max_i |e_i| / (atol + rtol max(|y_i|, |y'_i|)))
+ * and the counts of right-hand-side evaluations, accepted and rejected steps. */
+sr_status sr_flow_stats(const sr_flow* flow, double* last_err, long* n_rhs, long* n_accept, long* n_reject);
+
+/* Correlations at the current cutoff (Sec. 3, Eq. frg:correlation):
+ * chi_ij (device, may be NULL): chi^{cc}_{b j} for every basis site b and site j within
+ * range of b, layout [b][j][c], j in the order of sr_flow_chi_sites;
+ * chi_k (host, may be NULL): structure factor (Eq. frg:structurefactor)
+ * (1/N_b) sum_b sum_j cos(k (r_b - r_j)) sum_{mu = x,y,z} chi^{mu mu}_{b j} at the n_k
+ * momenta k_xyz (host, n_k x 3).  Synchronises the stream when chi_k is requested. */
+sr_status sr_measure_susceptibility(sr_flow* flow, int n_k, const double* k_xyz, double* chi_k,
+                                    double* chi_ij);
+
+/* Site list used by chi_ij: for each basis b, the N_tot sites within range of b as
+ * (n0, n1, n2, basis) (host out, N_basis x N_tot x 4). */
+sr_status sr_flow_chi_sites(const sr_flow* flow, int* sites);
+
+/* State access (device pointers, state layout).  get copies out, set copies in and sets
+ * the current cutoff.  Either array may be NULL. */
+sr_status sr_flow_get_state(const sr_flow* flow, double* d_sigma, double* d_gamma);
+sr_status sr_flow_set_state(sr_flow* flow, double lambda, const double* d_sigma, const double* d_gamma);
+sr_status sr_flow_lambda(const sr_flow* flow, double* lambda);
+
+sr_status sr_flow_destroy(sr_flow* flow);
+
+/* ---- measurement helpers (not part of the method) ---- */
+
+/* Record CUDA events around every right-hand-side kernel launch on the flow's stream
+ * (on != 0) or stop recording (on == 0, which also clears the record). */
+sr_status sr_flow_profile_enable(sr_flow* flow, int on);
+
+/* Recorded device time (ms) and launch count of the three right-hand-side kernels:
+ * index 0 self-energy flow, 1 integration nodes, 2 vertex flow.  Synchronises. */
+sr_status sr_flow_profile_read(sr_flow* flow, double* ms /*3*/, long* launches /*3*/);
+
+/* Integration-node counts of the last right-hand side (host out, 3 x N: channel s, t, u
+ * by transfer frequency), from which the algorithmic operation count follows.  Synchronises. */
+sr_status sr_flow_node_counts(const sr_flow* flow, int* counts);
+
+/* Throughput of fused multiply-adds on the current device (FLOP/s, 2 per FMA) for FP64
+ * (precision = SR_FP64) or FP32 (SR_FP32_MIXED), from a register-resident FMA chain kernel
+ * timed with CUDA events. */
+sr_status sr_peak_fma(int precision, double* flops_per_s);
+
+/* Thread-local message of the last error (empty string if none). */
+const char* sr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SR_H_ */

@@ -1,0 +1,308 @@
+"""ctypes binding of the C ABI in include/sr.h (argument marshalling only).
+
+Device buffers are PyTorch CUDA tensors (memory and streams only); every step of the flow
+runs in the library's kernels.  Names follow the C entry points: ``Lattice`` wraps
+``sr_lattice_create`` / ``sr_lattice_info`` / ``sr_lattice_map_pair``; ``Flow`` wraps
+``sr_flow_init``, ``sr_flow_rhs``, ``sr_flow_step``, ``sr_measure_susceptibility`` and the
+state accessors.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SR_SU2, SR_XYZ, SR_TRI = 0, 1, 2
+SR_FP64, SR_FP32_MIXED = 0, 1
+SR_EULER, SR_RK_ADAPTIVE, SR_RK_FIXED = 0, 1, 2
+_STATUS = {0: "SR_OK", 1: "SR_EINVAL", 2: "SR_ENOMEM", 3: "SR_ECUDA", 4: "SR_ESYMMETRY",
+           5: "SR_ENONFINITE", 6: "SR_ETIMEOUT", 7: "SR_EUNSUPPORTED"}
+
+
+class SrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Bond(C.Structure):
+    _fields_ = [("from_basis", C.c_int), ("to_basis", C.c_int), ("da", C.c_int * 3)]
+
+
+class _Coupling(C.Structure):
+    _fields_ = [("frm", C.c_int * 4), ("to", C.c_int * 4), ("M", C.c_double * 9)]
+
+
+class _Desc(C.Structure):
+    _fields_ = [("prim", C.c_double * 9), ("n_basis", C.c_int), ("basis_xyz", C.POINTER(C.c_double)),
+                ("n_bonds", C.c_int), ("bonds", C.POINTER(_Bond)), ("n_couplings", C.c_int),
+                ("couplings", C.POINTER(_Coupling)), ("range_L", C.c_int), ("backend", C.c_int),
+                ("eps", C.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library():
+    """Load libsr.so (building it first if the sources are newer).  Raises if unavailable."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()
+        if not os.path.exists(path):
+            raise OSError(f"CUDA library not found at {path}")
+        lib = C.CDLL(path)
+        vp, i, d, l = C.c_void_p, C.c_int, C.c_double, C.c_long
+        ip, dp, lp = C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_long)
+        sig = {
+            "sr_lattice_create": [C.POINTER(_Desc), C.POINTER(vp)],
+            "sr_lattice_info": [vp, ip, ip, ip, lp],
+            "sr_lattice_representatives": [vp, ip],
+            "sr_lattice_map_pair": [vp, ip, ip, ip, ip],
+            "sr_lattice_destroy": [vp],
+            "sr_frequency_mesh_exponential": [i, d, d, dp],
+            "sr_flow_init": [vp, i, dp, d, i, vp, C.POINTER(vp)],
+            "sr_flow_sizes": [vp, lp, ip, ip],
+            "sr_flow_rhs": [vp, d, vp, vp],
+            "sr_flow_step": [vp, d, i, d, d, dp],
+            "sr_flow_stats": [vp, dp, lp, lp, lp],
+            "sr_measure_susceptibility": [vp, i, dp, dp, vp],
+            "sr_flow_chi_sites": [vp, ip],
+            "sr_flow_get_state": [vp, vp, vp],
+            "sr_flow_set_state": [vp, d, vp, vp],
+            "sr_flow_lambda": [vp, dp],
+            "sr_flow_destroy": [vp],
+            "sr_flow_profile_enable": [vp, i],
+            "sr_flow_profile_read": [vp, dp, lp],
+            "sr_flow_node_counts": [vp, ip],
+            "sr_peak_fma": [i, dp],
+        }
+        for name, args in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        lib.sr_last_error.restype = C.c_char_p
+        lib.sr_last_error.argtypes = []
+        _lib = lib
+        return lib
+
+
+def _check(st: int):
+    if st != 0:
+        raise SrError(st, load_library().sr_last_error().decode())
+
+
+def _iptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def sr_peak_fma(precision: int) -> float:
+    v = C.c_double()
+    _check(load_library().sr_peak_fma(int(precision), C.byref(v)))
+    return v.value
+
+
+def sr_frequency_mesh_exponential(n: int, wmin: float, wmax: float) -> np.ndarray:
+    out = np.zeros(n)
+    _check(load_library().sr_frequency_mesh_exponential(n, wmin, wmax, _dptr(out)))
+    return out
+
+
+class Lattice:
+    """sr_lattice_create on plain arrays (prim 3x3, basis nb x 3, bonds (from, to, da0, da1, da2),
+    couplings (from[4], to[4], M 3x3))."""
+
+    def __init__(self, prim, basis, bonds, couplings, L: int, backend: int = SR_SU2, eps: float = 1e-5):
+        lib = load_library()
+        self._lib = lib
+        prim = np.ascontiguousarray(prim, dtype=np.float64).reshape(3, 3)
+        self._basis = np.ascontiguousarray(basis, dtype=np.float64).reshape(-1, 3)
+        self._bonds = (_Bond * len(bonds))()
+        for k, (f, t, d0, d1, d2) in enumerate(bonds):
+            self._bonds[k].from_basis, self._bonds[k].to_basis = int(f), int(t)
+            self._bonds[k].da[:] = [int(d0), int(d1), int(d2)]
+        self._coups = (_Coupling * max(1, len(couplings)))()
+        for k, (frm, to, M) in enumerate(couplings):
+            self._coups[k].frm[:] = [int(x) for x in frm]
+            self._coups[k].to[:] = [int(x) for x in to]
+            self._coups[k].M[:] = [float(x) for x in np.asarray(M, dtype=np.float64).reshape(9)]
+        desc = _Desc()
+        desc.prim[:] = list(prim.reshape(9))
+        desc.n_basis = self._basis.shape[0]
+        desc.basis_xyz = _dptr(self._basis)
+        desc.n_bonds = len(bonds)
+        desc.bonds = self._bonds
+        desc.n_couplings = len(couplings)
+        desc.couplings = self._coups
+        desc.range_L = int(L)
+        desc.backend = int(backend)
+        desc.eps = float(eps)
+        h = C.c_void_p()
+        _check(lib.sr_lattice_create(C.byref(desc), C.byref(h)))
+        self.h = h
+        self.backend = backend
+        self.prim = prim
+        self.basis = self._basis
+        ns, nt, nb, P = C.c_int(), C.c_int(), C.c_int(), C.c_long()
+        _check(lib.sr_lattice_info(h, C.byref(ns), C.byref(nt), C.byref(nb), C.byref(P)))
+        self.N_s, self.N_tot, self.N_basis, self.P = ns.value, nt.value, nb.value, P.value
+
+    @classmethod
+    def from_model(cls, model, L: int, backend=None, eps: float = 1e-5) -> "Lattice":
+        cell = model.cell
+        coups = [(c.frm, c.to, c.M) for c in model.couplings]
+        be = backend if backend is not None else (SR_XYZ if getattr(model, "backend", "SU2") == "XYZ" else SR_SU2)
+        return cls(cell.prim, cell.basis, cell.bonds, coups, L, be, eps)
+
+    def representatives(self) -> np.ndarray:
+        out = np.zeros((self.N_s, 4), dtype=np.int32)
+        _check(self._lib.sr_lattice_representatives(self.h, _iptr(out)))
+        return out
+
+    def map_pair(self, i1, i2):
+        a = np.ascontiguousarray(i1, dtype=np.int32)
+        b = np.ascontiguousarray(i2, dtype=np.int32)
+        r = C.c_int()
+        perm = np.zeros(4, dtype=np.int32)
+        _check(self._lib.sr_lattice_map_pair(self.h, _iptr(a), _iptr(b), C.byref(r), _iptr(perm)))
+        return r.value, perm
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                self._lib.sr_lattice_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class Flow:
+    """sr_flow_init: a flow on the current CUDA device and PyTorch stream."""
+
+    def __init__(self, lattice: Lattice, mesh, lambda_init: float, precision: int = SR_FP64, stream=None):
+        import torch
+        lib = load_library()
+        self._lib = lib
+        self.lattice = lattice
+        self.mesh = np.ascontiguousarray(mesh, dtype=np.float64)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        _check(lib.sr_flow_init(lattice.h, len(self.mesh), _dptr(self.mesh), float(lambda_init), int(precision),
+                                C.c_void_p(stream.cuda_stream), C.byref(h)))
+        self.h = h
+        ng, nf, nc = C.c_long(), C.c_int(), C.c_int()
+        _check(lib.sr_flow_sizes(h, C.byref(ng), C.byref(nf), C.byref(nc)))
+        self.n_gamma, self.N, self.n_comp = ng.value, nf.value, nc.value
+        self.npair = self.N * (self.N + 1) // 2
+
+    # state layout: [pair][t][c][site]
+    def shape(self):
+        return (self.npair, self.N, self.n_comp, self.lattice.N_s)
+
+    def rhs(self, lam: float, dsigma=None, dgamma=None):
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if dsigma is None:
+            dsigma = torch.empty(self.N, dtype=torch.float64, device=dev)
+        if dgamma is None:
+            dgamma = torch.empty(self.n_gamma, dtype=torch.float64, device=dev)
+        _check(self._lib.sr_flow_rhs(self.h, float(lam), _ptr(dsigma), _ptr(dgamma)))
+        return dsigma, dgamma
+
+    def step(self, lam_next: float, method: int = SR_EULER, rtol: float = 1e-6, atol: float = 1e-10) -> float:
+        reached = C.c_double()
+        _check(self._lib.sr_flow_step(self.h, float(lam_next), int(method), float(rtol), float(atol), C.byref(reached)))
+        return reached.value
+
+    def stats(self):
+        e, n, a, r = C.c_double(), C.c_long(), C.c_long(), C.c_long()
+        _check(self._lib.sr_flow_stats(self.h, C.byref(e), C.byref(n), C.byref(a), C.byref(r)))
+        return {"last_err": e.value, "n_rhs": n.value, "n_accept": a.value, "n_reject": r.value}
+
+    @property
+    def lam(self) -> float:
+        v = C.c_double()
+        _check(self._lib.sr_flow_lambda(self.h, C.byref(v)))
+        return v.value
+
+    def measure(self, kpts=None, want_ij: bool = True):
+        """chi(k) at the given momenta (host numpy) and chi_ij (CUDA tensor [b][j][c])."""
+        import torch
+        nk = 0 if kpts is None else len(kpts)
+        kp = np.ascontiguousarray(np.zeros((0, 3)) if kpts is None else kpts, dtype=np.float64).reshape(-1, 3)
+        chik = np.zeros(max(nk, 1))
+        chi_ij = None
+        if want_ij:
+            n = self.lattice.N_basis * self.lattice.N_tot * self.n_comp
+            chi_ij = torch.empty(n, dtype=torch.float64, device="cuda")
+        _check(self._lib.sr_measure_susceptibility(self.h, nk, _dptr(kp), _dptr(chik) if nk else None,
+                                                   _ptr(chi_ij)))
+        if chi_ij is not None:
+            chi_ij = chi_ij.view(self.lattice.N_basis, self.lattice.N_tot, self.n_comp)
+        return (chik[:nk] if nk else None), chi_ij
+
+    def chi_sites(self) -> np.ndarray:
+        out = np.zeros((self.lattice.N_basis * self.lattice.N_tot, 4), dtype=np.int32)
+        _check(self._lib.sr_flow_chi_sites(self.h, _iptr(out)))
+        return out.reshape(self.lattice.N_basis, self.lattice.N_tot, 4)
+
+    def get_state(self):
+        import torch
+        g = torch.empty(self.N, dtype=torch.float64, device="cuda")
+        G = torch.empty(self.n_gamma, dtype=torch.float64, device="cuda")
+        _check(self._lib.sr_flow_get_state(self.h, _ptr(g), _ptr(G)))
+        return g, G
+
+    def set_state(self, lam: float, sigma=None, gamma=None):
+        _check(self._lib.sr_flow_set_state(self.h, float(lam), _ptr(sigma), _ptr(gamma)))
+
+    def profile_enable(self, on: bool = True):
+        _check(self._lib.sr_flow_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self):
+        """(ms[3], launches[3]) of the self-energy, node and vertex kernels."""
+        ms = np.zeros(3)
+        n = (C.c_long * 3)()
+        _check(self._lib.sr_flow_profile_read(self.h, _dptr(ms), n))
+        return ms, np.array(list(n))
+
+    def node_counts(self) -> np.ndarray:
+        out = np.zeros(3 * self.N, dtype=np.int32)
+        _check(self._lib.sr_flow_node_counts(self.h, _iptr(out)))
+        return out.reshape(3, self.N)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.sr_flow_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,1142 @@
+// pf-FRG flow on one GB300 GPU: kernels of the right-hand side, Euler / Dormand-Prince
+// stepping, the correlation measurement, and the C ABI declared in include/sr.h.
+//
+// Right-hand side, per cutoff Lambda (arXiv:2109.13317, Sec. 3 and 4):
+//   1. k_sigma_rhs     dgamma(w_n): Hartree lattice sum + Fock on-site term at the two
+//                      delta points w2 = +-Lambda of the single-scale propagator.
+//   2. k_channel_nodes per channel (s, t, u) and transfer frequency: the w' integration
+//                      nodes and weights -- four exact delta points of S and the trapezoid
+//                      rule on the regular Katanin part -- shared by every vertex entry
+//                      with that transfer frequency (the paper's buffered weights).
+//   3. k_gamma_rhs     one CTA per stored (s, u, t) triple: all sites and components.
+//                      Per block of integration nodes it builds the interpolated vertex
+//                      rows over all irreducible sites in shared memory, then the s / u
+//                      channel products, the t-channel on-site terms, and the lattice sum
+//                      sum_j Gamma_{i1 j} Gamma_{j i2} through the tabulated site list.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "lattice.hpp"
+#include "sr.h"
+
+using namespace sr::dev;
+
+// ----------------------------------------------------------------------------- errors
+
+static thread_local std::string g_err;
+
+static sr_status fail(sr_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CK(call)                                                                                     \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) return fail(SR_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+extern "C" const char* sr_last_error(void) { return g_err.c_str(); }
+
+// ----------------------------------------------------------------------------- kernels
+
+namespace {
+
+constexpr int kQC = 16;       // integration nodes per shared-memory block
+constexpr int kThreads = 128;
+
+// Propagator products with Sigma = -i gamma: g(a) g(b) and g(a) r(b), r = -g^2 dSigma/dLambda.
+__device__ __forceinline__ double prop_gg(const double* w, int N, const double* gam, double a, double b) {
+    double ga = a + interp_odd(w, N, gam, a);
+    double gb = b + interp_odd(w, N, gam, b);
+    return -1.0 / (ga * gb);
+}
+__device__ __forceinline__ double prop_gr(const double* w, int N, const double* gam, const double* dgam, double a, double b) {
+    double ga = a + interp_odd(w, N, gam, a);
+    double gb = b + interp_odd(w, N, gam, b);
+    double db = interp_odd(w, N, dgam, b);
+    return -db / (ga * gb * gb);
+}
+
+__device__ __forceinline__ bool in_support(double lam, int ch, double v, double m) {
+    if (fabs(m) < lam) return false;
+    if (ch == 0) return fabs(v - m) >= lam;
+    if (ch == 1) return fabs(m - v) >= lam;
+    return fabs(v + m) >= lam;
+}
+
+__device__ __forceinline__ double preg(const double* w, int N, const double* gam, const double* dgam, int ch, double v, double x) {
+    if (ch == 0) return prop_gr(w, N, gam, dgam, x, v - x) + prop_gr(w, N, gam, dgam, v - x, x);
+    if (ch == 1) return prop_gr(w, N, gam, dgam, x, x - v) + prop_gr(w, N, gam, dgam, x - v, x);
+    return prop_gr(w, N, gam, dgam, x, v + x) + prop_gr(w, N, gam, dgam, v + x, x);
+}
+
+// Integration nodes of one channel (ch = 0 s, 1 t, 2 u) at transfer frequency w[vi].
+__global__ void k_channel_nodes(Geo g, const double* __restrict__ w, const double* __restrict__ gam,
+                                const double* __restrict__ dgam, double lam, double* __restrict__ nx,
+                                double* __restrict__ nW, float* __restrict__ nWf, int* __restrict__ ncount) {
+    int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= 3 * g.N) return;
+    const int ch = id / g.N, vi = id % g.N, N = g.N;
+    const double v = w[vi];
+    double* X = nx + (size_t)id * g.nmax;
+    double* Wt = nW + (size_t)id * g.nmax;
+    float* Wf = nWf + (size_t)id * g.nmax;
+    const double inv2pi = 1.0 / (2.0 * kPi);
+    int n = 0;
+    // delta points of the single-scale propagator, theta(0) = 1
+    for (int sg = 0; sg < 2; ++sg) {
+        double L = sg == 0 ? lam : -lam;
+        double a, th;
+        if (ch == 0) {          // G(w) S(s - w): w = s - L;  G(s - w) S(w): w = L
+            a = v - L; th = (fabs(a) - lam >= 0.0) ? 1.0 : 0.0;
+            double val = th * prop_gg(w, N, gam, a, L) * inv2pi;
+            X[n] = a; Wt[n] = val; ++n;
+            X[n] = L; Wt[n] = val; ++n;
+        } else if (ch == 1) {   // G(w) S(w - t): w = t + L;  G(w - t) S(w): w = L
+            a = v + L; th = (fabs(a) - lam >= 0.0) ? 1.0 : 0.0;
+            X[n] = a; Wt[n] = th * prop_gg(w, N, gam, a, L) * inv2pi; ++n;
+            a = L - v; th = (fabs(a) - lam >= 0.0) ? 1.0 : 0.0;
+            X[n] = L; Wt[n] = th * prop_gg(w, N, gam, a, L) * inv2pi; ++n;
+        } else {                // G(w) S(u + w): w = L - u;  G(u + w) S(w): w = L
+            a = L - v; th = (fabs(a) - lam >= 0.0) ? 1.0 : 0.0;
+            X[n] = a; Wt[n] = th * prop_gg(w, N, gam, a, L) * inv2pi; ++n;
+            a = v + L; th = (fabs(a) - lam >= 0.0) ? 1.0 : 0.0;
+            X[n] = L; Wt[n] = th * prop_gg(w, N, gam, a, L) * inv2pi; ++n;
+        }
+    }
+    // regular Katanin part: trapezoid on {+-w_n} merged with the break points, clipped
+    double pts[2 * kMaxFreq + 4];
+    int m = 0;
+    for (int i = N - 1; i >= 0; --i) pts[m++] = -w[i];
+    for (int i = 0; i < N; ++i) pts[m++] = w[i];
+    const double wmax = w[N - 1];
+    double bp[4];
+    if (ch == 2) { bp[0] = lam; bp[1] = -lam; bp[2] = -v + lam; bp[3] = -v - lam; }
+    else { bp[0] = lam; bp[1] = -lam; bp[2] = v + lam; bp[3] = v - lam; }
+    for (int i = 0; i < 4; ++i) {
+        double q = bp[i];
+        if (q > wmax) q = wmax;
+        if (q < -wmax) q = -wmax;
+        int j = m++;
+        while (j > 0 && pts[j - 1] > q) { pts[j] = pts[j - 1]; --j; }
+        pts[j] = q;
+    }
+    for (int i = 0; i < m; ++i) {
+        double wgt = 0.0;
+        if (i > 0 && pts[i] > pts[i - 1] && in_support(lam, ch, v, 0.5 * (pts[i] + pts[i - 1])))
+            wgt += 0.5 * (pts[i] - pts[i - 1]);
+        if (i + 1 < m && pts[i + 1] > pts[i] && in_support(lam, ch, v, 0.5 * (pts[i] + pts[i + 1])))
+            wgt += 0.5 * (pts[i + 1] - pts[i]);
+        if (wgt == 0.0) continue;
+        X[n] = pts[i];
+        Wt[n] = wgt * preg(w, N, gam, dgam, ch, v, pts[i]) * inv2pi;
+        ++n;
+    }
+    for (int i = 0; i < n; ++i) Wf[i] = (float)Wt[i];
+    ncount[id] = n;
+}
+
+// Deterministic block sum (fixed reduction tree for a fixed block size).
+template <int NV>
+__device__ void block_sum(double (&v)[NV], double* red /* NV * 32 */) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    __syncthreads();
+    if (lane == 0)
+        for (int k = 0; k < NV; ++k) red[k * 32 + wid] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NV; ++k) {
+            double a = 0.0;
+            for (int i = 0; i < nw; ++i) a += red[k * 32 + i];
+            v[k] = a;
+        }
+}
+
+// Flow of the self-energy, one block per mesh frequency w_n:
+// dgamma(w) = -(1/2pi) sum_{w2 = +-Lambda} H(w, w2) / (w2 + gamma(w2)),
+// H = 2 sum_j Gamma^00_{ref j}(w+w2, 0, w-w2) - sum_c f_c Gamma^cc_{ref ref}(w+w2, w2-w, 0).
+__global__ void k_sigma_rhs(Geo g, Tabs tb, const double* __restrict__ w, const double* __restrict__ gam,
+                            const double* __restrict__ G, double lam, double* __restrict__ dgam) {
+    __shared__ double red[2 * 32];
+    const int n = blockIdx.x;
+    const double w1 = w[n];
+    double H[2] = {0.0, 0.0};
+    for (int sg = 0; sg < 2; ++sg) {
+        const double w2 = sg == 0 ? lam : -lam;
+        Desc<double> d;
+        make_desc(w1 + w2, 0.0, w1 - w2, w, g, d);
+        double h = 0.0;
+        for (int r = threadIdx.x; r < g.Ns; r += blockDim.x) h += (double)tb.mult[r] * row_value(G, d, tb, g, r, 0);
+        h *= 2.0;
+        if (threadIdx.x == 0) {
+            Desc<double> e;
+            make_desc(w1 + w2, w2 - w1, 0.0, w, g, e);
+            double f = 0.0;
+            if (g.nc == 2) f = row_value(G, e, tb, g, 0, 0) + 3.0 * row_value(G, e, tb, g, 0, 1);
+            else for (int c = 0; c < 4; ++c) f += row_value(G, e, tb, g, 0, c);
+            h -= f;
+        }
+        H[sg] = h;
+    }
+    block_sum<2>(H, red);
+    if (threadIdx.x == 0) {
+        double acc = 0.0;
+        acc += H[0] / (lam + interp_odd(w, g.N, gam, lam));
+        acc += H[1] / (-lam + interp_odd(w, g.N, gam, -lam));
+        dgam[n] = -acc / (2.0 * kPi);
+    }
+}
+
+// Projected products of the three channels (hand-derived from the Pauli algebra):
+// SU2 (d = Gamma^00, s = Gamma^zz) and XYZ (0, x, y, z).
+template <typename T, int NC>
+__device__ __forceinline__ void s_product(const T* A, const T* B, T* o) {
+    if (NC == 2) {
+        o[0] = A[0] * B[0] + (T)3 * A[1] * B[1];
+        o[1] = A[0] * B[1] + A[1] * B[0] - (T)2 * A[1] * B[1];
+    } else {
+        o[0] = A[0] * B[0] + A[1] * B[1] + A[2] * B[2] + A[3] * B[3];
+        o[1] = A[0] * B[1] + A[1] * B[0] - (A[2] * B[3] + A[3] * B[2]);
+        o[2] = A[0] * B[2] + A[2] * B[0] - (A[1] * B[3] + A[3] * B[1]);
+        o[3] = A[0] * B[3] + A[3] * B[0] - (A[1] * B[2] + A[2] * B[1]);
+    }
+}
+template <typename T, int NC>
+__device__ __forceinline__ void u_product(const T* A, const T* B, T* o) {
+    if (NC == 2) {
+        o[0] = A[0] * B[0] + (T)3 * A[1] * B[1];
+        o[1] = A[0] * B[1] + A[1] * B[0] + (T)2 * A[1] * B[1];
+    } else {
+        o[0] = A[0] * B[0] + A[1] * B[1] + A[2] * B[2] + A[3] * B[3];
+        o[1] = A[0] * B[1] + A[1] * B[0] + (A[2] * B[3] + A[3] * B[2]);
+        o[2] = A[0] * B[2] + A[2] * B[0] + (A[1] * B[3] + A[3] * B[1]);
+        o[3] = A[0] * B[3] + A[3] * B[0] + (A[1] * B[2] + A[2] * B[1]);
+    }
+}
+// On-site factor sum_k s(k, c) C_k with s = -1 iff k and c are distinct spin components.
+template <typename T, int NC>
+__device__ __forceinline__ T onsite_factor(const T* C, int c) {
+    if (NC == 2) return c == 0 ? C[0] + (T)3 * C[1] : C[0] - C[1];
+    T acc = C[0];
+#pragma unroll
+    for (int k = 1; k < 4; ++k) acc += (c == 0 || k == c) ? C[k] : -C[k];
+    return acc;
+}
+
+template <typename T>
+struct ShPtrs {
+    T* acc;
+    T* part;
+    Desc<T>* desc;
+    T* rows;
+    T* onrow;
+    T* wq;
+};
+
+template <typename T, int NC>
+__device__ __forceinline__ ShPtrs<T> carve(unsigned char* raw, const Geo& g, const Tabs& tb) {
+    ShPtrs<T> p;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { unsigned char* q = raw + off; off += (bytes + 15) & ~size_t(15); return q; };
+    p.desc = (Desc<T>*)take(sizeof(Desc<T>) * kQC * 4);
+    p.acc = (T*)take(sizeof(T) * g.Ns * NC);
+    p.part = (T*)take(sizeof(T) * tb.nseg * NC);
+    p.rows = (T*)take(sizeof(T) * kQC * 2 * g.Ns * NC);
+    p.onrow = (T*)take(sizeof(T) * kQC * 2 * NC);
+    p.wq = (T*)take(sizeof(T) * kQC);
+    return p;
+}
+
+// Vertex arguments of one integration node (Eq. frg:flowexplicit:2particle):
+// row 0 / 1 of the s channel: (s, w1'-x, x-w2') and (s, x-w1, x-w2);
+// t channel: (w1+x, t, w1'-x), (x+w2', t, x-w2), on-site (w2'+x, w2-x, -t), (w1+x, x-w1', -t);
+// u channel: (w1+x, x-w2', u) and (w1'+x, w2-x, u).
+__device__ __forceinline__ void node_args(int ch, int rw, double x, double s, double t, double u, double w1p,
+                                          double w2p, double w1, double w2, double& a, double& b, double& c) {
+    if (ch == 0) {
+        if (rw == 0) { a = s; b = w1p - x; c = x - w2p; }
+        else { a = s; b = x - w1; c = x - w2; }
+    } else if (ch == 1) {
+        if (rw == 0) { a = w1 + x; b = t; c = w1p - x; }
+        else if (rw == 1) { a = x + w2p; b = t; c = x - w2; }
+        else if (rw == 2) { a = w2p + x; b = w2 - x; c = -t; }
+        else { a = w1 + x; b = x - w1p; c = -t; }
+    } else {
+        if (rw == 0) { a = w1 + x; b = x - w2p; c = u; }
+        else { a = w1p + x; b = w2 - x; c = u; }
+    }
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const double* __restrict__ w,
+                                                        const T* __restrict__ G, const double* __restrict__ nx,
+                                                        const T* __restrict__ nW, const int* __restrict__ ncount,
+                                                        double* __restrict__ dG) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    ShPtrs<T> sh = carve<T, NC>(smem, g, tb);
+    const int tid = threadIdx.x;
+    const int ti = blockIdx.x % g.N;
+    const int p = blockIdx.x / g.N;
+    int si = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
+    while ((si + 1) * (si + 2) / 2 <= p) ++si;
+    while (si * (si + 1) / 2 > p) --si;
+    const int ui = p - si * (si + 1) / 2;
+    const double s = w[si], t = w[ti], u = w[ui];
+    const double w1p = (s + t + u) / 2, w2p = (s - t - u) / 2, w1 = (s - t + u) / 2, w2 = (s + t - u) / 2;
+    const int row = g.Ns * NC;
+
+    for (int o = tid; o < row; o += blockDim.x) sh.acc[o] = (T)0;
+    for (int o = tid; o < tb.nseg * NC; o += blockDim.x) sh.part[o] = (T)0;
+
+    for (int ch = 0; ch < 3; ++ch) {
+        const int vi = ch == 0 ? si : (ch == 1 ? ti : ui);
+        const int cidx = ch * g.N + vi;
+        const int nq = ncount[cidx];
+        const double* X = nx + (size_t)cidx * g.nmax;
+        const T* Wp = nW + (size_t)cidx * g.nmax;
+        const int nrow = ch == 1 ? 4 : 2;
+        for (int q0 = 0; q0 < nq; q0 += kQC) {
+            const int qn = min(kQC, nq - q0);
+            __syncthreads();
+            // phase 1: lookup descriptors of every row at every node of this block
+            for (int idx = tid; idx < qn * nrow; idx += blockDim.x) {
+                const int q = idx / nrow, rw = idx % nrow;
+                const double x = X[q0 + q];
+                double a, b, c;
+                node_args(ch, rw, x, s, t, u, w1p, w2p, w1, w2, a, b, c);
+                make_desc(a, b, c, w, g, sh.desc[q * 4 + rw]);
+                if (rw == 0) sh.wq[q] = Wp[q0 + q];
+            }
+            __syncthreads();
+            // phase 2: interpolated rows over all irreducible sites (and the on-site rows)
+            const int nfull = qn * 2 * row;
+            const int nall = nfull + (ch == 1 ? qn * 2 * NC : 0);
+            for (int idx = tid; idx < nall; idx += blockDim.x) {
+                if (idx < nfull) {
+                    const int q = idx / (2 * row), rem = idx % (2 * row), rw = rem / row, e = rem % row;
+                    const int r = e / NC, c = e % NC;
+                    sh.rows[(q * 2 + rw) * row + e] = row_value(G, sh.desc[q * 4 + rw], tb, g, r, c);
+                } else {
+                    const int j = idx - nfull;
+                    const int q = j / (2 * NC), rw = (j / NC) % 2, c = j % NC;
+                    sh.onrow[(q * 2 + rw) * NC + c] = row_value(G, sh.desc[q * 4 + 2 + rw], tb, g, 0, c);
+                }
+            }
+            __syncthreads();
+            // phase 3: products
+            if (ch != 1) {
+                for (int r = tid; r < g.Ns; r += blockDim.x) {
+                    T o[NC], accl[NC];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) accl[c] = (T)0;
+                    for (int q = 0; q < qn; ++q) {
+                        const T* A = sh.rows + (q * 2) * row + r * NC;
+                        const T* B = sh.rows + (q * 2 + 1) * row + r * NC;
+                        if (ch == 0) s_product<T, NC>(A, B, o); else u_product<T, NC>(A, B, o);
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) accl[c] += sh.wq[q] * o[c];
+                    }
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) sh.acc[r * NC + c] += accl[c];
+                }
+            } else {
+                // lattice sum, per table segment (owned by one thread across node blocks)
+                for (int o = tid; o < tb.nseg * NC; o += blockDim.x) {
+                    const int sgi = o / NC, c = o % NC;
+                    T a = (T)0;
+                    for (int e = tb.seg_start[sgi]; e < tb.seg_start[sgi + 1]; ++e) {
+                        const int4 en = tb.rpa[e];
+                        const int ca = perm_of(en.z, c), cb = perm_of(en.w, c);
+                        for (int q = 0; q < qn; ++q)
+                            a += sh.wq[q] * sh.rows[(q * 2) * row + en.x * NC + ca] *
+                                 sh.rows[(q * 2 + 1) * row + en.y * NC + cb];
+                    }
+                    sh.part[o] += a;
+                }
+                // on-site terms
+                for (int r = tid; r < g.Ns; r += blockDim.x) {
+                    const int pon = tb.onsite_perm[r];
+                    T accl[NC];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) accl[c] = (T)0;
+                    for (int q = 0; q < qn; ++q) {
+                        const T* A = sh.rows + (q * 2) * row + r * NC;
+                        const T* B = sh.rows + (q * 2 + 1) * row + r * NC;
+                        const T* C0 = sh.onrow + (q * 2) * NC;
+                        const T* D = sh.onrow + (q * 2 + 1) * NC;
+                        T Cp[NC];
+#pragma unroll
+                        for (int k = 0; k < NC; ++k) Cp[k] = C0[perm_of(pon, k)];
+#pragma unroll
+                        for (int c = 0; c < NC; ++c)
+                            accl[c] += sh.wq[q] * (A[c] * onsite_factor<T, NC>(Cp, c) + onsite_factor<T, NC>(D, c) * B[c]);
+                    }
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) sh.acc[r * NC + c] += accl[c];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int o = tid; o < row; o += blockDim.x) {
+        const int r = o / NC, c = o % NC;
+        T a = (T)0;
+        for (int sgi = tb.r_seg[r]; sgi < tb.r_seg[r + 1]; ++sgi) a += sh.part[sgi * NC + c];
+        const double v = (double)sh.acc[o] - 2.0 * (double)a;
+        dG[((size_t)(p * g.N + ti) * NC + c) * g.Ns + r] = v;
+    }
+}
+
+__global__ void k_fill_init(Geo g, const double* __restrict__ init /* Ns * nc */, double* __restrict__ G) {
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= g.nent) return;
+    int r = (int)(i % g.Ns);
+    int c = (int)((i / g.Ns) % g.nc);
+    G[i] = init[r * g.nc + c];
+}
+
+__global__ void k_to_float(long n, const double* __restrict__ a, float* __restrict__ b) {
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+// y <- y + a f, flagging non-finite results.
+__global__ void k_axpy(long n, double* __restrict__ y, const double* __restrict__ f, double a, int* __restrict__ flag) {
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = y[i] + a * f[i];
+    if (!isfinite(v)) atomicOr(flag, 1);
+    y[i] = v;
+}
+
+struct KPtrs { const double* k[7]; };
+
+// Dormand-Prince stage state: out = y0 + h sum_{r < s} a_r k_r.
+__global__ void k_rk_stage(long n, const double* __restrict__ y0, KPtrs kp, int s, double a0, double a1, double a2,
+                           double a3, double a4, double a5, double h, double* __restrict__ out) {
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double a[6] = {a0, a1, a2, a3, a4, a5};
+    double acc = 0.0;
+    for (int r = 0; r < s; ++r) acc += a[r] * kp.k[r][i];
+    out[i] = y0[i] + h * acc;
+}
+
+// Fifth-order solution and error norm max |h (y5 - y4)| / (atol + rtol max(|y0|, |y_new|)).
+__global__ void k_rk_final(long n, const double* __restrict__ y0, KPtrs kp, double h, double rtol, double atol,
+                           double* __restrict__ out, unsigned long long* __restrict__ errbits, int* __restrict__ flag) {
+    const double b5[7] = {35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0.0};
+    const double b4[7] = {5179.0 / 57600, 0.0, 7571.0 / 16695, 393.0 / 640, -92097.0 / 339200, 187.0 / 2100, 1.0 / 40};
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    double e = 0.0;
+    if (i < n) {
+        double y5 = 0.0, y4 = 0.0;
+        for (int r = 0; r < 7; ++r) { double kv = kp.k[r][i]; y5 += b5[r] * kv; y4 += b4[r] * kv; }
+        double yn = y0[i] + h * y5;
+        e = fabs(h * (y5 - y4)) / (atol + rtol * fmax(fabs(y0[i]), fabs(yn)));
+        if (!isfinite(yn) || !isfinite(e)) atomicOr(flag, 1);
+        out[i] = yn;
+    }
+    for (int o = 16; o > 0; o >>= 1) e = fmax(e, __shfl_down_sync(0xffffffffu, e, o));
+    if ((threadIdx.x & 31) == 0 && e > 0.0) atomicMax(errbits, (unsigned long long)__double_as_longlong(e));
+}
+
+// Correlations chi^{cc}_{b j} (Eq. frg:correlation), one block per (b, j): bubble (local)
+// plus the product-trapezoid vertex term with the exact G^2 weights of each segment.
+template <int NC>
+__global__ void k_chi(Geo g, Tabs tb, const double* __restrict__ w, const double* __restrict__ gam,
+                      const double* __restrict__ G, double lam, const int2* __restrict__ cmap,
+                      const int* __restrict__ onsite, int ntot, double* __restrict__ chi) {
+    __shared__ double y[kMaxFreq + 1], Wn[kMaxFreq + 1];
+    __shared__ double red[NC * 32];
+    __shared__ int Ksh;
+    const int pidx = blockIdx.x;      // b * ntot + j
+    const int b = pidx / ntot;
+    const int on = onsite[pidx];
+    const int2 pm = cmap[pidx];
+    const int2 pon = cmap[b * ntot + 0];  // the first site of each list is (0, b) itself
+    const int N = g.N;
+    if (threadIdx.x == 0) {
+        int K = 0;
+        y[K++] = lam;
+        for (int i = 0; i < N; ++i) if (w[i] > lam) y[K++] = w[i];
+        for (int k = 0; k < K; ++k) Wn[k] = 0.0;
+        for (int k = 0; k + 1 < K; ++k) {
+            double ya = y[k] + interp_odd(w, N, gam, y[k]);
+            double yb = y[k + 1] + interp_odd(w, N, gam, y[k + 1]);
+            double seg = (y[k + 1] - y[k]) / (ya * yb);
+            Wn[k] += 0.5 * seg;
+            Wn[k + 1] += 0.5 * seg;
+        }
+        Wn[K - 1] += 1.0 / (y[K - 1] + interp_odd(w, N, gam, y[K - 1]));
+        Ksh = K;
+    }
+    __syncthreads();
+    const int K = Ksh, M = 2 * K;
+    double acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+    for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+        const int pi = idx / M, qi = idx % M;
+        const double xp = pi < K ? y[pi] : -y[pi - K];
+        const double xq = qi < K ? y[qi] : -y[qi - K];
+        const double wpq = Wn[pi % K] * Wn[qi % K];
+        Desc<double> d;
+        make_desc(xp + xq, 0.0, xp - xq, w, g, d);
+        double v[NC], e[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) v[c] = row_value(G, d, tb, g, pm.x, perm_of(pm.y, c));
+        if (on) {
+            make_desc(xp + xq, xq - xp, 0.0, w, g, d);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) e[c] = row_value(G, d, tb, g, pon.x, perm_of(pon.y, c));
+        }
+#pragma unroll
+        for (int mu = 0; mu < NC; ++mu) {
+            double F = 4.0 * v[mu];
+            if (on) {
+                double x;
+                if (NC == 2) x = mu == 0 ? 2.0 * (e[0] + 3.0 * e[1]) : 2.0 * (e[0] - e[1]);
+                else {
+                    x = 0.0;
+                    for (int k = 0; k < 4; ++k) x += (mu == 0 || k == 0 || k == mu) ? 2.0 * e[k] : -2.0 * e[k];
+                }
+                F -= x;
+            }
+            acc[mu] += wpq * F;
+        }
+    }
+    block_sum<NC>(acc, red);
+    if (threadIdx.x == 0) {
+        double bub = 0.0;
+        for (int k = 0; k < K; ++k) bub += Wn[k];
+        bub /= (2.0 * kPi);
+        for (int mu = 0; mu < NC; ++mu)
+            chi[(size_t)pidx * NC + mu] = (on ? bub : 0.0) - acc[mu] / (16.0 * kPi * kPi);
+    }
+}
+
+// chi(k) = (1/N_b) sum_{b, j} cos(k (r_b - r_j)) sum_{mu = x,y,z} chi^{mu mu}_{b j}.
+__global__ void k_chi_k(int nk, const double* __restrict__ kp, const double* __restrict__ chi,
+                        const double* __restrict__ dr, int npairs, int nb, int nc, double* __restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nk) return;
+    const double kx = kp[3 * i], ky = kp[3 * i + 1], kz = kp[3 * i + 2];
+    double acc = 0.0;
+    for (int p = 0; p < npairs; ++p) {
+        double sp = nc == 2 ? 3.0 * chi[(size_t)p * 2 + 1] : chi[(size_t)p * 4 + 1] + chi[(size_t)p * 4 + 2] + chi[(size_t)p * 4 + 3];
+        acc += cos(kx * dr[3 * p] + ky * dr[3 * p + 1] + kz * dr[3 * p + 2]) * sp;
+    }
+    out[i] = acc / nb;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------- objects
+
+template <typename T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    ~DevBuf() { if (p) cudaFree(p); }
+    cudaError_t alloc(size_t count) {
+        if (p) { cudaFree(p); p = nullptr; }
+        n = count;
+        if (count == 0) return cudaSuccess;
+        return cudaMalloc((void**)&p, sizeof(T) * count);
+    }
+    cudaError_t upload(const T* host, size_t count, cudaStream_t st) {
+        cudaError_t e = alloc(count);
+        if (e != cudaSuccess || count == 0) return e;
+        return cudaMemcpyAsync(p, host, sizeof(T) * count, cudaMemcpyHostToDevice, st);
+    }
+};
+
+struct sr_flow {
+    const sr_lattice* lat = nullptr;
+    Geo g{};
+    sr_precision prec = SR_FP64;
+    cudaStream_t stream = nullptr;
+    double lambda = 0.0;
+    std::vector<double> mesh;
+
+    DevBuf<double> w, gam, G, dgam, dG;
+    DevBuf<float> Gf;
+    DevBuf<double> nx, nW;
+    DevBuf<float> nWf;
+    DevBuf<int> ncount;
+    DevBuf<int> swap_r, swap_perm, onsite_perm, mult, seg_start, seg_r, r_seg;
+    DevBuf<int4> rpa;
+    int nseg = 0;
+    DevBuf<double> init;
+    DevBuf<int2> chi_map;
+    DevBuf<int> chi_onsite;
+    DevBuf<double> chi_dr, chi, kbuf, chik;
+    DevBuf<int> flag;
+    DevBuf<unsigned long long> errbits;
+    // Dormand-Prince work space (allocated on first use)
+    DevBuf<double> y0g, y0G, stg, stG;
+    DevBuf<double> kg[7], kG[7];
+    // launch timing (measurement only): event pairs per kernel id
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[3];
+    double last_err = 0.0, h_next = 0.0;
+    long n_rhs = 0, n_accept = 0, n_reject = 0;
+    size_t smem_rhs = 0;
+
+    Tabs tabs() const {
+        Tabs t;
+        t.swap_r = swap_r.p; t.swap_perm = swap_perm.p; t.onsite_perm = onsite_perm.p; t.mult = mult.p;
+        t.rpa = rpa.p; t.seg_start = seg_start.p; t.seg_r = seg_r.p; t.r_seg = r_seg.p; t.nseg = nseg;
+        return t;
+    }
+};
+
+static int pack_perm(const sr::Perm& p) { return p[0] | (p[1] << 2) | (p[2] << 4) | (p[3] << 6); }
+
+static size_t rhs_smem_bytes(const Geo& g, int nseg, bool fp32) {
+    size_t tsz = fp32 ? 4 : 8;
+    size_t dsz = fp32 ? sizeof(Desc<float>) : sizeof(Desc<double>);
+    auto rnd = [](size_t b) { return (b + 15) & ~size_t(15); };
+    return rnd(dsz * kQC * 4) + rnd(tsz * g.Ns * g.nc) + rnd(tsz * nseg * g.nc) + rnd(tsz * kQC * 2 * g.Ns * g.nc) +
+           rnd(tsz * kQC * 2 * g.nc) + rnd(tsz * kQC);
+}
+
+static sr_status prof_begin(sr_flow* f, int id, cudaEvent_t* b) {
+    if (!f->profiling) return SR_OK;
+    CK(cudaEventCreate(b));
+    CK(cudaEventRecord(*b, f->stream));
+    (void)id;
+    return SR_OK;
+}
+static sr_status prof_end(sr_flow* f, int id, cudaEvent_t b) {
+    if (!f->profiling) return SR_OK;
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    CK(cudaEventRecord(e, f->stream));
+    f->ev[id].push_back({b, e});
+    return SR_OK;
+}
+
+// Right-hand side at cutoff lam for the state (gam_s, G_s [, Gf_s]) into (dgam_o, dG_o).
+static sr_status run_rhs(sr_flow* f, double lam, const double* gam_s, const double* G_s, const float* Gf_s,
+                         double* dgam_o, double* dG_o) {
+    const Geo& g = f->g;
+    Tabs tb = f->tabs();
+    cudaEvent_t e0 = nullptr;
+    if (sr_status s = prof_begin(f, 0, &e0)) return s;
+    k_sigma_rhs<<<g.N, 64, 0, f->stream>>>(g, tb, f->w.p, gam_s, G_s, lam, dgam_o);
+    if (sr_status s = prof_end(f, 0, e0)) return s;
+    int nt = 3 * g.N;
+    if (sr_status s = prof_begin(f, 1, &e0)) return s;
+    k_channel_nodes<<<(nt + 63) / 64, 64, 0, f->stream>>>(g, f->w.p, gam_s, dgam_o, lam, f->nx.p, f->nW.p, f->nWf.p,
+                                                           f->ncount.p);
+    if (sr_status s = prof_end(f, 1, e0)) return s;
+    const int blocks = g.npair * g.N;
+    if (sr_status s = prof_begin(f, 2, &e0)) return s;
+    if (f->prec == SR_FP64) {
+        if (g.nc == 2)
+            k_gamma_rhs<double, 2><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, f->w.p, G_s, f->nx.p, f->nW.p, f->ncount.p, dG_o);
+        else
+            k_gamma_rhs<double, 4><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, f->w.p, G_s, f->nx.p, f->nW.p, f->ncount.p, dG_o);
+    } else {
+        if (g.nc == 2)
+            k_gamma_rhs<float, 2><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, f->w.p, Gf_s, f->nx.p, f->nWf.p, f->ncount.p, dG_o);
+        else
+            k_gamma_rhs<float, 4><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, f->w.p, Gf_s, f->nx.p, f->nWf.p, f->ncount.p, dG_o);
+    }
+    if (sr_status s = prof_end(f, 2, e0)) return s;
+    CK(cudaGetLastError());
+    f->n_rhs++;
+    return SR_OK;
+}
+
+static sr_status refresh_shadow(sr_flow* f, const double* G_s, float* Gf_s) {
+    if (f->prec != SR_FP32_MIXED) return SR_OK;
+    long n = f->g.nent;
+    k_to_float<<<(unsigned)((n + 255) / 256), 256, 0, f->stream>>>(n, G_s, Gf_s);
+    CK(cudaGetLastError());
+    return SR_OK;
+}
+
+// ----------------------------------------------------------------------------- ABI: lattice
+
+extern "C" sr_status sr_lattice_create(const sr_lattice_desc* desc, sr_lattice** out) {
+    if (!desc || !out) return fail(SR_EINVAL, "null argument");
+    *out = nullptr;
+    if (desc->n_basis <= 0 || !desc->basis_xyz) return fail(SR_EINVAL, "n_basis must be positive with basis_xyz given");
+    if (desc->n_bonds <= 0 || !desc->bonds) return fail(SR_EINVAL, "at least one bond is required");
+    if (desc->n_couplings < 0 || (desc->n_couplings > 0 && !desc->couplings)) return fail(SR_EINVAL, "bad couplings");
+    if (desc->range_L < 0 || desc->range_L > 64) return fail(SR_EINVAL, "range_L must be in [0, 64]");
+    if (desc->backend == SR_TRI) return fail(SR_EUNSUPPORTED, "the TRI core is not provided by this build");
+    if (desc->backend != SR_SU2 && desc->backend != SR_XYZ) return fail(SR_EINVAL, "unknown backend");
+    std::unique_ptr<sr_lattice> lat(new (std::nothrow) sr_lattice());
+    if (!lat) return fail(SR_ENOMEM, "out of host memory");
+    std::string msg;
+    sr_status st;
+    try {
+        st = sr::build_lattice(desc, lat.get(), &msg);
+    } catch (const std::bad_alloc&) {
+        return fail(SR_ENOMEM, "out of host memory");
+    } catch (...) {
+        return fail(SR_EINVAL, "lattice construction failed");
+    }
+    if (st != SR_OK) return fail(st, "%s", msg.c_str());
+    *out = lat.release();
+    return SR_OK;
+}
+
+extern "C" sr_status sr_lattice_info(const sr_lattice* lat, int* N_s, int* N_tot, int* N_basis, long* P) {
+    if (!lat) return fail(SR_EINVAL, "null lattice");
+    if (N_s) *N_s = lat->Ns;
+    if (N_tot) *N_tot = lat->Ntot;
+    if (N_basis) *N_basis = lat->nb;
+    if (P) *P = (long)lat->rpa.size();
+    return SR_OK;
+}
+
+extern "C" sr_status sr_lattice_representatives(const sr_lattice* lat, int* rep) {
+    if (!lat || !rep) return fail(SR_EINVAL, "null argument");
+    for (int r = 0; r < lat->Ns; ++r) {
+        const sr::SiteKey& s = lat->sites[lat->rep[r]];
+        rep[4 * r] = s.n[0]; rep[4 * r + 1] = s.n[1]; rep[4 * r + 2] = s.n[2]; rep[4 * r + 3] = s.b;
+    }
+    return SR_OK;
+}
+
+extern "C" sr_status sr_lattice_map_pair(const sr_lattice* lat, const int* i1, const int* i2, int* r, int* perm) {
+    if (!lat || !i1 || !i2 || !r) return fail(SR_EINVAL, "null argument");
+    if (i1[3] < 0 || i1[3] >= lat->nb || i2[3] < 0 || i2[3] >= lat->nb) return fail(SR_EINVAL, "basis index out of range");
+    sr::SiteKey a{{i1[0], i1[1], i1[2]}, i1[3]}, b{{i2[0], i2[1], i2[2]}, i2[3]};
+    sr::PairMap pm = lat->map_pair(a, b);
+    *r = pm.r;
+    if (perm) for (int c = 0; c < 4; ++c) perm[c] = lat->backend == SR_SU2 ? c : pm.perm[c];
+    return SR_OK;
+}
+
+extern "C" sr_status sr_lattice_destroy(sr_lattice* lat) {
+    delete lat;
+    return SR_OK;
+}
+
+extern "C" sr_status sr_frequency_mesh_exponential(int n, double wmin, double wmax, double* out) {
+    if (n < 2 || !(wmin > 0.0) || !(wmax > wmin) || !out) return fail(SR_EINVAL, "need n >= 2 and 0 < w_min < w_max");
+    for (int i = 0; i < n; ++i) out[i] = wmin * std::pow(wmax / wmin, (double)i / (double)(n - 1));
+    return SR_OK;
+}
+
+// ----------------------------------------------------------------------------- ABI: flow
+
+extern "C" sr_status sr_flow_init(const sr_lattice* lat, int n_freq, const double* freq_pos, double lambda_init,
+                                  sr_precision precision, void* cuda_stream, sr_flow** out) {
+    if (!lat || !freq_pos || !out) return fail(SR_EINVAL, "null argument");
+    *out = nullptr;
+    if (n_freq < 2 || n_freq > kMaxFreq) return fail(SR_EINVAL, "n_freq must be in [2, %d]", kMaxFreq);
+    for (int i = 0; i < n_freq; ++i) {
+        if (!(freq_pos[i] > 0.0) || !std::isfinite(freq_pos[i])) return fail(SR_EINVAL, "frequencies must be positive and finite");
+        if (i > 0 && !(freq_pos[i] > freq_pos[i - 1])) return fail(SR_EINVAL, "frequencies must be strictly ascending");
+    }
+    if (!(lambda_init > 0.0) || !std::isfinite(lambda_init)) return fail(SR_EINVAL, "lambda_init must be positive");
+    if (precision != SR_FP64 && precision != SR_FP32_MIXED) return fail(SR_EINVAL, "unknown precision");
+    std::unique_ptr<sr_flow> f(new (std::nothrow) sr_flow());
+    if (!f) return fail(SR_ENOMEM, "out of host memory");
+    f->lat = lat;
+    f->prec = precision;
+    f->stream = (cudaStream_t)cuda_stream;
+    f->lambda = lambda_init;
+    f->mesh.assign(freq_pos, freq_pos + n_freq);
+    Geo& g = f->g;
+    g.N = n_freq;
+    g.Ns = lat->Ns;
+    g.nc = lat->nc;
+    g.npair = n_freq * (n_freq + 1) / 2;
+    g.nmax = 2 * n_freq + 8;
+    g.nent = (long)g.npair * n_freq * g.nc * g.Ns;
+    if ((long)g.npair * n_freq * g.nc * g.Ns >= (1L << 31)) return fail(SR_EINVAL, "vertex too large for 32-bit offsets");
+
+    // lattice tables
+    std::vector<int> sp(lat->Ns), op(lat->Ns);
+    for (int r = 0; r < lat->Ns; ++r) { sp[r] = pack_perm(lat->swap_perm[r]); op[r] = pack_perm(lat->onsite_perm[r]); }
+    std::vector<int4> rp(lat->rpa.size());
+    for (size_t e = 0; e < lat->rpa.size(); ++e)
+        rp[e] = make_int4(lat->rpa[e].rA, lat->rpa[e].rB, pack_perm(lat->rpa[e].pA), pack_perm(lat->rpa[e].pB));
+    // lattice-sum work segments: runs of at most kSeg consecutive entries of one output site;
+    // segment k covers entries [seg_start[k], seg_start[k + 1])
+    std::vector<int> segs, segr, rseg(lat->Ns + 1, 0);
+    for (int r = 0; r < lat->Ns; ++r) {
+        rseg[r] = (int)segr.size();
+        for (int e = lat->rpa_off[r]; e < lat->rpa_off[r + 1]; e += kSeg) { segs.push_back(e); segr.push_back(r); }
+    }
+    rseg[lat->Ns] = (int)segr.size();
+    segs.push_back((int)lat->rpa.size());
+    f->nseg = (int)segr.size();
+    cudaStream_t st = f->stream;
+    CK(f->w.upload(freq_pos, n_freq, st));
+    CK(f->swap_r.upload(lat->swap_r.data(), lat->Ns, st));
+    CK(f->swap_perm.upload(sp.data(), lat->Ns, st));
+    CK(f->onsite_perm.upload(op.data(), lat->Ns, st));
+    CK(f->mult.upload(lat->mult.data(), lat->Ns, st));
+    CK(f->rpa.upload(rp.data(), rp.size(), st));
+    CK(f->seg_start.upload(segs.data(), segs.size(), st));
+    CK(f->seg_r.upload(segr.data(), segr.size(), st));
+    CK(f->r_seg.upload(rseg.data(), rseg.size(), st));
+    CK(f->init.upload(lat->init_gamma.data(), lat->init_gamma.size(), st));
+    {
+        std::vector<int2> cm(lat->chi_map.size());
+        for (size_t i = 0; i < cm.size(); ++i) cm[i] = make_int2(lat->chi_map[i].r, pack_perm(lat->chi_map[i].perm));
+        CK(f->chi_map.upload(cm.data(), cm.size(), st));
+        CK(f->chi_onsite.upload(lat->chi_onsite.data(), lat->chi_onsite.size(), st));
+        CK(f->chi_dr.upload(lat->chi_dr.data(), lat->chi_dr.size(), st));
+        CK(f->chi.alloc(lat->chi_map.size() * g.nc));
+    }
+    // state
+    CK(f->gam.alloc(g.N));
+    CK(f->G.alloc(g.nent));
+    CK(f->dgam.alloc(g.N));
+    CK(f->dG.alloc(g.nent));
+    if (precision == SR_FP32_MIXED) CK(f->Gf.alloc(g.nent));
+    CK(f->nx.alloc((size_t)3 * g.N * g.nmax));
+    CK(f->nW.alloc((size_t)3 * g.N * g.nmax));
+    CK(f->nWf.alloc((size_t)3 * g.N * g.nmax));
+    CK(f->ncount.alloc((size_t)3 * g.N));
+    CK(f->flag.alloc(1));
+    CK(f->errbits.alloc(1));
+    CK(cudaMemsetAsync(f->gam.p, 0, sizeof(double) * g.N, st));
+    k_fill_init<<<(unsigned)((g.nent + 255) / 256), 256, 0, st>>>(g, f->init.p, f->G.p);
+    CK(cudaGetLastError());
+    if (sr_status s2 = refresh_shadow(f.get(), f->G.p, f->Gf.p)) return s2;
+    f->smem_rhs = rhs_smem_bytes(g, f->nseg, precision == SR_FP32_MIXED);
+    if (f->smem_rhs > 227 * 1024) return fail(SR_EUNSUPPORTED, "lattice too large for one CTA's shared memory (%zu bytes)", f->smem_rhs);
+    if (precision == SR_FP64) {
+        CK(cudaFuncSetAttribute(k_gamma_rhs<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->smem_rhs));
+        CK(cudaFuncSetAttribute(k_gamma_rhs<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->smem_rhs));
+    } else {
+        CK(cudaFuncSetAttribute(k_gamma_rhs<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->smem_rhs));
+        CK(cudaFuncSetAttribute(k_gamma_rhs<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->smem_rhs));
+    }
+    CK(cudaStreamSynchronize(st));
+    *out = f.release();
+    return SR_OK;
+}
+
+extern "C" sr_status sr_flow_sizes(const sr_flow* f, long* n_gamma, int* n_freq, int* n_comp) {
+    if (!f) return fail(SR_EINVAL, "null flow");
+    if (n_gamma) *n_gamma = f->g.nent;
+    if (n_freq) *n_freq = f->g.N;
+    if (n_comp) *n_comp = f->g.nc;
+    return SR_OK;
+}
+
+extern "C" sr_status sr_flow_rhs(sr_flow* f, double lambda, double* d_dsigma, double* d_dgamma) {
+    if (!f) return fail(SR_EINVAL, "null flow");
+    if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(SR_EINVAL, "lambda must be positive");
+    if (sr_status s = run_rhs(f, lambda, f->gam.p, f->G.p, f->Gf.p, f->dgam.p, f->dG.p)) return s;
+    if (d_dsigma) CK(cudaMemcpyAsync(d_dsigma, f->dgam.p, sizeof(double) * f->g.N, cudaMemcpyDeviceToDevice, f->stream));
+    if (d_dgamma) CK(cudaMemcpyAsync(d_dgamma, f->dG.p, sizeof(double) * f->g.nent, cudaMemcpyDeviceToDevice, f->stream));
+    return SR_OK;
+}
+
+static sr_status check_flag(sr_flow* f, double lam) {
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, f->flag.p, sizeof(int), cudaMemcpyDeviceToHost, f->stream));
+    CK(cudaStreamSynchronize(f->stream));
+    if (h) return fail(SR_ENONFINITE, "non-finite value in the flow at Lambda = %.17g", lam);
+    return SR_OK;
+}
+
+static sr_status euler_step(sr_flow* f, double lam_next) {
+    const Geo& g = f->g;
+    const double dl = f->lambda - lam_next;
+    if (sr_status s = run_rhs(f, f->lambda, f->gam.p, f->G.p, f->Gf.p, f->dgam.p, f->dG.p)) return s;
+    CK(cudaMemsetAsync(f->flag.p, 0, sizeof(int), f->stream));
+    k_axpy<<<1, 256, 0, f->stream>>>(g.N, f->gam.p, f->dgam.p, -dl, f->flag.p);
+    k_axpy<<<(unsigned)((g.nent + 255) / 256), 256, 0, f->stream>>>(g.nent, f->G.p, f->dG.p, -dl, f->flag.p);
+    CK(cudaGetLastError());
+    if (sr_status s = refresh_shadow(f, f->G.p, f->Gf.p)) return s;
+    if (sr_status s = check_flag(f, lam_next)) return s;
+    f->lambda = lam_next;
+    return SR_OK;
+}
+
+static sr_status ensure_rk(sr_flow* f) {
+    if (f->y0G.p) return SR_OK;
+    const Geo& g = f->g;
+    CK(f->y0g.alloc(g.N));
+    CK(f->y0G.alloc(g.nent));
+    CK(f->stg.alloc(g.N));
+    CK(f->stG.alloc(g.nent));
+    for (int i = 0; i < 7; ++i) { CK(f->kg[i].alloc(g.N)); CK(f->kG[i].alloc(g.nent)); }
+    return SR_OK;
+}
+
+// One Dormand-Prince 5(4) step of size h from the current state; writes the fifth-order
+// solution into the state and the error norm into f->last_err (synchronises).
+static sr_status dp54_step(sr_flow* f, double h, double rtol, double atol) {
+    static const double C[7] = {0.0, 1.0 / 5, 3.0 / 10, 4.0 / 5, 8.0 / 9, 1.0, 1.0};
+    static const double A[7][6] = {{0},
+                                   {1.0 / 5},
+                                   {3.0 / 40, 9.0 / 40},
+                                   {44.0 / 45, -56.0 / 15, 32.0 / 9},
+                                   {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729},
+                                   {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656},
+                                   {35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
+    if (sr_status s = ensure_rk(f)) return s;
+    const Geo& g = f->g;
+    cudaStream_t st = f->stream;
+    CK(cudaMemcpyAsync(f->y0g.p, f->gam.p, sizeof(double) * g.N, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(f->y0G.p, f->G.p, sizeof(double) * g.nent, cudaMemcpyDeviceToDevice, st));
+    KPtrs pg, pG;
+    for (int i = 0; i < 7; ++i) { pg.k[i] = f->kg[i].p; pG.k[i] = f->kG[i].p; }
+    const unsigned bG = (unsigned)((g.nent + 255) / 256);
+    for (int s = 0; s < 7; ++s) {
+        const double* sg = f->y0g.p;
+        const double* sG = f->y0G.p;
+        if (s > 0) {
+            k_rk_stage<<<1, 256, 0, st>>>(g.N, f->y0g.p, pg, s, A[s][0], A[s][1], A[s][2], A[s][3], A[s][4], A[s][5], h, f->stg.p);
+            k_rk_stage<<<bG, 256, 0, st>>>(g.nent, f->y0G.p, pG, s, A[s][0], A[s][1], A[s][2], A[s][3], A[s][4], A[s][5], h, f->stG.p);
+            CK(cudaGetLastError());
+            sg = f->stg.p;
+            sG = f->stG.p;
+        }
+        if (sr_status e = refresh_shadow(f, sG, f->Gf.p)) return e;
+        if (sr_status e = run_rhs(f, f->lambda + C[s] * h, sg, sG, f->Gf.p, f->kg[s].p, f->kG[s].p)) return e;
+    }
+    CK(cudaMemsetAsync(f->errbits.p, 0, sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(f->flag.p, 0, sizeof(int), st));
+    k_rk_final<<<1, 256, 0, st>>>(g.N, f->y0g.p, pg, h, rtol, atol, f->gam.p, f->errbits.p, f->flag.p);
+    k_rk_final<<<bG, 256, 0, st>>>(g.nent, f->y0G.p, pG, h, rtol, atol, f->G.p, f->errbits.p, f->flag.p);
+    CK(cudaGetLastError());
+    unsigned long long eb = 0;
+    int fl = 0;
+    CK(cudaMemcpyAsync(&eb, f->errbits.p, sizeof(eb), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&fl, f->flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double err;
+    std::memcpy(&err, &eb, sizeof(err));
+    f->last_err = err;
+    if (fl) return fail(SR_ENONFINITE, "non-finite value in a Dormand-Prince step at Lambda = %.17g", f->lambda);
+    return SR_OK;
+}
+
+static sr_status restore_y0(sr_flow* f) {
+    const Geo& g = f->g;
+    CK(cudaMemcpyAsync(f->gam.p, f->y0g.p, sizeof(double) * g.N, cudaMemcpyDeviceToDevice, f->stream));
+    CK(cudaMemcpyAsync(f->G.p, f->y0G.p, sizeof(double) * g.nent, cudaMemcpyDeviceToDevice, f->stream));
+    return refresh_shadow(f, f->G.p, f->Gf.p);
+}
+
+extern "C" sr_status sr_flow_step(sr_flow* f, double lambda_next, int method, double rtol, double atol, double* reached) {
+    if (!f) return fail(SR_EINVAL, "null flow");
+    if (!(lambda_next > 0.0) || !(lambda_next < f->lambda)) return fail(SR_EINVAL, "lambda_next must lie in (0, lambda)");
+    if (method == SR_EULER) {
+        if (sr_status s = euler_step(f, lambda_next)) return s;
+    } else if (method == SR_RK_FIXED) {
+        if (sr_status s = dp54_step(f, lambda_next - f->lambda, rtol, atol)) return s;
+        if (sr_status s = refresh_shadow(f, f->G.p, f->Gf.p)) return s;
+        f->lambda = lambda_next;
+        f->n_accept++;
+    } else if (method == SR_RK_ADAPTIVE) {
+        if (!(rtol > 0.0) || !(atol >= 0.0)) return fail(SR_EINVAL, "rtol must be positive and atol non-negative");
+        double h = f->h_next < 0.0 ? f->h_next : (lambda_next - f->lambda);
+        int guard = 0;
+        while (f->lambda > lambda_next) {
+            if (++guard > 100000) return fail(SR_ETIMEOUT, "adaptive stepping did not reach lambda_next");
+            if (f->lambda + h < lambda_next) h = lambda_next - f->lambda;
+            sr_status s = dp54_step(f, h, rtol, atol);
+            if (s != SR_OK && s != SR_ENONFINITE) return s;
+            double err = s == SR_ENONFINITE ? INFINITY : f->last_err;
+            double fac = err == 0.0 ? 5.0 : 0.9 * std::pow(err, -0.2);
+            if (err <= 1.0) {
+                f->lambda += h;
+                if (std::fabs(f->lambda - lambda_next) <= 1e-14 * std::fabs(lambda_next)) f->lambda = lambda_next;
+                if (sr_status e = refresh_shadow(f, f->G.p, f->Gf.p)) return e;
+                f->n_accept++;
+                h *= std::min(5.0, std::max(0.2, fac));
+                f->h_next = h;
+            } else {
+                if (sr_status e = restore_y0(f)) return e;
+                f->n_reject++;
+                h *= std::max(0.2, std::min(1.0, fac));
+                if (std::fabs(h) < 1e-14 * f->lambda) return fail(SR_ENONFINITE, "step size underflow at Lambda = %.17g", f->lambda);
+            }
+        }
+    } else {
+        return fail(SR_EINVAL, "unknown method");
+    }
+    if (reached) *reached = f->lambda;
+    return SR_OK;
+}
+
+extern "C" sr_status sr_flow_stats(const sr_flow* f, double* last_err, long* n_rhs, long* n_accept, long* n_reject) {
+    if (!f) return fail(SR_EINVAL, "null flow");
+    if (last_err) *last_err = f->last_err;
+    if (n_rhs) *n_rhs = f->n_rhs;
+    if (n_accept) *n_accept = f->n_accept;
+    if (n_reject) *n_reject = f->n_reject;
+    return SR_OK;
+}
+
+extern "C" sr_status sr_measure_susceptibility(sr_flow* f, int n_k, const double* k_xyz, double* chi_k, double* chi_ij) {
+    if (!f) return fail(SR_EINVAL, "null flow");
+    if (n_k < 0 || (n_k > 0 && chi_k && !k_xyz)) return fail(SR_EINVAL, "bad momenta");
+    const sr_lattice* lat = f->lat;
+    const Geo& g = f->g;
+    const int npairs = (int)lat->chi_map.size();
+    Tabs tb = f->tabs();
+    if (g.nc == 2)
+        k_chi<2><<<npairs, 128, 0, f->stream>>>(g, tb, f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_map.p, f->chi_onsite.p, lat->Ntot, f->chi.p);
+    else
+        k_chi<4><<<npairs, 128, 0, f->stream>>>(g, tb, f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_map.p, f->chi_onsite.p, lat->Ntot, f->chi.p);
+    CK(cudaGetLastError());
+    if (chi_ij) CK(cudaMemcpyAsync(chi_ij, f->chi.p, sizeof(double) * npairs * g.nc, cudaMemcpyDeviceToDevice, f->stream));
+    if (chi_k && n_k > 0) {
+        if (f->kbuf.n < (size_t)3 * n_k) CK(f->kbuf.alloc((size_t)3 * n_k));
+        if (f->chik.n < (size_t)n_k) CK(f->chik.alloc(n_k));
+        CK(cudaMemcpyAsync(f->kbuf.p, k_xyz, sizeof(double) * 3 * n_k, cudaMemcpyHostToDevice, f->stream));
+        k_chi_k<<<(n_k + 127) / 128, 128, 0, f->stream>>>(n_k, f->kbuf.p, f->chi.p, f->chi_dr.p, npairs, lat->nb, g.nc, f->chik.p);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(chi_k, f->chik.p, sizeof(double) * n_k, cudaMemcpyDeviceToHost, f->stream));
+        CK(cudaStreamSynchronize(f->stream));
+    }
+    return SR_OK;
+}
+
+extern "C" sr_status sr_flow_chi_sites(const sr_flow* f, int* sites) {
+    if (!f || !sites) return fail(SR_EINVAL, "null argument");
+    const auto& cs = f->lat->chi_sites;
+    for (size_t i = 0; i < cs.size(); ++i) {
+        sites[4 * i] = cs[i].n[0]; sites[4 * i + 1] = cs[i].n[1]; sites[4 * i + 2] = cs[i].n[2]; sites[4 * i + 3] = cs[i].b;
+    }
+    return SR_OK;
+}
+
+extern "C" sr_status sr_flow_get_state(const sr_flow* f, double* d_sigma, double* d_gamma) {
+    if (!f) return fail(SR_EINVAL, "null flow");
+    if (d_sigma) CK(cudaMemcpyAsync(d_sigma, f->gam.p, sizeof(double) * f->g.N, cudaMemcpyDeviceToDevice, f->stream));
+    if (d_gamma) CK(cudaMemcpyAsync(d_gamma, f->G.p, sizeof(double) * f->g.nent, cudaMemcpyDeviceToDevice, f->stream));
+    return SR_OK;
+}
+
+extern "C" sr_status sr_flow_set_state(sr_flow* f, double lambda, const double* d_sigma, const double* d_gamma) {
+    if (!f) return fail(SR_EINVAL, "null flow");
+    if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(SR_EINVAL, "lambda must be positive");
+    if (d_sigma) CK(cudaMemcpyAsync(f->gam.p, d_sigma, sizeof(double) * f->g.N, cudaMemcpyDeviceToDevice, f->stream));
+    if (d_gamma) CK(cudaMemcpyAsync(f->G.p, d_gamma, sizeof(double) * f->g.nent, cudaMemcpyDeviceToDevice, f->stream));
+    if (sr_status s = refresh_shadow(f, f->G.p, f->Gf.p)) return s;
+    f->lambda = lambda;
+    f->h_next = 0.0;
+    return SR_OK;
+}
+
+extern "C" sr_status sr_flow_lambda(const sr_flow* f, double* lambda) {
+    if (!f || !lambda) return fail(SR_EINVAL, "null argument");
+    *lambda = f->lambda;
+    return SR_OK;
+}
+
+static void clear_profile(sr_flow* f) {
+    for (int k = 0; k < 3; ++k) {
+        for (auto& pr : f->ev[k]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+        f->ev[k].clear();
+    }
+}
+
+extern "C" sr_status sr_flow_destroy(sr_flow* f) {
+    if (f && f->stream) cudaStreamSynchronize(f->stream);
+    if (f) clear_profile(f);
+    delete f;
+    return SR_OK;
+}
+
+extern "C" sr_status sr_flow_profile_enable(sr_flow* f, int on) {
+    if (!f) return fail(SR_EINVAL, "null flow");
+    CK(cudaStreamSynchronize(f->stream));
+    clear_profile(f);
+    f->profiling = on != 0;
+    return SR_OK;
+}
+
+extern "C" sr_status sr_flow_profile_read(sr_flow* f, double* ms, long* launches) {
+    if (!f || !ms || !launches) return fail(SR_EINVAL, "null argument");
+    CK(cudaStreamSynchronize(f->stream));
+    for (int k = 0; k < 3; ++k) {
+        double acc = 0.0;
+        for (auto& pr : f->ev[k]) {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, pr.first, pr.second));
+            acc += t;
+        }
+        ms[k] = acc;
+        launches[k] = (long)f->ev[k].size();
+    }
+    return SR_OK;
+}
+
+extern "C" sr_status sr_flow_node_counts(const sr_flow* f, int* counts) {
+    if (!f || !counts) return fail(SR_EINVAL, "null argument");
+    CK(cudaMemcpyAsync(counts, f->ncount.p, sizeof(int) * 3 * f->g.N, cudaMemcpyDeviceToHost, f->stream));
+    CK(cudaStreamSynchronize(f->stream));
+    return SR_OK;
+}
+
+namespace {
+template <typename T>
+__global__ void k_fma_peak(T* out, int iters, T a, T b) {
+    T x0 = (T)threadIdx.x, x1 = x0 + (T)1, x2 = x0 + (T)2, x3 = x0 + (T)3;
+    T x4 = x0 + (T)4, x5 = x0 + (T)5, x6 = x0 + (T)6, x7 = x0 + (T)7;
+    for (int i = 0; i < iters; ++i) {
+        x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+        x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+    }
+    T s = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+    if (s == (T)-1.2345) out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+}  // namespace
+
+extern "C" sr_status sr_peak_fma(int precision, double* flops) {
+    if (!flops) return fail(SR_EINVAL, "null argument");
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int threads = 256, blocks = nsm * 8;
+    const int iters = precision == SR_FP64 ? 4096 : 65536;
+    void* buf = nullptr;
+    CK(cudaMalloc(&buf, sizeof(double) * threads * blocks));
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        CK(cudaEventRecord(a));
+        if (precision == SR_FP64) k_fma_peak<double><<<blocks, threads>>>((double*)buf, iters, 0.999999, 1e-7);
+        else k_fma_peak<float><<<blocks, threads>>>((float*)buf, iters, 0.999999f, 1e-7f);
+        CK(cudaEventRecord(b));
+        CK(cudaEventSynchronize(b));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, a, b));
+        if (rep > 0) best = std::min(best, t);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(buf);
+    *flops = 2.0 * 8.0 * (double)iters * threads * blocks / (best * 1e-3);
+    return SR_OK;
+}

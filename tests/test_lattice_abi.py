@@ -1,0 +1,161 @@
+"""Host-side tests of the C ABI library (no GPU): exported symbols, lattice truncation and
+symmetry tables (Sec. 4.1 of arXiv:2109.13317), error reporting."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+import paper_2109_13317_gb300 as sr
+from oracle import oracle as O
+from tests.helpers import evolved_oracle, gpu_comp_map
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLD = os.path.join(ROOT, "tests", "golden")
+
+
+def test_library_exports_every_declared_symbol():
+    lib = sr.load_library()
+    decls = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            decls |= set(re.findall(r"^\s*(?:sr_status|const char\*)\s+(sr_\w+)\s*\(", txt, re.M))
+    assert len(decls) >= 15
+    for name in sorted(decls):
+        assert hasattr(lib, name), name
+
+
+def _gold_counts():
+    rows = []
+    for line in open(os.path.join(GOLD, "paper_lattice_counts.txt")):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            n, L, nt, ns = line.split()
+            rows.append((n, int(L), int(nt), int(ns)))
+    return rows
+
+
+@pytest.mark.parametrize("name,L,ntot,ns", _gold_counts())
+def test_printed_site_counts(name, L, ntot, ns):
+    lat = sr.Lattice.from_model(W.nn_heisenberg(W.CELLS[name]()), L)
+    if ntot > 0:
+        assert lat.N_tot == ntot
+    if ns > 0:
+        assert lat.N_s == ns
+
+
+def test_square_point_group_orbit_counts():
+    # square lattice, Manhattan ball of radius L, orbits of the 8-element point group:
+    # sites (a, b) with a >= b >= 0, a + b <= L
+    for L in range(0, 9):
+        lat = sr.Lattice.from_model(W.nn_heisenberg(W.square()), L)
+        assert lat.N_tot == 2 * L * L + 2 * L + 1
+        assert lat.N_s == sum(1 for a in range(L + 1) for b in range(a + 1) if a + b <= L)
+
+
+def test_lattice_sum_table_counts_brute_force():
+    """P = sum over irreducible sites i2 of the number of sites j within range of both the
+    reference site and i2 (test-side BFS)."""
+    from tests.test_oracle_pins import _bond_distance_sites
+    for model, L in [(W.square_j1j2(1, 0.5), 3), (W.nn_heisenberg(W.kagome()), 3)]:
+        lat = sr.Lattice.from_model(model, L)
+        d0 = _bond_distance_sites(model.cell, L)
+        P = 0
+        for rep in lat.representatives():
+            rep = tuple(int(x) for x in rep)
+            for j in d0:
+                # j within range of rep: shift j by -rep's cell, compare with the ball of rep's basis
+                dj = (j[0] - rep[0], j[1] - rep[1], j[2] - rep[2], j[3])
+                ball = _ball_cache(model.cell, L, rep[3])
+                if dj in ball:
+                    P += 1
+        assert P == lat.P
+
+
+_balls = {}
+
+
+def _ball_cache(cell, L, b):
+    key = (cell.name, L, b)
+    if key not in _balls:
+        from collections import deque
+        start = (0, 0, 0, b)
+        dist = {start: 0}
+        q = deque([start])
+        while q:
+            cur = q.popleft()
+            if dist[cur] >= L:
+                continue
+            for (fb, tb, d0, d1, d2) in cell.bonds:
+                for sgn, a, bb in ((1, fb, tb), (-1, tb, fb)):
+                    if cur[3] != a:
+                        continue
+                    nx = (cur[0] + sgn * d0, cur[1] + sgn * d1, cur[2] + sgn * d2, bb)
+                    if nx not in dist:
+                        dist[nx] = dist[cur] + 1
+                        q.append(nx)
+        _balls[key] = dist
+    return _balls[key]
+
+
+@pytest.mark.parametrize("model,L", [(W.square_j1j2(1.0, 0.5), 2), (W.nn_heisenberg(W.honeycomb()), 2),
+                                     (W.nn_heisenberg(W.kagome()), 2), (W.honeycomb_kitaev(0.2, -1.0), 2)])
+def test_symmetry_tables_against_unreduced_oracle(model, L):
+    """Every pair (b, j) of the oracle's translation-only storage maps to an irreducible site
+    and a component permutation; after a few flow steps the oracle's value of the pair must
+    equal the value stored for its image (the symmetry reduction is exact)."""
+    mesh = O.mesh_exponential(5, 0.05, 10.0)
+    of = evolved_oracle(model, L, mesh, [6.0, 3.0, 1.5])
+    lat = sr.Lattice.from_model(model, L)
+    nc = 2 if model.backend == "SU2" else 4
+    cm = gpu_comp_map(nc)
+    _, G = of.get_state()
+    reps = lat.representatives()
+    ref_blk = of.block(G, 0)
+    rep_k = [of.find(0, r[:3], int(r[3])) for r in reps]
+    for b in range(of.nb):
+        blk = of.block(G, b)
+        for k, s in enumerate(of.sites(b)):
+            r, perm = lat.map_pair([0, 0, 0, b], s)
+            assert r >= 0
+            for c in range(4):
+                # oracle component c of the pair equals oracle component of the stored image
+                src_c = c if nc == 4 else c
+                img_c = perm[src_c] if nc == 4 else c
+                np.testing.assert_allclose(blk[k, c], ref_blk[rep_k[r], img_c], rtol=1e-11, atol=1e-14)
+    assert np.abs(G).max() > 0
+
+
+def test_errors_are_reported():
+    # TRI core and off-diagonal couplings are not provided
+    m = W.nn_heisenberg(W.square())
+    with pytest.raises(sr.SrError) as e:
+        sr.Lattice.from_model(m, 2, backend=2)
+    assert e.value.status == 7
+    m2 = W.nn_heisenberg(W.square())
+    m2.couplings[0].M = np.array([[0, 1.0, 0], [0, 0, 0], [0, 0, 0]])
+    with pytest.raises(sr.SrError) as e:
+        sr.Lattice.from_model(m2, 2, backend=1)
+    assert e.value.status == 7
+    # Kitaev couplings on the SU2 core
+    with pytest.raises(sr.SrError) as e:
+        sr.Lattice.from_model(W.honeycomb_kitaev(0.2, -1.0), 2, backend=0)
+    assert e.value.status == 7
+    # inequivalent sites: honeycomb with a coupling on one sublattice only
+    hc = W.honeycomb()
+    bad = W.Model(hc, [W.Coupling((0, 0, 0, 0), (0, 0, 0, 1), np.eye(3)),
+                       W.Coupling((0, 0, 0, 0), (1, 0, 0, 0), 0.3 * np.eye(3))])
+    with pytest.raises(sr.SrError) as e:
+        sr.Lattice.from_model(bad, 2)
+    assert e.value.status == 4
+    with pytest.raises(sr.SrError) as e:
+        sr.Lattice(np.eye(3), [[0, 0, 0]], [(0, 0, 1, 0, 0)], [], -1)
+    assert e.value.status == 1
+
+
+def test_frequency_mesh_matches_oracle():
+    a = sr.sr_frequency_mesh_exponential(48, 0.001, 100.0)
+    b = O.mesh_exponential(48, 0.001, 100.0)
+    np.testing.assert_allclose(a, b, rtol=1e-15)
