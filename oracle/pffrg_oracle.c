@@ -535,26 +535,28 @@ static int channel_nodes(const OrState* st, int ch, double v, double* x, double*
     const double lam = st->lam;
     const double inv2pi = 1.0 / (2.0 * OR_PI);
     int n = 0;
+    /* a delta point whose partner propagator G(a) lies below the cutoff (theta = 0) is absent:
+     * the term is zero, not 0 * g(a), which diverges where a + gamma(a) = 0 */
     for (int sg = 0; sg < 2; ++sg) {
         double L = sg == 0 ? lam : -lam;
         double a, th;
         switch (ch) {
         case CH_S:  /* G(w) S(s - w): w = s - L;  G(s - w) S(w): w = L */
             a = v - L; th = theta(fabs(a) - lam);
-            x[n] = a; W[n] = th * prop_gg(st, a, L) * inv2pi; ++n;
-            x[n] = L; W[n] = th * prop_gg(st, a, L) * inv2pi; ++n;
+            x[n] = a; W[n] = th != 0.0 ? prop_gg(st, a, L) * inv2pi : 0.0; ++n;
+            x[n] = L; W[n] = th != 0.0 ? prop_gg(st, a, L) * inv2pi : 0.0; ++n;
             break;
         case CH_T:  /* G(w) S(w - t): w = t + L;  G(w - t) S(w): w = L */
             a = v + L; th = theta(fabs(a) - lam);
-            x[n] = a; W[n] = th * prop_gg(st, a, L) * inv2pi; ++n;
+            x[n] = a; W[n] = th != 0.0 ? prop_gg(st, a, L) * inv2pi : 0.0; ++n;
             a = L - v; th = theta(fabs(a) - lam);
-            x[n] = L; W[n] = th * prop_gg(st, a, L) * inv2pi; ++n;
+            x[n] = L; W[n] = th != 0.0 ? prop_gg(st, a, L) * inv2pi : 0.0; ++n;
             break;
         default:    /* G(w) S(u + w): w = L - u;  G(u + w) S(w): w = L */
             a = L - v; th = theta(fabs(a) - lam);
-            x[n] = a; W[n] = th * prop_gg(st, a, L) * inv2pi; ++n;
+            x[n] = a; W[n] = th != 0.0 ? prop_gg(st, a, L) * inv2pi : 0.0; ++n;
             a = v + L; th = theta(fabs(a) - lam);
-            x[n] = L; W[n] = th * prop_gg(st, a, L) * inv2pi; ++n;
+            x[n] = L; W[n] = th != 0.0 ? prop_gg(st, a, L) * inv2pi : 0.0; ++n;
             break;
         }
     }

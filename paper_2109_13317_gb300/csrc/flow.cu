@@ -98,25 +98,26 @@ __global__ void k_channel_nodes(Geo g, const double* __restrict__ w, const doubl
     float* Wf = nWf + (size_t)id * g.nmax;
     const double inv2pi = 1.0 / (2.0 * kPi);
     int n = 0;
-    // delta points of the single-scale propagator, theta(0) = 1
+    // delta points of the single-scale propagator, theta(0) = 1; a point whose partner
+    // propagator lies below the cutoff (theta = 0) contributes exactly zero
     for (int sg = 0; sg < 2; ++sg) {
         double L = sg == 0 ? lam : -lam;
-        double a, th;
+        double a;
         if (ch == 0) {          // G(w) S(s - w): w = s - L;  G(s - w) S(w): w = L
-            a = v - L; th = (fabs(a) - lam >= 0.0) ? 1.0 : 0.0;
-            double val = th * prop_gg(w, N, gam, a, L) * inv2pi;
+            a = v - L;
+            double val = (fabs(a) - lam >= 0.0) ? prop_gg(w, N, gam, a, L) * inv2pi : 0.0;
             X[n] = a; Wt[n] = val; ++n;
             X[n] = L; Wt[n] = val; ++n;
         } else if (ch == 1) {   // G(w) S(w - t): w = t + L;  G(w - t) S(w): w = L
-            a = v + L; th = (fabs(a) - lam >= 0.0) ? 1.0 : 0.0;
-            X[n] = a; Wt[n] = th * prop_gg(w, N, gam, a, L) * inv2pi; ++n;
-            a = L - v; th = (fabs(a) - lam >= 0.0) ? 1.0 : 0.0;
-            X[n] = L; Wt[n] = th * prop_gg(w, N, gam, a, L) * inv2pi; ++n;
+            a = v + L;
+            X[n] = a; Wt[n] = (fabs(a) - lam >= 0.0) ? prop_gg(w, N, gam, a, L) * inv2pi : 0.0; ++n;
+            a = L - v;
+            X[n] = L; Wt[n] = (fabs(a) - lam >= 0.0) ? prop_gg(w, N, gam, a, L) * inv2pi : 0.0; ++n;
         } else {                // G(w) S(u + w): w = L - u;  G(u + w) S(w): w = L
-            a = L - v; th = (fabs(a) - lam >= 0.0) ? 1.0 : 0.0;
-            X[n] = a; Wt[n] = th * prop_gg(w, N, gam, a, L) * inv2pi; ++n;
-            a = v + L; th = (fabs(a) - lam >= 0.0) ? 1.0 : 0.0;
-            X[n] = L; Wt[n] = th * prop_gg(w, N, gam, a, L) * inv2pi; ++n;
+            a = L - v;
+            X[n] = a; Wt[n] = (fabs(a) - lam >= 0.0) ? prop_gg(w, N, gam, a, L) * inv2pi : 0.0; ++n;
+            a = v + L;
+            X[n] = L; Wt[n] = (fabs(a) - lam >= 0.0) ? prop_gg(w, N, gam, a, L) * inv2pi : 0.0; ++n;
         }
     }
     // regular Katanin part: trapezoid on {+-w_n} merged with the break points, clipped

@@ -583,3 +583,13 @@ def test_dp54_step_agrees_with_fine_steps():
     d_eu = np.abs(Ge - Gb).max() / np.abs(Gb).max()
     assert d_rk < 1e-6 and d_eu > 100 * d_rk
     assert err > 0
+
+
+def test_rhs_finite_when_cutoff_equals_a_mesh_point():
+    """Lambda on a mesh point makes a delta point fall on w = 0 with theta = 0: the term is
+    absent (G vanishes below the cutoff) and the RHS stays finite."""
+    mesh = O.mesh_exponential(6, 0.05, 5.0)
+    f = _evolved(W.square_j1j2(1.0, 0.5), 1, mesh, [4.0, 2.0, 1.0])
+    for lam in (mesh[0], mesh[2], mesh[-1]):
+        dg, dG = f.rhs(lam)
+        assert np.all(np.isfinite(dg)) and np.all(np.isfinite(dG))
