@@ -108,25 +108,26 @@ def _dist():
     return ws, rank, local
 
 
-def _algorithmic_flops(counts: np.ndarray, N: int, Ns: int, nc: int, P: int) -> float:
-    """Floating-point operations of one vertex-flow launch as the algorithm is laid out:
-    per integration node and stored triple, trilinear interpolation (8 FMA = 16 flop per
-    interpolated value) of two vertex rows over all irreducible sites and components for the
-    s and u channels and two rows plus two on-site rows for the t channel; the projected
-    products (s / u: 14 flop per site for SU2, 36 for XYZ); the lattice sum (3 flop per table
-    entry and component); the t-channel on-site terms (9 flop per site and component)."""
+def _algorithmic_flops(counts: np.ndarray, N: int, Ns: int, nc: int, P: int, nprod: int) -> float:
+    """Floating-point operations of one vertex-flow launch.  Per stored triple (s, t, u) and
+    integration node: every vertex row needed by the flow equations is interpolated over all
+    irreducible sites and components; one of the three frequency arguments of every row is a
+    mesh frequency, so an interpolated value is 4 corners = 8 flop.  The s and u channels need
+    two rows and the projected product (14 flop per site SU2, 36 XYZ); the t channel needs two
+    rows, two on-site rows (n_c values), the on-site terms (9 flop per site and component)
+    and the lattice sum, evaluated as 3 flop (W A B + acc) per distinct product of table
+    rows.  Per triple, the lattice sum's table gather adds P n_c flop."""
     row = Ns * nc
     prod = 14 if nc == 2 else 36
-    per_s = 2 * row * 16 + Ns * prod
+    per_s = 2 * row * 8 + Ns * prod
     per_u = per_s
-    per_t = (2 * row + 2 * nc) * 16 + 3 * P * nc + 9 * row
+    per_t = (2 * row + 2 * nc) * 8 + 3 * nprod + 9 * row
     ns, nt, nu = counts[0].astype(np.float64), counts[1].astype(np.float64), counts[2].astype(np.float64)
-    # triples: s_i >= u_i, any t_i
-    tot = 0.0
-    cs = np.cumsum(np.ones(N))  # number of u_i <= s_i
-    tot += N * float(np.sum(ns * cs)) * per_s                # s channel: depends on s_i
-    tot += (N * (N + 1) / 2) * float(np.sum(nt)) * per_t     # t channel: depends on t_i
-    tot += N * float(np.sum(nu * (N - np.arange(N)))) * per_u  # u channel: depends on u_i
+    cs = np.arange(1, N + 1, dtype=np.float64)   # number of u_i <= s_i
+    tot = N * float(np.sum(ns * cs)) * per_s                   # s channel: node count depends on s_i
+    tot += (N * (N + 1) / 2) * float(np.sum(nt)) * per_t       # t channel: on t_i
+    tot += N * float(np.sum(nu * (N - np.arange(N)))) * per_u  # u channel: on u_i
+    tot += (N * N * (N + 1) / 2) * P * nc                      # lattice-sum gather per triple
     return tot
 
 
@@ -313,13 +314,36 @@ def run_ours(args):
     value = n_ent * ws / (t_step * 1e-3)
 
     # roofline of the dominant kernel (vertex flow)
-    flops = _algorithmic_flops(counts, fl.N, lat.N_s, fl.n_comp, lat.P)
+    flops = _algorithmic_flops(counts, fl.N, lat.N_s, fl.n_comp, lat.P, fl.lattice_sum_products())
     k_ms = kms[2] / max(kn[2], 1)
     achieved = flops / (k_ms * 1e-3) / 1e12
     peak_fp64_nominal = 1.25     # TFLOP/s, recipe table
     peak_fp32_units = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
     peak = peak_fp64_nominal if prec == sr.SR_FP64 else peak_fp32_units
     measured_peak = sr.sr_peak_fma(prec) / 1e12
+
+    extra = {}
+    if not args.no_fp32 and prec == sr.SR_FP64:
+        fl2, ms2, kms2, kn2, counts2, _, _ = _measure_precision(sr, torch, cfg, lat, mesh, sr.SR_FP32_MIXED,
+                                                                 args.steps, args.warmup, lams, flush, kgrid)
+        # accuracy of the mixed flow after the same Euler steps: chi(k) and Gamma vs the FP64 flow
+        assert abs(fl.lam - fl2.lam) <= 1e-12 * fl.lam
+        ck64, _ = fl.measure(kgrid, want_ij=False)
+        ck32, _ = fl2.measure(kgrid, want_ij=False)
+        _, G64 = fl.get_state()
+        _, G32 = fl2.get_state()
+        flops2 = _algorithmic_flops(counts2, fl2.N, lat.N_s, fl2.n_comp, lat.P, fl2.lattice_sum_products())
+        k2 = kms2[2] / max(kn2[2], 1)
+        extra["fp32_mixed"] = {"value": n_ent * ws / (sum(ms2) / len(ms2) * 1e-3), "unit": UNIT,
+                               "ms_per_step": sum(ms2) / len(ms2), "dtype": "f32-mixed",
+                               "gamma_rhs_ms": k2,
+                               "gamma_rhs_tflops": flops2 / (k2 * 1e-3) / 1e12,
+                               "frac_of_fp32_peak": flops2 / (k2 * 1e-3) / 1e12 / (152 * 128 * 2 * 2.07e9 / 1e12),
+                               "chi_rel_err_vs_fp64": float(np.abs(ck32 - ck64).max() / np.abs(ck64).max()),
+                               "gamma_rel_err_vs_fp64": float((G32 - G64).abs().max() / G64.abs().max()),
+                               "lambda": fl.lam,
+                               "note": f"both flows integrated with the same {i_end} Euler steps from Lambda=100"}
+        fl2.close()
 
     # end to end through the public API: state in from pinned host memory, step, state out
     g_h = torch.empty(fl.N, dtype=torch.float64).pin_memory()
@@ -344,20 +368,6 @@ def run_ours(args):
         lam = lam * 0.95
     e2e_val = n_ent * ws / statistics.median(e2e_t)
     bytes_state = 8 * (fl.N + fl.n_gamma)
-
-    extra = {}
-    if not args.no_fp32 and prec == sr.SR_FP64:
-        fl2, ms2, kms2, kn2, counts2, _, _ = _measure_precision(sr, torch, cfg, lat, mesh, sr.SR_FP32_MIXED,
-                                                                 args.steps, args.warmup, lams, flush, kgrid)
-        # accuracy of the mixed flow at the same cutoff: chi and Gamma against the FP64 flow
-        ck64, _ = fl.measure(kgrid, want_ij=False) if abs(fl.lam - fl2.lam) < 1e-12 else (None, None)
-        ck32, _ = fl2.measure(kgrid, want_ij=False)
-        extra["fp32_mixed"] = {"value": n_ent * ws / (sum(ms2) / len(ms2) * 1e-3), "unit": UNIT,
-                               "ms_per_step": sum(ms2) / len(ms2),
-                               "gamma_rhs_ms": kms2[2] / max(kn2[2], 1),
-                               "chi_rel_err_vs_fp64": (float(np.abs(ck32 - ck64).max() / np.abs(ck64).max())
-                                                       if ck64 is not None else None)}
-        fl2.close()
 
     clocks = sampler.summary() if sampler else None
     cpu = None

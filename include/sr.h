@@ -172,6 +172,10 @@ sr_status sr_flow_profile_read(sr_flow* flow, double* ms /*3*/, long* launches /
  * by transfer frequency), from which the algorithmic operation count follows.  Synchronises. */
 sr_status sr_flow_node_counts(const sr_flow* flow, int* counts);
 
+/* Number of distinct products in the lattice sum of one vertex entry (the deduplicated
+ * pairs (stored site A, component) x (stored site B, component) over the table). */
+sr_status sr_flow_lattice_sum_products(const sr_flow* flow, long* n_products);
+
 /* Throughput of fused multiply-adds on the current device (FLOP/s, 2 per FMA) for FP64
  * (precision = SR_FP64) or FP32 (SR_FP32_MIXED), from a register-resident FMA chain kernel
  * timed with CUDA events. */

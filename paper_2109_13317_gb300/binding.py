@@ -85,6 +85,7 @@ def load_library():
             "sr_flow_profile_enable": [vp, i],
             "sr_flow_profile_read": [vp, dp, lp],
             "sr_flow_node_counts": [vp, ip],
+            "sr_flow_lattice_sum_products": [vp, lp],
             "sr_peak_fma": [i, dp],
         }
         for name, args in sig.items():
@@ -290,6 +291,11 @@ class Flow:
         n = (C.c_long * 3)()
         _check(self._lib.sr_flow_profile_read(self.h, _dptr(ms), n))
         return ms, np.array(list(n))
+
+    def lattice_sum_products(self) -> int:
+        n = C.c_long()
+        _check(self._lib.sr_flow_lattice_sum_products(self.h, C.byref(n)))
+        return n.value
 
     def node_counts(self) -> np.ndarray:
         out = np.zeros(3 * self.N, dtype=np.int32)

@@ -20,6 +20,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <string>
 #include <vector>
@@ -60,15 +61,15 @@ constexpr int kQC = 16;       // integration nodes per shared-memory block
 constexpr int kThreads = 128;
 
 // Propagator products with Sigma = -i gamma: g(a) g(b) and g(a) r(b), r = -g^2 dSigma/dLambda.
-__device__ __forceinline__ double prop_gg(const double* w, int N, const double* gam, double a, double b) {
-    double ga = a + interp_odd(w, N, gam, a);
-    double gb = b + interp_odd(w, N, gam, b);
+__device__ __forceinline__ double prop_gg(const double* w, const double* invh, int N, const double* gam, double a, double b) {
+    double ga = a + interp_odd(w, invh, N, gam, a);
+    double gb = b + interp_odd(w, invh, N, gam, b);
     return -1.0 / (ga * gb);
 }
-__device__ __forceinline__ double prop_gr(const double* w, int N, const double* gam, const double* dgam, double a, double b) {
-    double ga = a + interp_odd(w, N, gam, a);
-    double gb = b + interp_odd(w, N, gam, b);
-    double db = interp_odd(w, N, dgam, b);
+__device__ __forceinline__ double prop_gr(const double* w, const double* invh, int N, const double* gam, const double* dgam, double a, double b) {
+    double ga = a + interp_odd(w, invh, N, gam, a);
+    double gb = b + interp_odd(w, invh, N, gam, b);
+    double db = interp_odd(w, invh, N, dgam, b);
     return -db / (ga * gb * gb);
 }
 
@@ -79,14 +80,14 @@ __device__ __forceinline__ bool in_support(double lam, int ch, double v, double 
     return fabs(v + m) >= lam;
 }
 
-__device__ __forceinline__ double preg(const double* w, int N, const double* gam, const double* dgam, int ch, double v, double x) {
-    if (ch == 0) return prop_gr(w, N, gam, dgam, x, v - x) + prop_gr(w, N, gam, dgam, v - x, x);
-    if (ch == 1) return prop_gr(w, N, gam, dgam, x, x - v) + prop_gr(w, N, gam, dgam, x - v, x);
-    return prop_gr(w, N, gam, dgam, x, v + x) + prop_gr(w, N, gam, dgam, v + x, x);
+__device__ __forceinline__ double preg(const double* w, const double* invh, int N, const double* gam, const double* dgam, int ch, double v, double x) {
+    if (ch == 0) return prop_gr(w, invh, N, gam, dgam, x, v - x) + prop_gr(w, invh, N, gam, dgam, v - x, x);
+    if (ch == 1) return prop_gr(w, invh, N, gam, dgam, x, x - v) + prop_gr(w, invh, N, gam, dgam, x - v, x);
+    return prop_gr(w, invh, N, gam, dgam, x, v + x) + prop_gr(w, invh, N, gam, dgam, v + x, x);
 }
 
 // Integration nodes of one channel (ch = 0 s, 1 t, 2 u) at transfer frequency w[vi].
-__global__ void k_channel_nodes(Geo g, const double* __restrict__ w, const double* __restrict__ gam,
+__global__ void k_channel_nodes(Geo g, const double* __restrict__ w, const double* __restrict__ invh, const double* __restrict__ gam,
                                 const double* __restrict__ dgam, double lam, double* __restrict__ nx,
                                 double* __restrict__ nW, float* __restrict__ nWf, int* __restrict__ ncount) {
     int id = blockIdx.x * blockDim.x + threadIdx.x;
@@ -105,19 +106,19 @@ __global__ void k_channel_nodes(Geo g, const double* __restrict__ w, const doubl
         double a;
         if (ch == 0) {          // G(w) S(s - w): w = s - L;  G(s - w) S(w): w = L
             a = v - L;
-            double val = (fabs(a) - lam >= 0.0) ? prop_gg(w, N, gam, a, L) * inv2pi : 0.0;
+            double val = (fabs(a) - lam >= 0.0) ? prop_gg(w, invh, N, gam, a, L) * inv2pi : 0.0;
             X[n] = a; Wt[n] = val; ++n;
             X[n] = L; Wt[n] = val; ++n;
         } else if (ch == 1) {   // G(w) S(w - t): w = t + L;  G(w - t) S(w): w = L
             a = v + L;
-            X[n] = a; Wt[n] = (fabs(a) - lam >= 0.0) ? prop_gg(w, N, gam, a, L) * inv2pi : 0.0; ++n;
+            X[n] = a; Wt[n] = (fabs(a) - lam >= 0.0) ? prop_gg(w, invh, N, gam, a, L) * inv2pi : 0.0; ++n;
             a = L - v;
-            X[n] = L; Wt[n] = (fabs(a) - lam >= 0.0) ? prop_gg(w, N, gam, a, L) * inv2pi : 0.0; ++n;
+            X[n] = L; Wt[n] = (fabs(a) - lam >= 0.0) ? prop_gg(w, invh, N, gam, a, L) * inv2pi : 0.0; ++n;
         } else {                // G(w) S(u + w): w = L - u;  G(u + w) S(w): w = L
             a = L - v;
-            X[n] = a; Wt[n] = (fabs(a) - lam >= 0.0) ? prop_gg(w, N, gam, a, L) * inv2pi : 0.0; ++n;
+            X[n] = a; Wt[n] = (fabs(a) - lam >= 0.0) ? prop_gg(w, invh, N, gam, a, L) * inv2pi : 0.0; ++n;
             a = v + L;
-            X[n] = L; Wt[n] = (fabs(a) - lam >= 0.0) ? prop_gg(w, N, gam, a, L) * inv2pi : 0.0; ++n;
+            X[n] = L; Wt[n] = (fabs(a) - lam >= 0.0) ? prop_gg(w, invh, N, gam, a, L) * inv2pi : 0.0; ++n;
         }
     }
     // regular Katanin part: trapezoid on {+-w_n} merged with the break points, clipped
@@ -145,7 +146,7 @@ __global__ void k_channel_nodes(Geo g, const double* __restrict__ w, const doubl
             wgt += 0.5 * (pts[i + 1] - pts[i]);
         if (wgt == 0.0) continue;
         X[n] = pts[i];
-        Wt[n] = wgt * preg(w, N, gam, dgam, ch, v, pts[i]) * inv2pi;
+        Wt[n] = wgt * preg(w, invh, N, gam, dgam, ch, v, pts[i]) * inv2pi;
         ++n;
     }
     for (int i = 0; i < n; ++i) Wf[i] = (float)Wt[i];
@@ -183,13 +184,13 @@ __global__ void k_sigma_rhs(Geo g, Tabs tb, const double* __restrict__ w, const 
     for (int sg = 0; sg < 2; ++sg) {
         const double w2 = sg == 0 ? lam : -lam;
         Desc<double> d;
-        make_desc(w1 + w2, 0.0, w1 - w2, w, g, d);
+        make_desc(w1 + w2, 0.0, w1 - w2, w, tb.invh, g, d);
         double h = 0.0;
         for (int r = threadIdx.x; r < g.Ns; r += blockDim.x) h += (double)tb.mult[r] * row_value(G, d, tb, g, r, 0);
         h *= 2.0;
         if (threadIdx.x == 0) {
             Desc<double> e;
-            make_desc(w1 + w2, w2 - w1, 0.0, w, g, e);
+            make_desc(w1 + w2, w2 - w1, 0.0, w, tb.invh, g, e);
             double f = 0.0;
             if (g.nc == 2) f = row_value(G, e, tb, g, 0, 0) + 3.0 * row_value(G, e, tb, g, 0, 1);
             else for (int c = 0; c < 4; ++c) f += row_value(G, e, tb, g, 0, c);
@@ -200,8 +201,8 @@ __global__ void k_sigma_rhs(Geo g, Tabs tb, const double* __restrict__ w, const 
     block_sum<2>(H, red);
     if (threadIdx.x == 0) {
         double acc = 0.0;
-        acc += H[0] / (lam + interp_odd(w, g.N, gam, lam));
-        acc += H[1] / (-lam + interp_odd(w, g.N, gam, -lam));
+        acc += H[0] / (lam + interp_odd(w, tb.invh, g.N, gam, lam));
+        acc += H[1] / (-lam + interp_odd(w, tb.invh, g.N, gam, -lam));
         dgam[n] = -acc / (2.0 * kPi);
     }
 }
@@ -259,7 +260,7 @@ __device__ __forceinline__ ShPtrs<T> carve(unsigned char* raw, const Geo& g, con
     auto take = [&](size_t bytes) { unsigned char* q = raw + off; off += (bytes + 15) & ~size_t(15); return q; };
     p.desc = (Desc<T>*)take(sizeof(Desc<T>) * kQC * 4);
     p.acc = (T*)take(sizeof(T) * g.Ns * NC);
-    p.part = (T*)take(sizeof(T) * tb.nseg * NC);
+    p.part = (T*)take(sizeof(T) * tb.nprod);
     p.rows = (T*)take(sizeof(T) * kQC * 2 * g.Ns * NC);
     p.onrow = (T*)take(sizeof(T) * kQC * 2 * NC);
     p.wq = (T*)take(sizeof(T) * kQC);
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const do
     const int row = g.Ns * NC;
 
     for (int o = tid; o < row; o += blockDim.x) sh.acc[o] = (T)0;
-    for (int o = tid; o < tb.nseg * NC; o += blockDim.x) sh.part[o] = (T)0;
+    for (int o = tid; o < tb.nprod; o += blockDim.x) sh.part[o] = (T)0;
 
     for (int ch = 0; ch < 3; ++ch) {
         const int vi = ch == 0 ? si : (ch == 1 ? ti : ui);
@@ -323,7 +324,7 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const do
                 const double x = X[q0 + q];
                 double a, b, c;
                 node_args(ch, rw, x, s, t, u, w1p, w2p, w1, w2, a, b, c);
-                make_desc(a, b, c, w, g, sh.desc[q * 4 + rw]);
+                make_desc(a, b, c, w, tb.invh, g, sh.desc[q * 4 + rw]);
                 if (rw == 0) sh.wq[q] = Wp[q0 + q];
             }
             __syncthreads();
@@ -359,17 +360,13 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const do
                     for (int c = 0; c < NC; ++c) sh.acc[r * NC + c] += accl[c];
                 }
             } else {
-                // lattice sum, per table segment (owned by one thread across node blocks)
-                for (int o = tid; o < tb.nseg * NC; o += blockDim.x) {
-                    const int sgi = o / NC, c = o % NC;
+                // lattice sum: every distinct product (row A entry, row B entry) integrated over
+                // the nodes of this block; each product is owned by one thread across blocks
+                for (int o = tid; o < tb.nprod; o += blockDim.x) {
+                    const int2 pr = tb.prod[o];
                     T a = (T)0;
-                    for (int e = tb.seg_start[sgi]; e < tb.seg_start[sgi + 1]; ++e) {
-                        const int4 en = tb.rpa[e];
-                        const int ca = perm_of(en.z, c), cb = perm_of(en.w, c);
-                        for (int q = 0; q < qn; ++q)
-                            a += sh.wq[q] * sh.rows[(q * 2) * row + en.x * NC + ca] *
-                                 sh.rows[(q * 2 + 1) * row + en.y * NC + cb];
-                    }
+                    for (int q = 0; q < qn; ++q)
+                        a += sh.wq[q] * sh.rows[(q * 2) * row + pr.x] * sh.rows[(q * 2 + 1) * row + pr.y];
                     sh.part[o] += a;
                 }
                 // on-site terms
@@ -400,7 +397,7 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const do
     for (int o = tid; o < row; o += blockDim.x) {
         const int r = o / NC, c = o % NC;
         T a = (T)0;
-        for (int sgi = tb.r_seg[r]; sgi < tb.r_seg[r + 1]; ++sgi) a += sh.part[sgi * NC + c];
+        for (int k = tb.gath_off[o]; k < tb.gath_off[o + 1]; ++k) a += sh.part[tb.gath_idx[k]];
         const double v = (double)sh.acc[o] - 2.0 * (double)a;
         dG[((size_t)(p * g.N + ti) * NC + c) * g.Ns + r] = v;
     }
@@ -481,13 +478,13 @@ __global__ void k_chi(Geo g, Tabs tb, const double* __restrict__ w, const double
         for (int i = 0; i < N; ++i) if (w[i] > lam) y[K++] = w[i];
         for (int k = 0; k < K; ++k) Wn[k] = 0.0;
         for (int k = 0; k + 1 < K; ++k) {
-            double ya = y[k] + interp_odd(w, N, gam, y[k]);
-            double yb = y[k + 1] + interp_odd(w, N, gam, y[k + 1]);
+            double ya = y[k] + interp_odd(w, tb.invh, N, gam, y[k]);
+            double yb = y[k + 1] + interp_odd(w, tb.invh, N, gam, y[k + 1]);
             double seg = (y[k + 1] - y[k]) / (ya * yb);
             Wn[k] += 0.5 * seg;
             Wn[k + 1] += 0.5 * seg;
         }
-        Wn[K - 1] += 1.0 / (y[K - 1] + interp_odd(w, N, gam, y[K - 1]));
+        Wn[K - 1] += 1.0 / (y[K - 1] + interp_odd(w, tb.invh, N, gam, y[K - 1]));
         Ksh = K;
     }
     __syncthreads();
@@ -501,12 +498,12 @@ __global__ void k_chi(Geo g, Tabs tb, const double* __restrict__ w, const double
         const double xq = qi < K ? y[qi] : -y[qi - K];
         const double wpq = Wn[pi % K] * Wn[qi % K];
         Desc<double> d;
-        make_desc(xp + xq, 0.0, xp - xq, w, g, d);
+        make_desc(xp + xq, 0.0, xp - xq, w, tb.invh, g, d);
         double v[NC], e[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) v[c] = row_value(G, d, tb, g, pm.x, perm_of(pm.y, c));
         if (on) {
-            make_desc(xp + xq, xq - xp, 0.0, w, g, d);
+            make_desc(xp + xq, xq - xp, 0.0, w, tb.invh, g, d);
 #pragma unroll
             for (int c = 0; c < NC; ++c) e[c] = row_value(G, d, tb, g, pon.x, perm_of(pon.y, c));
         }
@@ -584,9 +581,10 @@ struct sr_flow {
     DevBuf<double> nx, nW;
     DevBuf<float> nWf;
     DevBuf<int> ncount;
-    DevBuf<int> swap_r, swap_perm, onsite_perm, mult, seg_start, seg_r, r_seg;
-    DevBuf<int4> rpa;
-    int nseg = 0;
+    DevBuf<int> swap_r, swap_perm, onsite_perm, mult, gath_off, gath_idx;
+    DevBuf<int2> prod;
+    DevBuf<double> invh;
+    int nprod = 0;
     DevBuf<double> init;
     DevBuf<int2> chi_map;
     DevBuf<int> chi_onsite;
@@ -606,18 +604,18 @@ struct sr_flow {
     Tabs tabs() const {
         Tabs t;
         t.swap_r = swap_r.p; t.swap_perm = swap_perm.p; t.onsite_perm = onsite_perm.p; t.mult = mult.p;
-        t.rpa = rpa.p; t.seg_start = seg_start.p; t.seg_r = seg_r.p; t.r_seg = r_seg.p; t.nseg = nseg;
+        t.prod = prod.p; t.gath_off = gath_off.p; t.gath_idx = gath_idx.p; t.nprod = nprod; t.invh = invh.p;
         return t;
     }
 };
 
 static int pack_perm(const sr::Perm& p) { return p[0] | (p[1] << 2) | (p[2] << 4) | (p[3] << 6); }
 
-static size_t rhs_smem_bytes(const Geo& g, int nseg, bool fp32) {
+static size_t rhs_smem_bytes(const Geo& g, int nprod, bool fp32) {
     size_t tsz = fp32 ? 4 : 8;
     size_t dsz = fp32 ? sizeof(Desc<float>) : sizeof(Desc<double>);
     auto rnd = [](size_t b) { return (b + 15) & ~size_t(15); };
-    return rnd(dsz * kQC * 4) + rnd(tsz * g.Ns * g.nc) + rnd(tsz * nseg * g.nc) + rnd(tsz * kQC * 2 * g.Ns * g.nc) +
+    return rnd(dsz * kQC * 4) + rnd(tsz * g.Ns * g.nc) + rnd(tsz * nprod) + rnd(tsz * kQC * 2 * g.Ns * g.nc) +
            rnd(tsz * kQC * 2 * g.nc) + rnd(tsz * kQC);
 }
 
@@ -648,7 +646,7 @@ static sr_status run_rhs(sr_flow* f, double lam, const double* gam_s, const doub
     if (sr_status s = prof_end(f, 0, e0)) return s;
     int nt = 3 * g.N;
     if (sr_status s = prof_begin(f, 1, &e0)) return s;
-    k_channel_nodes<<<(nt + 63) / 64, 64, 0, f->stream>>>(g, f->w.p, gam_s, dgam_o, lam, f->nx.p, f->nW.p, f->nWf.p,
+    k_channel_nodes<<<(nt + 63) / 64, 64, 0, f->stream>>>(g, f->w.p, f->invh.p, gam_s, dgam_o, lam, f->nx.p, f->nW.p, f->nWf.p,
                                                            f->ncount.p);
     if (sr_status s = prof_end(f, 1, e0)) return s;
     const int blocks = g.npair * g.N;
@@ -776,29 +774,41 @@ extern "C" sr_status sr_flow_init(const sr_lattice* lat, int n_freq, const doubl
     // lattice tables
     std::vector<int> sp(lat->Ns), op(lat->Ns);
     for (int r = 0; r < lat->Ns; ++r) { sp[r] = pack_perm(lat->swap_perm[r]); op[r] = pack_perm(lat->onsite_perm[r]); }
-    std::vector<int4> rp(lat->rpa.size());
-    for (size_t e = 0; e < lat->rpa.size(); ++e)
-        rp[e] = make_int4(lat->rpa[e].rA, lat->rpa[e].rB, pack_perm(lat->rpa[e].pA), pack_perm(lat->rpa[e].pB));
-    // lattice-sum work segments: runs of at most kSeg consecutive entries of one output site;
-    // segment k covers entries [seg_start[k], seg_start[k + 1])
-    std::vector<int> segs, segr, rseg(lat->Ns + 1, 0);
-    for (int r = 0; r < lat->Ns; ++r) {
-        rseg[r] = (int)segr.size();
-        for (int e = lat->rpa_off[r]; e < lat->rpa_off[r + 1]; e += kSeg) { segs.push_back(e); segr.push_back(r); }
+    // lattice sum: distinct products (row index A, row index B) over all table entries and
+    // components, and for every output (site, component) the list of its products
+    std::vector<int2> prods;
+    std::vector<int> goff(lat->Ns * lat->nc + 1, 0), gidx;
+    {
+        std::map<std::pair<int, int>, int> pid;
+        for (int r = 0; r < lat->Ns; ++r)
+            for (int c = 0; c < lat->nc; ++c) {
+                goff[r * lat->nc + c] = (int)gidx.size();
+                for (int e = lat->rpa_off[r]; e < lat->rpa_off[r + 1]; ++e) {
+                    const sr::RpaEntry& en = lat->rpa[e];
+                    int ia = en.rA * lat->nc + en.pA[c], ib = en.rB * lat->nc + en.pB[c];
+                    auto key = std::make_pair(ia, ib);
+                    auto it = pid.find(key);
+                    int u;
+                    if (it == pid.end()) { u = (int)prods.size(); pid[key] = u; prods.push_back(make_int2(ia, ib)); }
+                    else u = it->second;
+                    gidx.push_back(u);
+                }
+            }
+        goff[lat->Ns * lat->nc] = (int)gidx.size();
     }
-    rseg[lat->Ns] = (int)segr.size();
-    segs.push_back((int)lat->rpa.size());
-    f->nseg = (int)segr.size();
+    f->nprod = (int)prods.size();
+    std::vector<double> ih(n_freq - 1);
+    for (int i = 0; i + 1 < n_freq; ++i) ih[i] = 1.0 / (freq_pos[i + 1] - freq_pos[i]);
     cudaStream_t st = f->stream;
     CK(f->w.upload(freq_pos, n_freq, st));
+    CK(f->invh.upload(ih.data(), ih.size(), st));
     CK(f->swap_r.upload(lat->swap_r.data(), lat->Ns, st));
     CK(f->swap_perm.upload(sp.data(), lat->Ns, st));
     CK(f->onsite_perm.upload(op.data(), lat->Ns, st));
     CK(f->mult.upload(lat->mult.data(), lat->Ns, st));
-    CK(f->rpa.upload(rp.data(), rp.size(), st));
-    CK(f->seg_start.upload(segs.data(), segs.size(), st));
-    CK(f->seg_r.upload(segr.data(), segr.size(), st));
-    CK(f->r_seg.upload(rseg.data(), rseg.size(), st));
+    CK(f->prod.upload(prods.data(), prods.size(), st));
+    CK(f->gath_off.upload(goff.data(), goff.size(), st));
+    CK(f->gath_idx.upload(gidx.data(), gidx.size(), st));
     CK(f->init.upload(lat->init_gamma.data(), lat->init_gamma.size(), st));
     {
         std::vector<int2> cm(lat->chi_map.size());
@@ -824,7 +834,7 @@ extern "C" sr_status sr_flow_init(const sr_lattice* lat, int n_freq, const doubl
     k_fill_init<<<(unsigned)((g.nent + 255) / 256), 256, 0, st>>>(g, f->init.p, f->G.p);
     CK(cudaGetLastError());
     if (sr_status s2 = refresh_shadow(f.get(), f->G.p, f->Gf.p)) return s2;
-    f->smem_rhs = rhs_smem_bytes(g, f->nseg, precision == SR_FP32_MIXED);
+    f->smem_rhs = rhs_smem_bytes(g, f->nprod, precision == SR_FP32_MIXED);
     if (f->smem_rhs > 227 * 1024) return fail(SR_EUNSUPPORTED, "lattice too large for one CTA's shared memory (%zu bytes)", f->smem_rhs);
     if (precision == SR_FP64) {
         CK(cudaFuncSetAttribute(k_gamma_rhs<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->smem_rhs));
@@ -1088,6 +1098,12 @@ extern "C" sr_status sr_flow_profile_read(sr_flow* f, double* ms, long* launches
         ms[k] = acc;
         launches[k] = (long)f->ev[k].size();
     }
+    return SR_OK;
+}
+
+extern "C" sr_status sr_flow_lattice_sum_products(const sr_flow* f, long* n) {
+    if (!f || !n) return fail(SR_EINVAL, "null argument");
+    *n = f->nprod;
     return SR_OK;
 }
 
