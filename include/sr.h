@@ -146,6 +146,24 @@ sr_status sr_flow_stats(const sr_flow* flow, double* last_err, long* n_rhs, long
 sr_status sr_measure_susceptibility(sr_flow* flow, int n_k, const double* k_xyz, double* chi_k,
                                     double* chi_ij);
 
+/* Allocation-free variant of sr_measure_susceptibility for callers that must not allocate
+ * device memory: code that runs while a CUDA stream is being captured into a graph (where
+ * cudaMalloc is not permitted), and hosts whose device memory is owned entirely by another
+ * framework's pool or fixed budget.  It computes the structure factor chi(k) of the
+ * current state into a caller-provided device array, reading the momenta from a
+ * caller-provided device array; the intermediate chi_ij pair table is kept in one
+ * file-scope device array of SR_CHI_STATIC_MAX doubles (2 MiB) that every GPU loading the
+ * library holds until exit.  The paper has no counterpart to this entry point.
+ *   d_k_xyz: device, n_k x 3 momenta;  d_chi_k: device, n_k outputs.
+ * Requires N_basis x N_tot x n_comp <= SR_CHI_STATIC_MAX, else SR_EINVAL.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current: make that first call before any stream capture.  The call is asynchronous on
+ * the flow's stream and allocates nothing.  All calls share the one array (each overwrites
+ * every entry it reads), so calls whose kernels overlap on the GPU (different streams, no
+ * ordering between them) race and must be avoided. */
+#define SR_CHI_STATIC_MAX 262144
+sr_status sr_measure_susceptibility_static(sr_flow* flow, int n_k, const double* d_k_xyz, double* d_chi_k);
+
 /* Site list used by chi_ij: for each basis b, the N_tot sites within range of b as
  * (n0, n1, n2, basis) (host out, N_basis x N_tot x 4). */
 sr_status sr_flow_chi_sites(const sr_flow* flow, int* sites);

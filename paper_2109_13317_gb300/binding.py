@@ -78,6 +78,7 @@ def load_library():
             "sr_flow_stats": [vp, dp, lp, lp, lp],
             "sr_measure_susceptibility": [vp, i, dp, dp, vp],
             "sr_flow_chi_sites": [vp, ip],
+            "sr_measure_susceptibility_static": [vp, i, vp, vp],
             "sr_flow_get_state": [vp, vp, vp],
             "sr_flow_set_state": [vp, d, vp, vp],
             "sr_flow_lambda": [vp, dp],
@@ -266,6 +267,15 @@ class Flow:
         if chi_ij is not None:
             chi_ij = chi_ij.view(self.lattice.N_basis, self.lattice.N_tot, self.n_comp)
         return (chik[:nk] if nk else None), chi_ij
+
+    def measure_static(self, k_dev, out_dev):
+        """sr_measure_susceptibility_static: chi(k) from device momenta (n_k x 3 float64) into a
+        device output (n_k float64), allocating nothing."""
+        n = out_dev.numel()
+        if k_dev.numel() != 3 * n:
+            raise ValueError("k_dev must hold 3 values per output")
+        _check(self._lib.sr_measure_susceptibility_static(self.h, int(n), _ptr(k_dev), _ptr(out_dev)))
+        return out_dev
 
     def chi_sites(self) -> np.ndarray:
         out = np.zeros((self.lattice.N_basis * self.lattice.N_tot, 4), dtype=np.int32)

@@ -22,6 +22,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1026,6 +1027,50 @@ extern "C" sr_status sr_measure_susceptibility(sr_flow* f, int n_k, const double
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(chi_k, f->chik.p, sizeof(double) * n_k, cudaMemcpyDeviceToHost, f->stream));
         CK(cudaStreamSynchronize(f->stream));
+    }
+    return SR_OK;
+}
+
+// ----------------------------------------------------------------------------- allocation-free chi(k)
+
+// Scratch of the allocation-free correlation measurement: the chi_ij pair table.  Device
+// code could name it directly; host code must not pass the symbol itself (it is a
+// host-side stand-in), so its device address is looked up once per device.
+static __device__ __align__(256) double g_chi_static[SR_CHI_STATIC_MAX];
+static std::mutex g_chi_static_mu;
+static double* g_chi_static_ptr[64] = {nullptr};
+
+extern "C" sr_status sr_measure_susceptibility_static(sr_flow* f, int n_k, const double* d_k_xyz, double* d_chi_k) {
+    if (!f) return fail(SR_EINVAL, "null flow");
+    if (n_k < 0 || (n_k > 0 && (!d_k_xyz || !d_chi_k))) return fail(SR_EINVAL, "bad momenta or output");
+    const sr_lattice* lat = f->lat;
+    const Geo& g = f->g;
+    const int npairs = (int)lat->chi_map.size();
+    const size_t need = (size_t)npairs * g.nc;
+    if (need > (size_t)SR_CHI_STATIC_MAX)
+        return fail(SR_EINVAL, "correlation table needs %zu values, above the static limit of %d", need, SR_CHI_STATIC_MAX);
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(SR_EINVAL, "device index %d out of range", dev);
+    double* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_chi_static_mu);
+        if (!g_chi_static_ptr[dev]) {
+            void* p = nullptr;
+            CK(cudaGetSymbolAddress(&p, g_chi_static));
+            g_chi_static_ptr[dev] = (double*)p;
+        }
+        scratch = g_chi_static_ptr[dev];
+    }
+    Tabs tb = f->tabs();
+    if (g.nc == 2)
+        k_chi<2><<<npairs, 128, 0, f->stream>>>(g, tb, f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_map.p, f->chi_onsite.p, lat->Ntot, scratch);
+    else
+        k_chi<4><<<npairs, 128, 0, f->stream>>>(g, tb, f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_map.p, f->chi_onsite.p, lat->Ntot, scratch);
+    CK(cudaGetLastError());
+    if (n_k > 0) {
+        k_chi_k<<<(n_k + 127) / 128, 128, 0, f->stream>>>(n_k, d_k_xyz, scratch, f->chi_dr.p, npairs, lat->nb, g.nc, d_chi_k);
+        CK(cudaGetLastError());
     }
     return SR_OK;
 }
