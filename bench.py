@@ -384,7 +384,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == sr.SR_FP64 else "f32-mixed", "data": "synthetic",
             "config": {"workload": WORKLOAD, "lattice": "square J1=1 J2=0.5", "range_L": cfg.L,
-                       "N_s": lat.N_s, "N_tot": lat.N_tot, "P": lat.P, "n_freq": cfg.n_freq,
+                       "N_s": lat.N_s, "N_tot": lat.N_tot, "P": lat.P, "lattice_sum_products": fl.lattice_sum_products(),
+                       "n_freq": cfg.n_freq,
                        "freq_range": [cfg.w_min, cfg.w_max], "entries": n_ent, "core": "SU2",
                        "step": "Euler step (self-energy + vertex flow + update) + chi(k) on 64x64 k-grid",
                        "lambda_range_timed": [float(lam_rng[0]), float(lam_rng[1])],

@@ -185,13 +185,13 @@ __global__ void k_sigma_rhs(Geo g, Tabs tb, const double* __restrict__ w, const 
     for (int sg = 0; sg < 2; ++sg) {
         const double w2 = sg == 0 ? lam : -lam;
         Desc<double> d;
-        make_desc(w1 + w2, 0.0, w1 - w2, w, tb.invh, g, d);
+        make_desc(w1 + w2, 0.0, w1 - w2, 1, 0, tb, g, d);
         double h = 0.0;
         for (int r = threadIdx.x; r < g.Ns; r += blockDim.x) h += (double)tb.mult[r] * row_value(G, d, tb, g, r, 0);
         h *= 2.0;
         if (threadIdx.x == 0) {
             Desc<double> e;
-            make_desc(w1 + w2, w2 - w1, 0.0, w, tb.invh, g, e);
+            make_desc(w1 + w2, w2 - w1, 0.0, 2, 0, tb, g, e);
             double f = 0.0;
             if (g.nc == 2) f = row_value(G, e, tb, g, 0, 0) + 3.0 * row_value(G, e, tb, g, 0, 1);
             else for (int c = 0; c < 4; ++c) f += row_value(G, e, tb, g, 0, c);
@@ -325,22 +325,32 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const do
                 const double x = X[q0 + q];
                 double a, b, c;
                 node_args(ch, rw, x, s, t, u, w1p, w2p, w1, w2, a, b, c);
-                make_desc(a, b, c, w, tb.invh, g, sh.desc[q * 4 + rw]);
+                const int exs = ch == 0 ? 0 : (ch == 2 ? 2 : (rw < 2 ? 1 : 2));
+                make_desc(a, b, c, exs, vi, tb, g, sh.desc[q * 4 + rw]);
                 if (rw == 0) sh.wq[q] = Wp[q0 + q];
             }
             __syncthreads();
-            // phase 2: interpolated rows over all irreducible sites (and the on-site rows)
-            const int nfull = qn * 2 * row;
-            const int nall = nfull + (ch == 1 ? qn * 2 * NC : 0);
-            for (int idx = tid; idx < nall; idx += blockDim.x) {
-                if (idx < nfull) {
-                    const int q = idx / (2 * row), rem = idx % (2 * row), rw = rem / row, e = rem % row;
+            // phase 2: interpolated rows over all irreducible sites (and the on-site rows); the
+            // first row of every node (and the second on-site row) carries the node weight
+            {
+                const int nfull = qn * 2 * row;
+                int q = tid / (2 * row), rem = tid % (2 * row);
+                int rw = rem / row, e = rem % row;
+                for (int idx = tid; idx < nfull; idx += blockDim.x) {
                     const int r = e / NC, c = e % NC;
-                    sh.rows[(q * 2 + rw) * row + e] = row_value(G, sh.desc[q * 4 + rw], tb, g, r, c);
-                } else {
-                    const int j = idx - nfull;
-                    const int q = j / (2 * NC), rw = (j / NC) % 2, c = j % NC;
-                    sh.onrow[(q * 2 + rw) * NC + c] = row_value(G, sh.desc[q * 4 + 2 + rw], tb, g, 0, c);
+                    T v = row_value(G, sh.desc[q * 4 + rw], tb, g, r, c);
+                    if (rw == 0) v *= sh.wq[q];
+                    sh.rows[(q * 2 + rw) * row + e] = v;
+                    e += blockDim.x;
+                    while (e >= row) { e -= row; if (++rw == 2) { rw = 0; ++q; } }
+                }
+                if (ch == 1) {
+                    for (int j = tid; j < qn * 2 * NC; j += blockDim.x) {
+                        const int qq = j / (2 * NC), rr = (j / NC) % 2, c = j % NC;
+                        T v = row_value(G, sh.desc[qq * 4 + 2 + rr], tb, g, 0, c);
+                        if (rr == 1) v *= sh.wq[qq];
+                        sh.onrow[(qq * 2 + rr) * NC + c] = v;
+                    }
                 }
             }
             __syncthreads();
@@ -355,7 +365,7 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const do
                         const T* B = sh.rows + (q * 2 + 1) * row + r * NC;
                         if (ch == 0) s_product<T, NC>(A, B, o); else u_product<T, NC>(A, B, o);
 #pragma unroll
-                        for (int c = 0; c < NC; ++c) accl[c] += sh.wq[q] * o[c];
+                        for (int c = 0; c < NC; ++c) accl[c] += o[c];
                     }
 #pragma unroll
                     for (int c = 0; c < NC; ++c) sh.acc[r * NC + c] += accl[c];
@@ -367,7 +377,7 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const do
                     const int2 pr = tb.prod[o];
                     T a = (T)0;
                     for (int q = 0; q < qn; ++q)
-                        a += sh.wq[q] * sh.rows[(q * 2) * row + pr.x] * sh.rows[(q * 2 + 1) * row + pr.y];
+                        a += sh.rows[(q * 2) * row + pr.x] * sh.rows[(q * 2 + 1) * row + pr.y];
                     sh.part[o] += a;
                 }
                 // on-site terms
@@ -386,7 +396,7 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const do
                         for (int k = 0; k < NC; ++k) Cp[k] = C0[perm_of(pon, k)];
 #pragma unroll
                         for (int c = 0; c < NC; ++c)
-                            accl[c] += sh.wq[q] * (A[c] * onsite_factor<T, NC>(Cp, c) + onsite_factor<T, NC>(D, c) * B[c]);
+                            accl[c] += A[c] * onsite_factor<T, NC>(Cp, c) + onsite_factor<T, NC>(D, c) * B[c];
                     }
 #pragma unroll
                     for (int c = 0; c < NC; ++c) sh.acc[r * NC + c] += accl[c];
@@ -499,12 +509,12 @@ __global__ void k_chi(Geo g, Tabs tb, const double* __restrict__ w, const double
         const double xq = qi < K ? y[qi] : -y[qi - K];
         const double wpq = Wn[pi % K] * Wn[qi % K];
         Desc<double> d;
-        make_desc(xp + xq, 0.0, xp - xq, w, tb.invh, g, d);
+        make_desc(xp + xq, 0.0, xp - xq, 1, 0, tb, g, d);
         double v[NC], e[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) v[c] = row_value(G, d, tb, g, pm.x, perm_of(pm.y, c));
         if (on) {
-            make_desc(xp + xq, xq - xp, 0.0, w, tb.invh, g, d);
+            make_desc(xp + xq, xq - xp, 0.0, 2, 0, tb, g, d);
 #pragma unroll
             for (int c = 0; c < NC; ++c) e[c] = row_value(G, d, tb, g, pon.x, perm_of(pon.y, c));
         }
@@ -585,6 +595,7 @@ struct sr_flow {
     DevBuf<int> swap_r, swap_perm, onsite_perm, mult, gath_off, gath_idx;
     DevBuf<int2> prod;
     DevBuf<double> invh;
+    DevBuf<float> wf, invhf;
     int nprod = 0;
     DevBuf<double> init;
     DevBuf<int2> chi_map;
@@ -606,6 +617,7 @@ struct sr_flow {
         Tabs t;
         t.swap_r = swap_r.p; t.swap_perm = swap_perm.p; t.onsite_perm = onsite_perm.p; t.mult = mult.p;
         t.prod = prod.p; t.gath_off = gath_off.p; t.gath_idx = gath_idx.p; t.nprod = nprod; t.invh = invh.p;
+        t.w = w.p; t.wf = wf.p; t.invhf = invhf.p;
         return t;
     }
 };
@@ -803,6 +815,15 @@ extern "C" sr_status sr_flow_init(const sr_lattice* lat, int n_freq, const doubl
     cudaStream_t st = f->stream;
     CK(f->w.upload(freq_pos, n_freq, st));
     CK(f->invh.upload(ih.data(), ih.size(), st));
+    {
+        std::vector<float> wfl(n_freq), ihf(n_freq - 1);
+        for (int i = 0; i < n_freq; ++i) wfl[i] = (float)freq_pos[i];
+        for (int i = 0; i + 1 < n_freq; ++i) ihf[i] = 1.0f / (wfl[i + 1] - wfl[i]);
+        CK(f->wf.upload(wfl.data(), wfl.size(), st));
+        CK(f->invhf.upload(ihf.data(), ihf.size(), st));
+        g.log2w0 = (float)std::log2(freq_pos[0]);
+        g.inv_dlog2 = (float)((n_freq - 1) / std::log2(freq_pos[n_freq - 1] / freq_pos[0]));
+    }
     CK(f->swap_r.upload(lat->swap_r.data(), lat->Ns, st));
     CK(f->swap_perm.upload(sp.data(), lat->Ns, st));
     CK(f->onsite_perm.upload(op.data(), lat->Ns, st));

@@ -23,6 +23,8 @@ struct Geo {
     int npair;    // N (N + 1) / 2
     int nmax;     // node capacity per (channel, transfer frequency): 2N + 8
     long nent;    // Gamma entries
+    float log2w0;     // log2(w[0])
+    float inv_dlog2;  // (N - 1) / log2(w[N-1] / w[0]): interval guess for a log-spaced mesh
 };
 
 // Tables of the lattice (device pointers).
@@ -36,6 +38,9 @@ struct Tabs {
     const int* gath_idx;     // P * nc: product of each table entry, grouped by output
     int nprod;
     const double* invh;      // N - 1: 1 / (w[a+1] - w[a])
+    const double* w;         // N: mesh
+    const float* wf;         // N: mesh (FP32)
+    const float* invhf;      // N - 1: 1 / (w[a+1] - w[a]) (FP32)
 };
 
 __device__ __forceinline__ int perm_of(int packed, int c) { return (packed >> (2 * c)) & 3; }
@@ -86,40 +91,81 @@ struct Desc {
     T ws[8];    // weight applied to the spin components
 };
 
+// Interval guess for x inside the mesh, from the log spacing (exact for a logarithmic mesh
+// up to one step; any mesh is then corrected by the exact comparisons of the caller).
+__device__ __forceinline__ int interval_guess(const Geo& g, float x) {
+    int k = __float2int_rd((__log2f(x) - g.log2w0) * g.inv_dlog2);
+    return max(0, min(k, g.N - 2));
+}
+
+// Corners and weights of one axis: the interval [w_k, w_k+1] with w_k <= x < w_k+1 and the
+// paper's linear weights; one corner at a mesh point or outside the mesh (constant
+// extrapolation).  FP64 for T = double (decisions identical to a binary search), FP32
+// arithmetic for T = float.
 template <typename T>
-__device__ __forceinline__ void make_desc(double s, double t, double u, const double* __restrict__ w,
-                                          const double* __restrict__ invh, const Geo& g, Desc<T>& d) {
+__device__ __forceinline__ void axis_weights(const Tabs& tb, const Geo& g, double x, int& n, int* ix, T* wx) {
+    const int N = g.N;
+    if constexpr (sizeof(T) == 8) {
+        const double* w = tb.w;
+        if (x <= w[0]) { n = 1; ix[0] = 0; wx[0] = (T)1; return; }
+        if (x >= w[N - 1]) { n = 1; ix[0] = N - 1; wx[0] = (T)1; return; }
+        int k = interval_guess(g, (float)x);
+        while (k > 0 && x < w[k]) --k;
+        while (k < N - 2 && x >= w[k + 1]) ++k;
+        const double w1 = (x - w[k]) * tb.invh[k];
+        if (w1 == 0.0) { n = 1; ix[0] = k; wx[0] = (T)1; return; }
+        n = 2; ix[0] = k; ix[1] = k + 1;
+        wx[0] = (T)((w[k + 1] - x) * tb.invh[k]);
+        wx[1] = (T)w1;
+    } else {
+        const float* w = tb.wf;
+        const float xf = (float)x;
+        if (xf <= w[0]) { n = 1; ix[0] = 0; wx[0] = (T)1; return; }
+        if (xf >= w[N - 1]) { n = 1; ix[0] = N - 1; wx[0] = (T)1; return; }
+        int k = interval_guess(g, xf);
+        while (k > 0 && xf < w[k]) --k;
+        while (k < N - 2 && xf >= w[k + 1]) ++k;
+        const float w1 = (xf - w[k]) * tb.invhf[k];
+        if (w1 == 0.0f) { n = 1; ix[0] = k; wx[0] = (T)1; return; }
+        n = 2; ix[0] = k; ix[1] = k + 1;
+        wx[0] = (T)((w[k + 1] - xf) * tb.invhf[k]);
+        wx[1] = (T)w1;
+    }
+}
+
+// Descriptor of Gamma(s, t, u).  ex_slot (0 s, 1 t, 2 u; -1 none) names an argument known
+// to be the mesh frequency w[ex_idx] (or 0, clamped to w[0]), which needs no interval search.
+template <typename T>
+__device__ __forceinline__ void make_desc(double s, double t, double u, int ex_slot, int ex_idx, const Tabs& tb,
+                                          const Geo& g, Desc<T>& d) {
     int swap = 0;
     if (t < 0.0) t = -t;
     if (s < 0.0) { s = -s; swap ^= 1; }
     if (u < 0.0) { u = -u; swap ^= 1; }
-    double flip = 1.0;
-    if (s < u) { double tmp = s; s = u; u = tmp; flip = -1.0; }
+    bool flip = false;
+    if (s < u) { double tmp = s; s = u; u = tmp; flip = true; if (ex_slot != 1 && ex_slot >= 0) ex_slot = 2 - ex_slot; }
     int ix[3][2], nx[3];
-    double wx[3][2];
+    T wx[3][2];
     const double arg[3] = {s, t, u};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        int lo; double w0, w1;
-        bracket(w, invh, g.N, arg[a], lo, w0, w1);
-        if (w1 == 0.0) { nx[a] = 1; ix[a][0] = lo; wx[a][0] = w0; }
-        else if (w0 == 0.0) { nx[a] = 1; ix[a][0] = lo + 1; wx[a][0] = w1; }
-        else { nx[a] = 2; ix[a][0] = lo; wx[a][0] = w0; ix[a][1] = lo + 1; wx[a][1] = w1; }
+        if (a == ex_slot) { nx[a] = 1; ix[a][0] = ex_idx; wx[a][0] = (T)1; }
+        else axis_weights<T>(tb, g, arg[a], nx[a], ix[a], wx[a]);
     }
     const int row = g.nc * g.Ns;
     int k = 0;
     for (int a = 0; a < nx[0]; ++a)
         for (int b = 0; b < nx[1]; ++b)
             for (int c = 0; c < nx[2]; ++c) {
-                int si = ix[0][a], ti = ix[1][b], ui = ix[2][c];
-                double wt = wx[0][a] * wx[1][b] * wx[2][c];
-                double sg = flip;
+                const int si = ix[0][a], ti = ix[1][b], ui = ix[2][c];
+                const T wt = wx[0][a] * wx[1][b] * wx[2][c];
+                bool neg = flip;
                 int p;
                 if (si >= ui) p = pair_index(si, ui);
-                else { p = pair_index(ui, si); sg = -flip; }
+                else { p = pair_index(ui, si); neg = !neg; }
                 d.off[k] = (p * g.N + ti) * row;
-                d.wd[k] = (T)(wt * sg);
-                d.ws[k] = (T)wt;
+                d.wd[k] = neg ? -wt : wt;
+                d.ws[k] = wt;
                 ++k;
             }
     d.n = k;

@@ -233,3 +233,51 @@ def test_nonfinite_state_is_reported():
     with pytest.raises(sr.SrError) as e:
         fl.step(1.5, sr.SR_EULER)
     assert e.value.status == 5
+
+
+def _oracle_adaptive(of, lam0, lam1, rtol, atol, h0):
+    """Dormand-Prince 5(4) with the standard controller (h <- h clamp(0.9 err^-1/5, 0.2, 5)),
+    driven on the oracle's fixed step; returns the accepted cutoffs."""
+    lam, h, acc = lam0, h0, [lam0]
+    while lam > lam1:
+        if lam + h < lam1:
+            h = lam1 - lam
+        g0, G0 = of.get_state()
+        err = of.dp54(lam, lam + h, rtol, atol)
+        fac = 5.0 if err == 0 else 0.9 * err ** -0.2
+        if err <= 1.0:
+            lam = lam + h
+            acc.append(lam)
+            h *= min(5.0, max(0.2, fac))
+        else:
+            of.set_state(g0, G0)
+            h *= max(0.2, min(1.0, fac))
+    return acc
+
+
+def test_adaptive_rk_parity():
+    """Adaptive Dormand-Prince: (1) the GPU replays the oracle's accepted steps with fixed DP5
+    steps and matches to FP64 tolerance; (2) the GPU's own controller reaches the target and
+    agrees with the oracle's adaptive solution to the requested tolerance."""
+    model = W.square_j1j2(1.0, 0.5)
+    L, mesh = 1, O.mesh_exponential(6, 0.05, 10.0)
+    rtol, atol = 1e-6, 1e-10
+    of = O.OracleFlow(model, L, mesh)
+    acc = _oracle_adaptive(of, 8.0, 2.0, rtol, atol, -0.5)
+    assert len(acc) > 3
+    g_o, G_o = of.get_state()
+    lat, fl = _gpu_flow(model, L, mesh, 8.0)
+    for lam in acc[1:]:
+        fl.step(lam, sr.SR_RK_FIXED, rtol, atol)
+    g, G = fl.get_state()
+    assert _rel(g.cpu().numpy(), g_o) < 1e-9
+    _compare_gamma(G.cpu().numpy().reshape(fl.npair, fl.N, fl.n_comp, lat.N_s),
+                   oracle_to_gpu(of, lat, G_o, fl.n_comp), 1e-9)
+    lat2, fl2 = _gpu_flow(model, L, mesh, 8.0)
+    reached = fl2.step(2.0, sr.SR_RK_ADAPTIVE, rtol, atol)
+    assert reached == 2.0
+    st = fl2.stats()
+    assert st["n_accept"] >= 2 and st["n_rhs"] == 7 * (st["n_accept"] + st["n_reject"])
+    g2, G2 = fl2.get_state()
+    _compare_gamma(G2.cpu().numpy().reshape(fl2.npair, fl2.N, fl2.n_comp, lat2.N_s),
+                   oracle_to_gpu(of, lat2, G_o, fl2.n_comp), 1e-4)
