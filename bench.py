@@ -47,6 +47,7 @@ def _args():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-mixed side measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-flow", action="store_true", help="skip the full adaptive Lambda flow")
     return ap.parse_args()
 
 
@@ -278,6 +279,34 @@ def _measure_precision(sr, torch, cfg, lat, mesh, prec, steps, warmup, lams, flu
     return fl, ms, kms, kn, counts, (lam_start, lams[i]), i
 
 
+def _full_flow(sr, torch, cfg, lat, mesh, prec, kgrid, n_out=50):
+    """The whole flow of the workload: adaptive Dormand-Prince 5(4) (rtol 1e-6, atol 1e-10)
+    from Lambda = 100 to 0.01 with chi(k) on the k-grid at n_out log-spaced output cutoffs.
+    Timed with CUDA events on the flow's stream (the controller synchronises once per step)."""
+    fl = sr.Flow(lat, mesh, cfg.lam_max, prec)
+    grid = W.lambda_list(cfg.lam_max, cfg.lam_min, n_out)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    a.record(stream)
+    chimax = []
+    for lam in grid[1:]:
+        fl.step(float(lam), sr.SR_RK_ADAPTIVE, cfg.rtol, cfg.atol)
+        ck, _ = fl.measure(kgrid, want_ij=False)
+        chimax.append(float(ck.max()))
+    b.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    st = fl.stats()
+    ck, _ = fl.measure(kgrid, want_ij=False)
+    fl.close()
+    return {"seconds": a.elapsed_time(b) * 1e-3, "wall_seconds": wall, "rhs_evaluations": st["n_rhs"],
+            "accepted": st["n_accept"], "rejected": st["n_reject"], "chi_max_final": chimax[-1]}, \
+        np.array(chimax), ck
+
+
 def run_ours(args):
     import torch
     import paper_2109_13317_gb300 as sr
@@ -368,6 +397,15 @@ def run_ours(args):
         lam = lam * 0.95
     e2e_val = n_ent * ws / statistics.median(e2e_t)
     bytes_state = 8 * (fl.N + fl.n_gamma)
+
+    if not args.no_flow and prec == sr.SR_FP64:
+        f64, cm64, ck64 = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP64, kgrid)
+        f32, cm32, ck32 = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP32_MIXED, kgrid)
+        f32["chi_rel_err_vs_fp64_final"] = float(np.abs(ck32 - ck64).max() / np.abs(ck64).max())
+        f32["chi_max_rel_err_vs_fp64_all_outputs"] = float(np.abs(cm32 - cm64).max() / np.abs(cm64).max())
+        f32["speedup_vs_fp64"] = f64["seconds"] / f32["seconds"]
+        extra["full_flow"] = {"method": "adaptive Dormand-Prince 5(4), rtol 1e-6, atol 1e-10",
+                              "lambda": [cfg.lam_max, cfg.lam_min], "outputs": 50, "fp64": f64, "fp32_mixed": f32}
 
     clocks = sampler.summary() if sampler else None
     cpu = None

@@ -414,6 +414,236 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const do
     }
 }
 
+
+// ----------------------------------------------------------------------------- FP32 vertex flow
+
+constexpr int kQF = 32;   // integration nodes per shared-memory block (FP32 kernel)
+
+template <int NC, bool DENSE>
+struct ShF {
+    DescF* desc;
+    float* rows;
+    float* onrow;
+    float* wq;
+    float* acc;
+    float* cacc;
+};
+
+__host__ __device__ inline size_t rnd16(size_t b) { return (b + 15) & ~size_t(15); }
+
+__host__ __device__ inline size_t f32_smem_bytes(int Ns, int nsp, int nc, int nprod, bool dense) {
+    const size_t rowp = (size_t)nc * nsp;
+    return rnd16(sizeof(DescF) * kQF * 4) + rnd16(sizeof(float) * kQF * 2 * rowp) + rnd16(sizeof(float) * kQF * 2 * nc) +
+           rnd16(sizeof(float) * kQF) + rnd16(sizeof(float) * Ns * nc) +
+           rnd16(sizeof(float) * (dense ? (size_t)nc * nsp * nsp : (size_t)nprod));
+}
+
+// FP32-mixed vertex flow: the same equations as k_gamma_rhs with FP32 rows, products and
+// accumulation (descriptor decisions and node positions stay FP64).  Rows are interpolated
+// four padded sites at a time from the FP32 shadow (Gs: the same shadow with the exchanged
+// pair stored in place, for lookups whose arguments exchange the two sites).  With DENSE
+// (SU2), the lattice sum is the per-triple contraction C[c][rA][rB] = sum_q A_q B_q in 4x4
+// register tiles, gathered through the table at the end.
+template <int NC, bool DENSE>
+__global__ void __launch_bounds__(kThreads) k_gamma_rhs_f32(Geo g, Tabs tb, const float* __restrict__ Gf,
+                                                            const float* __restrict__ Gs, const double* __restrict__ nx,
+                                                            const float* __restrict__ nW, const int* __restrict__ ncount,
+                                                            double* __restrict__ dG) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nsp = g.nsp, nsp4 = nsp >> 2, rowp = NC * nsp;
+    ShF<NC, DENSE> sh;
+    {
+        size_t off = 0;
+        auto take = [&](size_t bytes) { unsigned char* q = smem + off; off += rnd16(bytes); return q; };
+        sh.desc = (DescF*)take(sizeof(DescF) * kQF * 4);
+        sh.rows = (float*)take(sizeof(float) * kQF * 2 * rowp);
+        sh.onrow = (float*)take(sizeof(float) * kQF * 2 * NC);
+        sh.wq = (float*)take(sizeof(float) * kQF);
+        sh.acc = (float*)take(sizeof(float) * g.Ns * NC);
+        sh.cacc = (float*)take(sizeof(float) * (DENSE ? NC * nsp * nsp : tb.nprod));
+    }
+    const int tid = threadIdx.x;
+    const int ti = blockIdx.x % g.N;
+    const int p = blockIdx.x / g.N;
+    int si = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
+    while ((si + 1) * (si + 2) / 2 <= p) ++si;
+    while (si * (si + 1) / 2 > p) --si;
+    const int ui = p - si * (si + 1) / 2;
+    const double* w = tb.w;
+    const double s = w[si], t = w[ti], u = w[ui];
+    const double w1p = (s + t + u) / 2, w2p = (s - t - u) / 2, w1 = (s - t + u) / 2, w2 = (s + t - u) / 2;
+    const int ncacc = DENSE ? NC * nsp * nsp : tb.nprod;
+    for (int o = tid; o < g.Ns * NC; o += blockDim.x) sh.acc[o] = 0.0f;
+    for (int o = tid; o < ncacc; o += blockDim.x) sh.cacc[o] = 0.0f;
+
+    for (int ch = 0; ch < 3; ++ch) {
+        const int vi = ch == 0 ? si : (ch == 1 ? ti : ui);
+        const int cidx = ch * g.N + vi;
+        const int nq = ncount[cidx];
+        const double* X = nx + (size_t)cidx * g.nmax;
+        const float* Wp = nW + (size_t)cidx * g.nmax;
+        const int nrow = ch == 1 ? 4 : 2;
+        for (int q0 = 0; q0 < nq; q0 += kQF) {
+            const int qn = min(kQF, nq - q0);
+            __syncthreads();
+            for (int idx = tid; idx < qn * nrow; idx += blockDim.x) {
+                const int q = idx / nrow, rw = idx % nrow;
+                const double x = X[q0 + q];
+                double a, b, c;
+                node_args(ch, rw, x, s, t, u, w1p, w2p, w1, w2, a, b, c);
+                const int exs = ch == 0 ? 0 : (ch == 2 ? 2 : (rw < 2 ? 1 : 2));
+                make_desc4(a, b, c, exs, vi, tb, g, rowp, sh.desc[q * 4 + rw]);
+                if (rw == 0) sh.wq[q] = Wp[q0 + q];
+            }
+            __syncthreads();
+            // rows: four padded sites per item; row 0 carries the node weight
+            const int nitems = qn * 2 * NC * nsp4;
+            for (int it = tid; it < nitems; it += blockDim.x) {
+                const int r4 = it % nsp4;
+                int t2 = it / nsp4;
+                const int c = t2 % NC;
+                t2 /= NC;
+                const int rw = t2 & 1, q = t2 >> 1;
+                const DescF& d = sh.desc[q * 4 + rw];
+                const float* base = (d.swap ? Gs : Gf) + c * nsp + 4 * r4;
+                const int4 ov = *reinterpret_cast<const int4*>(d.off);
+                const float4 wv = c == 0 ? *reinterpret_cast<const float4*>(d.wd) : *reinterpret_cast<const float4*>(d.ws);
+                const float4 g0 = __ldg(reinterpret_cast<const float4*>(base + ov.x));
+                const float4 g1 = __ldg(reinterpret_cast<const float4*>(base + ov.y));
+                const float4 g2 = __ldg(reinterpret_cast<const float4*>(base + ov.z));
+                const float4 g3 = __ldg(reinterpret_cast<const float4*>(base + ov.w));
+                float4 v;
+                v.x = wv.x * g0.x + wv.y * g1.x + wv.z * g2.x + wv.w * g3.x;
+                v.y = wv.x * g0.y + wv.y * g1.y + wv.z * g2.y + wv.w * g3.y;
+                v.z = wv.x * g0.z + wv.y * g1.z + wv.z * g2.z + wv.w * g3.z;
+                v.w = wv.x * g0.w + wv.y * g1.w + wv.z * g2.w + wv.w * g3.w;
+                if (rw == 0) {
+                    const float wq = sh.wq[q];
+                    v.x *= wq; v.y *= wq; v.z *= wq; v.w *= wq;
+                }
+                *reinterpret_cast<float4*>(sh.rows + (q * 2 + rw) * rowp + c * nsp + 4 * r4) = v;
+            }
+            if (ch == 1) {
+                for (int j = tid; j < qn * 2 * NC; j += blockDim.x) {
+                    const int qq = j / (2 * NC), rr = (j / NC) % 2, c = j % NC;
+                    const DescF& d = sh.desc[qq * 4 + 2 + rr];
+                    const float* base = Gf + c * nsp;   // the on-site pair is its own exchange
+                    const float* wgt = c == 0 ? d.wd : d.ws;
+                    float v = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) v += wgt[k] * base[d.off[k]];
+                    if (rr == 1) v *= sh.wq[qq];
+                    sh.onrow[(qq * 2 + rr) * NC + c] = v;
+                }
+            }
+            __syncthreads();
+            if (ch != 1) {
+                for (int r = tid; r < g.Ns; r += blockDim.x) {
+                    float o[NC], accl[NC], A[NC], B[NC];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) accl[c] = 0.0f;
+                    for (int q = 0; q < qn; ++q) {
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) {
+                            A[c] = sh.rows[(q * 2) * rowp + c * nsp + r];
+                            B[c] = sh.rows[(q * 2 + 1) * rowp + c * nsp + r];
+                        }
+                        if (ch == 0) s_product<float, NC>(A, B, o); else u_product<float, NC>(A, B, o);
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) accl[c] += o[c];
+                    }
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) sh.acc[r * NC + c] += accl[c];
+                }
+            } else {
+                if (DENSE) {
+                    const int ntile = NC * nsp4 * nsp4;
+                    for (int tl = tid; tl < ntile; tl += blockDim.x) {
+                        const int c = tl / (nsp4 * nsp4), ra = (tl / nsp4) % nsp4, rb = tl % nsp4;
+                        float a4[4][4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) a4[i][j] = 0.0f;
+                        for (int q = 0; q < qn; ++q) {
+                            const float4 av = *reinterpret_cast<const float4*>(sh.rows + (q * 2) * rowp + c * nsp + 4 * ra);
+                            const float4 bv = *reinterpret_cast<const float4*>(sh.rows + (q * 2 + 1) * rowp + c * nsp + 4 * rb);
+                            const float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) a4[i][j] += ar[i] * br[j];
+                        }
+                        float* cp = sh.cacc + c * nsp * nsp + (4 * ra) * nsp + 4 * rb;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            float4 cv = *reinterpret_cast<float4*>(cp + i * nsp);
+                            cv.x += a4[i][0]; cv.y += a4[i][1]; cv.z += a4[i][2]; cv.w += a4[i][3];
+                            *reinterpret_cast<float4*>(cp + i * nsp) = cv;
+                        }
+                    }
+                } else {
+                    for (int o = tid; o < tb.nprod; o += blockDim.x) {
+                        const int2 pr = tb.prodp[o];
+                        float a = 0.0f;
+                        for (int q = 0; q < qn; ++q) a += sh.rows[(q * 2) * rowp + pr.x] * sh.rows[(q * 2 + 1) * rowp + pr.y];
+                        sh.cacc[o] += a;
+                    }
+                }
+                for (int r = tid; r < g.Ns; r += blockDim.x) {
+                    const int pon = tb.onsite_perm[r];
+                    float accl[NC];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) accl[c] = 0.0f;
+                    for (int q = 0; q < qn; ++q) {
+                        float A[NC], B[NC], Cp[NC], D[NC];
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) {
+                            A[c] = sh.rows[(q * 2) * rowp + c * nsp + r];
+                            B[c] = sh.rows[(q * 2 + 1) * rowp + c * nsp + r];
+                            Cp[c] = sh.onrow[(q * 2) * NC + perm_of(pon, c)];
+                            D[c] = sh.onrow[(q * 2 + 1) * NC + c];
+                        }
+#pragma unroll
+                        for (int c = 0; c < NC; ++c)
+                            accl[c] += A[c] * onsite_factor<float, NC>(Cp, c) + onsite_factor<float, NC>(D, c) * B[c];
+                    }
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) sh.acc[r * NC + c] += accl[c];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int* gidx = DENSE ? tb.dgath_idx : tb.gath_idx;
+    for (int o = tid; o < g.Ns * NC; o += blockDim.x) {
+        const int r = o / NC, c = o % NC;
+        float a = 0.0f;
+        for (int k = tb.gath_off[o]; k < tb.gath_off[o + 1]; ++k) a += sh.cacc[gidx[k]];
+        dG[((size_t)(p * g.N + ti) * NC + c) * g.Ns + r] = (double)sh.acc[o] - 2.0 * (double)a;
+    }
+}
+
+// FP32 shadow of the state in the padded layout, and (with_swap) the exchanged copy in which
+// entry (c, r) holds the stored value of the pair (rep_r, ref): component perm(c) of site
+// swap_r[r].  Padding sites are zero.
+__global__ void k_shadow(Geo g, Tabs tb, const double* __restrict__ G, float* __restrict__ Gf, int with_swap) {
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= g.nentp) return;
+    const int rowp = g.nc * g.nsp;
+    const long pt = i / rowp;
+    const int rem = (int)(i % rowp);
+    const int c = rem / g.nsp, r = rem % g.nsp;
+    const double* src = G + pt * g.nc * g.Ns;
+    float v = 0.0f, vs = 0.0f;
+    if (r < g.Ns) {
+        v = (float)src[c * g.Ns + r];
+        if (with_swap) vs = (float)src[perm_of(tb.swap_perm[r], c) * g.Ns + tb.swap_r[r]];
+    }
+    Gf[i] = v;
+    if (with_swap) Gf[g.nentp + i] = vs;
+}
+
 __global__ void k_fill_init(Geo g, const double* __restrict__ init /* Ns * nc */, double* __restrict__ G) {
     long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i >= g.nent) return;
@@ -422,10 +652,6 @@ __global__ void k_fill_init(Geo g, const double* __restrict__ init /* Ns * nc */
     G[i] = init[r * g.nc + c];
 }
 
-__global__ void k_to_float(long n, const double* __restrict__ a, float* __restrict__ b) {
-    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (i < n) b[i] = (float)a[i];
-}
 
 // y <- y + a f, flagging non-finite results.
 __global__ void k_axpy(long n, double* __restrict__ y, const double* __restrict__ f, double a, int* __restrict__ flag) {
@@ -596,6 +822,9 @@ struct sr_flow {
     DevBuf<int2> prod;
     DevBuf<double> invh;
     DevBuf<float> wf, invhf;
+    DevBuf<int2> prodp;
+    DevBuf<int> dgath_idx;
+    bool has_swap = false, dense = false;
     int nprod = 0;
     DevBuf<double> init;
     DevBuf<int2> chi_map;
@@ -617,7 +846,7 @@ struct sr_flow {
         Tabs t;
         t.swap_r = swap_r.p; t.swap_perm = swap_perm.p; t.onsite_perm = onsite_perm.p; t.mult = mult.p;
         t.prod = prod.p; t.gath_off = gath_off.p; t.gath_idx = gath_idx.p; t.nprod = nprod; t.invh = invh.p;
-        t.w = w.p; t.wf = wf.p; t.invhf = invhf.p;
+        t.w = w.p; t.wf = wf.p; t.invhf = invhf.p; t.prodp = prodp.p; t.dgath_idx = dgath_idx.p;
         return t;
     }
 };
@@ -670,10 +899,13 @@ static sr_status run_rhs(sr_flow* f, double lam, const double* gam_s, const doub
         else
             k_gamma_rhs<double, 4><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, f->w.p, G_s, f->nx.p, f->nW.p, f->ncount.p, dG_o);
     } else {
-        if (g.nc == 2)
-            k_gamma_rhs<float, 2><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, f->w.p, Gf_s, f->nx.p, f->nWf.p, f->ncount.p, dG_o);
+        const float* Gs = f->has_swap ? Gf_s + g.nentp : Gf_s;
+        if (g.nc == 2 && f->dense)
+            k_gamma_rhs_f32<2, true><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, Gf_s, Gs, f->nx.p, f->nWf.p, f->ncount.p, dG_o);
+        else if (g.nc == 2)
+            k_gamma_rhs_f32<2, false><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, Gf_s, Gs, f->nx.p, f->nWf.p, f->ncount.p, dG_o);
         else
-            k_gamma_rhs<float, 4><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, f->w.p, Gf_s, f->nx.p, f->nWf.p, f->ncount.p, dG_o);
+            k_gamma_rhs_f32<4, false><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, Gf_s, Gs, f->nx.p, f->nWf.p, f->ncount.p, dG_o);
     }
     if (sr_status s = prof_end(f, 2, e0)) return s;
     CK(cudaGetLastError());
@@ -683,8 +915,8 @@ static sr_status run_rhs(sr_flow* f, double lam, const double* gam_s, const doub
 
 static sr_status refresh_shadow(sr_flow* f, const double* G_s, float* Gf_s) {
     if (f->prec != SR_FP32_MIXED) return SR_OK;
-    long n = f->g.nent;
-    k_to_float<<<(unsigned)((n + 255) / 256), 256, 0, f->stream>>>(n, G_s, Gf_s);
+    long n = f->g.nentp;
+    k_shadow<<<(unsigned)((n + 255) / 256), 256, 0, f->stream>>>(f->g, f->tabs(), G_s, Gf_s, f->has_swap ? 1 : 0);
     CK(cudaGetLastError());
     return SR_OK;
 }
@@ -782,6 +1014,8 @@ extern "C" sr_status sr_flow_init(const sr_lattice* lat, int n_freq, const doubl
     g.npair = n_freq * (n_freq + 1) / 2;
     g.nmax = 2 * n_freq + 8;
     g.nent = (long)g.npair * n_freq * g.nc * g.Ns;
+    g.nsp = (g.Ns + 3) & ~3;
+    g.nentp = (long)g.npair * n_freq * g.nc * g.nsp;
     if ((long)g.npair * n_freq * g.nc * g.Ns >= (1L << 31)) return fail(SR_EINVAL, "vertex too large for 32-bit offsets");
 
     // lattice tables
@@ -810,6 +1044,30 @@ extern "C" sr_status sr_flow_init(const sr_lattice* lat, int n_freq, const doubl
         goff[lat->Ns * lat->nc] = (int)gidx.size();
     }
     f->nprod = (int)prods.size();
+    // padded-layout products, site-exchange map, dense (SU2) gather indices
+    {
+        const int nsp = g.nsp;
+        std::vector<int2> pp(prods.size());
+        for (size_t k = 0; k < prods.size(); ++k) {
+            const int ra = prods[k].x / lat->nc, ca = prods[k].x % lat->nc;
+            const int rb = prods[k].y / lat->nc, cb = prods[k].y % lat->nc;
+            pp[k] = make_int2(ca * nsp + ra, cb * nsp + rb);
+        }
+        CK(f->prodp.upload(pp.data(), pp.size(), f->stream));
+        f->has_swap = false;
+        for (int r = 0; r < lat->Ns; ++r) {
+            if (lat->swap_r[r] != r) f->has_swap = true;
+            for (int c = 0; c < lat->nc; ++c) if (lat->swap_perm[r][c] != c) f->has_swap = true;
+        }
+        f->dense = lat->nc == 2;
+        std::vector<int> dg(gidx.size());
+        for (size_t k = 0; k < gidx.size(); ++k) {
+            const int ra = prods[gidx[k]].x / lat->nc, ca = prods[gidx[k]].x % lat->nc;
+            const int rb = prods[gidx[k]].y / lat->nc;
+            dg[k] = ca * nsp * nsp + ra * nsp + rb;
+        }
+        CK(f->dgath_idx.upload(dg.data(), dg.size(), f->stream));
+    }
     std::vector<double> ih(n_freq - 1);
     for (int i = 0; i + 1 < n_freq; ++i) ih[i] = 1.0 / (freq_pos[i + 1] - freq_pos[i]);
     cudaStream_t st = f->stream;
@@ -845,7 +1103,7 @@ extern "C" sr_status sr_flow_init(const sr_lattice* lat, int n_freq, const doubl
     CK(f->G.alloc(g.nent));
     CK(f->dgam.alloc(g.N));
     CK(f->dG.alloc(g.nent));
-    if (precision == SR_FP32_MIXED) CK(f->Gf.alloc(g.nent));
+    if (precision == SR_FP32_MIXED) CK(f->Gf.alloc((size_t)g.nentp * (f->has_swap ? 2 : 1)));
     CK(f->nx.alloc((size_t)3 * g.N * g.nmax));
     CK(f->nW.alloc((size_t)3 * g.N * g.nmax));
     CK(f->nWf.alloc((size_t)3 * g.N * g.nmax));
@@ -856,14 +1114,16 @@ extern "C" sr_status sr_flow_init(const sr_lattice* lat, int n_freq, const doubl
     k_fill_init<<<(unsigned)((g.nent + 255) / 256), 256, 0, st>>>(g, f->init.p, f->G.p);
     CK(cudaGetLastError());
     if (sr_status s2 = refresh_shadow(f.get(), f->G.p, f->Gf.p)) return s2;
-    f->smem_rhs = rhs_smem_bytes(g, f->nprod, precision == SR_FP32_MIXED);
+    f->smem_rhs = precision == SR_FP32_MIXED ? f32_smem_bytes(g.Ns, g.nsp, g.nc, f->nprod, f->dense)
+                                             : rhs_smem_bytes(g, f->nprod, false);
     if (f->smem_rhs > 227 * 1024) return fail(SR_EUNSUPPORTED, "lattice too large for one CTA's shared memory (%zu bytes)", f->smem_rhs);
     if (precision == SR_FP64) {
         CK(cudaFuncSetAttribute(k_gamma_rhs<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->smem_rhs));
         CK(cudaFuncSetAttribute(k_gamma_rhs<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->smem_rhs));
     } else {
-        CK(cudaFuncSetAttribute(k_gamma_rhs<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->smem_rhs));
-        CK(cudaFuncSetAttribute(k_gamma_rhs<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->smem_rhs));
+        CK(cudaFuncSetAttribute(k_gamma_rhs_f32<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->smem_rhs));
+        CK(cudaFuncSetAttribute(k_gamma_rhs_f32<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->smem_rhs));
+        CK(cudaFuncSetAttribute(k_gamma_rhs_f32<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->smem_rhs));
     }
     CK(cudaStreamSynchronize(st));
     *out = f.release();

@@ -23,6 +23,8 @@ struct Geo {
     int npair;    // N (N + 1) / 2
     int nmax;     // node capacity per (channel, transfer frequency): 2N + 8
     long nent;    // Gamma entries
+    int nsp;          // sites padded to a multiple of 4 (FP32 shadow layout)
+    long nentp;       // entries of the padded FP32 shadow
     float log2w0;     // log2(w[0])
     float inv_dlog2;  // (N - 1) / log2(w[N-1] / w[0]): interval guess for a log-spaced mesh
 };
@@ -41,6 +43,8 @@ struct Tabs {
     const double* w;         // N: mesh
     const float* wf;         // N: mesh (FP32)
     const float* invhf;      // N - 1: 1 / (w[a+1] - w[a]) (FP32)
+    const int2* prodp;       // nprod: lattice-sum products in the padded layout (c * nsp + r)
+    const int* dgath_idx;    // P * nc: dense-contraction index c * nsp^2 + rA * nsp + rB (SU2)
 };
 
 __device__ __forceinline__ int perm_of(int packed, int c) { return (packed >> (2 * c)) & 3; }
@@ -169,6 +173,59 @@ __device__ __forceinline__ void make_desc(double s, double t, double u, int ex_s
                 ++k;
             }
     d.n = k;
+    d.swap = swap;
+}
+
+// Four-corner descriptor of the FP32 kernel (every row there has one argument on the mesh,
+// so at most four corners carry weight; unused corners have weight zero and offset zero).
+struct __align__(16) DescF {
+    int off[4];
+    float wd[4];
+    float ws[4];
+    int swap;
+    int pad[3];
+};
+
+__device__ __forceinline__ void make_desc4(double s, double t, double u, int ex_slot, int ex_idx, const Tabs& tb,
+                                           const Geo& g, int rowp, DescF& d) {
+    int swap = 0;
+    if (t < 0.0) t = -t;
+    if (s < 0.0) { s = -s; swap ^= 1; }
+    if (u < 0.0) { u = -u; swap ^= 1; }
+    bool flip = false;
+    if (s < u) { double tmp = s; s = u; u = tmp; flip = true; if (ex_slot != 1) ex_slot = 2 - ex_slot; }
+    int ix[3][2], nx[3];
+    float wx[3][2];
+    const double arg[3] = {s, t, u};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a == ex_slot) { nx[a] = 1; ix[a][0] = ex_idx; wx[a][0] = 1.0f; ix[a][1] = ex_idx; wx[a][1] = 0.0f; }
+        else {
+            axis_weights<float>(tb, g, arg[a], nx[a], ix[a], wx[a]);
+            if (nx[a] == 1) { ix[a][1] = ix[a][0]; wx[a][1] = 0.0f; }
+        }
+    }
+    // four corners over the two non-exact axes (zero-weight corners kept, pointing at offset 0)
+    const int ea = ex_slot;  // the exact axis contributes index ix[ea][0] with weight 1
+    const int a0 = ea == 0 ? 1 : 0, a1 = ea == 2 ? 1 : 2;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        int id[3];
+        float wt = 1.0f;
+        id[ea] = ix[ea][0];
+        const int b0 = k & 1, b1 = k >> 1;
+        id[a0] = ix[a0][b0];
+        id[a1] = ix[a1][b1];
+        wt = wx[a0][b0] * wx[a1][b1];
+        bool neg = flip;
+        int p;
+        if (id[0] >= id[2]) p = pair_index(id[0], id[2]);
+        else { p = pair_index(id[2], id[0]); neg = !neg; }
+        const bool live = wt != 0.0f;
+        d.off[k] = live ? (p * g.N + id[1]) * rowp : 0;
+        d.wd[k] = neg ? -wt : wt;
+        d.ws[k] = wt;
+    }
     d.swap = swap;
 }
 

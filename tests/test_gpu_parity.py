@@ -172,9 +172,12 @@ def test_rk_fixed_step_parity():
     assert abs(err - err_o) <= 1e-6 * err_o
 
 
-def test_fp32_mixed_within_tolerance():
-    model = W.square_j1j2(1.0, 0.5)
-    L, mesh = 2, O.mesh_exponential(8, 0.02, 20.0)
+@pytest.mark.parametrize("name,mk,L,N,wmin,wmax", CASES)
+def test_fp32_mixed_within_tolerance(name, mk, L, N, wmin, wmax):
+    """FP32-mixed right-hand side (FP32 rows, products and accumulation; FP64 self-energy,
+    propagators and node positions) against the FP64 oracle: 1e-3 on Gamma."""
+    model = mk()
+    mesh = O.mesh_exponential(N, wmin, wmax)
     of = evolved_oracle(model, L, mesh, [8.0, 4.0, 2.0, 1.0])
     lat, fl = _gpu_flow(model, L, mesh, 1.0, sr.SR_FP32_MIXED)
     _load_oracle_state(fl, lat, of, 1.0)
