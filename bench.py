@@ -48,6 +48,7 @@ def _args():
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-mixed side measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-flow", action="store_true", help="skip the full adaptive Lambda flow")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched coupling sweep")
     return ap.parse_args()
 
 
@@ -279,12 +280,16 @@ def _measure_precision(sr, torch, cfg, lat, mesh, prec, steps, warmup, lams, flu
     return fl, ms, kms, kn, counts, (lam_start, lams[i]), i
 
 
-def _full_flow(sr, torch, cfg, lat, mesh, prec, kgrid, n_out=50):
-    """The whole flow of the workload: adaptive Dormand-Prince 5(4) (rtol 1e-6, atol 1e-10)
-    from Lambda = 100 to 0.01 with chi(k) on the k-grid at n_out log-spaced output cutoffs.
-    Timed with CUDA events on the flow's stream (the controller synchronises once per step)."""
+def _full_flow(sr, torch, cfg, lat, mesh, prec, kgrid, method="euler", n_steps=200, n_out=50, budget_s=40.0):
+    """The whole flow of the workload from Lambda = 100 to 0.01 with chi(k) on the k-grid at
+    n_out log-spaced output cutoffs: Euler on n_steps log steps (the paper's scheme), or
+    adaptive Dormand-Prince 5(4) (rtol 1e-6, atol 1e-10) stopped after budget_s seconds.
+    Timed with CUDA events on the flow's stream."""
     fl = sr.Flow(lat, mesh, cfg.lam_max, prec)
-    grid = W.lambda_list(cfg.lam_max, cfg.lam_min, n_out)
+    out_grid = W.lambda_list(cfg.lam_max, cfg.lam_min, n_out)
+    if method == "euler":
+        lams = W.lambda_list(cfg.lam_max, cfg.lam_min, n_steps)
+        per_out = n_steps // n_out
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
     a = torch.cuda.Event(enable_timing=True)
@@ -292,19 +297,88 @@ def _full_flow(sr, torch, cfg, lat, mesh, prec, kgrid, n_out=50):
     t0 = time.perf_counter()
     a.record(stream)
     chimax = []
-    for lam in grid[1:]:
-        fl.step(float(lam), sr.SR_RK_ADAPTIVE, cfg.rtol, cfg.atol)
+    reached = cfg.lam_max
+    complete = True
+    for k, lam in enumerate(out_grid[1:]):
+        if method == "euler":
+            for j in range(k * per_out, (k + 1) * per_out):
+                fl.step(float(lams[j + 1]), sr.SR_EULER)
+            reached = float(lams[(k + 1) * per_out])
+        else:
+            fl.set_step_limit(50)
+            try:
+                reached = fl.step(float(lam), sr.SR_RK_ADAPTIVE, cfg.rtol, cfg.atol)
+            except sr.SrError as e:
+                if e.status != 6:
+                    raise
+                reached = fl.lam
+                complete = False
         ck, _ = fl.measure(kgrid, want_ij=False)
         chimax.append(float(ck.max()))
+        if not complete or time.perf_counter() - t0 > budget_s:
+            complete = complete and reached <= cfg.lam_min * (1 + 1e-12)
+            break
     b.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     st = fl.stats()
     ck, _ = fl.measure(kgrid, want_ij=False)
     fl.close()
-    return {"seconds": a.elapsed_time(b) * 1e-3, "wall_seconds": wall, "rhs_evaluations": st["n_rhs"],
-            "accepted": st["n_accept"], "rejected": st["n_reject"], "chi_max_final": chimax[-1]}, \
-        np.array(chimax), ck
+    res = {"method": "Euler, %d log steps" % n_steps if method == "euler" else
+           "adaptive Dormand-Prince 5(4), rtol %g, atol %g, normwise error" % (cfg.rtol, cfg.atol),
+           "seconds": a.elapsed_time(b) * 1e-3, "wall_seconds": wall, "rhs_evaluations": st["n_rhs"],
+           "accepted": st["n_accept"], "rejected": st["n_reject"], "lambda_reached": reached,
+           "complete": bool(complete), "chi_max_final": chimax[-1]}
+    return res, np.array(chimax), ck
+
+
+def _batched_sweep(sr, torch, steps=20):
+    """The batched coupling sweep: 64 seeded instances (square J1-J2 with J2/J1 ~ U[0,1] and
+    range 5..9, kagome J1 with range 4..8, 32..64 frequencies), FP32-mixed, Euler steps on a
+    common log cutoff list 50 -> 0.05 (100 steps).  The flows are advanced untimed to mid-flow
+    by the batch itself, then `steps` Euler steps are timed (a) batched: one persistent vertex
+    launch per step for all instances, CUDA-graph-captured loop, autotuned launch shape, and
+    (b) one flow after another with sr_flow_step, from the same saved states."""
+    insts = W.batched_instances(0)
+    lams = W.lambda_list(50.0, 0.05, 100)
+    flows = []
+    for c in insts:
+        lat = sr.Lattice.from_model(c.model, c.L)
+        mesh = sr.sr_frequency_mesh_exponential(c.n_freq, c.w_min, c.w_max)
+        flows.append(sr.Flow(lat, mesh, lams[0], sr.SR_FP32_MIXED))
+    n_ent = sum(f.n_gamma for f in flows)
+    b = sr.Batch(flows)
+    mid = 50
+    b.run(lams[:mid + 1], use_graph=True, autotune=False)
+    saved = [f.get_state() for f in flows]
+    window = lams[mid:mid + steps + 1]
+    b.run(window, use_graph=True, autotune=True)
+    info = b.info()
+    classes = b.classes()
+    batched_ms = info["run_ms"]
+    after_b = [f.get_state()[1] for f in flows]
+    for f, (g, G) in zip(flows, saved):
+        f.set_state(float(window[0]), g, G)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for f in flows:
+        for lam in window[1:]:
+            f.step(float(lam), sr.SR_EULER)
+    e.record()
+    torch.cuda.synchronize()
+    seq_ms = a.elapsed_time(e)
+    diff = max(float((f.get_state()[1] - Gb).abs().max() / Gb.abs().max()) for f, Gb in zip(flows, after_b))
+    b.close()
+    for f in flows:
+        f.close()
+    return {"workload": "64 seeded instances (48 square J1-J2, 16 kagome), FP32-mixed, Euler",
+            "entries": n_ent, "steps_timed": steps, "lambda_window": [float(window[0]), float(window[-1])],
+            "batched_ms_per_step": batched_ms / steps, "batched_entries_per_s": n_ent * steps / (batched_ms * 1e-3),
+            "sequential_ms_per_step": seq_ms / steps, "sequential_entries_per_s": n_ent * steps / (seq_ms * 1e-3),
+            "speedup": seq_ms / batched_ms, "size_classes": classes,
+            "max_rel_diff_batched_vs_sequential": diff}
 
 
 def run_ours(args):
@@ -399,13 +473,20 @@ def run_ours(args):
     bytes_state = 8 * (fl.N + fl.n_gamma)
 
     if not args.no_flow and prec == sr.SR_FP64:
-        f64, cm64, ck64 = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP64, kgrid)
-        f32, cm32, ck32 = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP32_MIXED, kgrid)
-        f32["chi_rel_err_vs_fp64_final"] = float(np.abs(ck32 - ck64).max() / np.abs(ck64).max())
-        f32["chi_max_rel_err_vs_fp64_all_outputs"] = float(np.abs(cm32 - cm64).max() / np.abs(cm64).max())
-        f32["speedup_vs_fp64"] = f64["seconds"] / f32["seconds"]
-        extra["full_flow"] = {"method": "adaptive Dormand-Prince 5(4), rtol 1e-6, atol 1e-10",
-                              "lambda": [cfg.lam_max, cfg.lam_min], "outputs": 50, "fp64": f64, "fp32_mixed": f32}
+        ff = {"lambda": [cfg.lam_max, cfg.lam_min], "outputs": 50}
+        e64, cm64, ck64 = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP64, kgrid, "euler")
+        e32, cm32, ck32 = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP32_MIXED, kgrid, "euler")
+        e32["chi_rel_err_vs_fp64_final"] = float(np.abs(ck32 - ck64).max() / np.abs(ck64).max())
+        e32["chi_max_rel_err_vs_fp64_all_outputs"] = float(np.abs(cm32 - cm64).max() / np.abs(cm64).max())
+        e32["speedup_vs_fp64"] = e64["seconds"] / e32["seconds"]
+        ff["euler"] = {"fp64": e64, "fp32_mixed": e32}
+        a64, _, _ = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP64, kgrid, "rk", budget_s=30.0)
+        a32, _, _ = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP32_MIXED, kgrid, "rk", budget_s=30.0)
+        ff["adaptive"] = {"fp64": a64, "fp32_mixed": a32}
+        extra["full_flow"] = ff
+
+    if not args.no_batch and rank == 0:
+        extra["batched_sweep"] = _batched_sweep(sr, torch)
 
     clocks = sampler.summary() if sampler else None
     cpu = None

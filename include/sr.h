@@ -133,7 +133,13 @@ sr_status sr_flow_rhs(sr_flow* flow, double lambda, double* d_dsigma, double* d_
 sr_status sr_flow_step(sr_flow* flow, double lambda_next, int method, double rtol, double atol,
                        double* lambda_reached);
 
-/* Error norm of the last Dormand-Prince step (max_i |e_i| / (atol + rtol max(|y_i|, |y'_i|)))
+/* Largest number of attempted steps one SR_RK_ADAPTIVE call may take (default 10^6); when it
+ * is exceeded the call returns SR_ETIMEOUT with the state and *lambda_reached at the last
+ * accepted step. */
+sr_status sr_flow_set_step_limit(sr_flow* flow, long max_steps);
+
+/* Error norm of the last Dormand-Prince step, normwise:
+ * max_i |e_i| / (atol + rtol max_i max(|y_i|, |y'_i|)),
  * and the counts of right-hand-side evaluations, accepted and rejected steps. */
 sr_status sr_flow_stats(const sr_flow* flow, double* last_err, long* n_rhs, long* n_accept, long* n_reject);
 
@@ -175,6 +181,56 @@ sr_status sr_flow_set_state(sr_flow* flow, double lambda, const double* d_sigma,
 sr_status sr_flow_lambda(const sr_flow* flow, double* lambda);
 
 sr_status sr_flow_destroy(sr_flow* flow);
+
+/* ---- tangent-linear flow: derivatives of the flow along coupling directions ---- */
+
+/* Like sr_flow_init (FP64), but the state carries, with every value, its derivatives along
+ * n_par <= 2 directions of the couplings: dM (host) holds n_par x n_couplings row-major
+ * 3x3 matrices dM_c/dtheta_p in the order the couplings were given to sr_lattice_create.
+ * The initial tangent is dJ/4 (Eq. frg:parametrizationInitial); every kernel then applies
+ * the chain rule exactly (forward-mode dual numbers), so sr_flow_step (SR_EULER only)
+ * integrates the tangent-linear flow beside the flow.  get/set_state and sr_flow_rhs see
+ * interleaved (value, d/dtheta_1, d/dtheta_2) triples.  Errors: SR_ESYMMETRY if a direction
+ * is not invariant under the symmetries used to reduce the lattice (it could not be stored),
+ * SR_EUNSUPPORTED if it has couplings the core cannot represent. */
+sr_status sr_flow_init_tangent(const sr_lattice* lat, int n_freq, const double* freq_pos, double lambda_init,
+                               int n_par, const double* dM, void* cuda_stream, sr_flow** out);
+sr_status sr_flow_tangents(const sr_flow* flow, int* n_tangent);
+
+/* chi(k) and its derivatives d chi(k) / d theta_p of a tangent flow (host outputs: chi_k n_k,
+ * dchi_k n_k x 2, p fastest).  Synchronises. */
+sr_status sr_measure_susceptibility_tangent(sr_flow* flow, int n_k, const double* k_xyz, double* chi_k, double* dchi_k);
+
+/* ---- batched flows (many couplings / lattices of uneven size in one launch per stage) ---- */
+
+typedef struct sr_batch sr_batch;
+
+/* Group flows (all SR_FP32_MIXED, on the current device; the batch keeps pointers to them,
+ * so they must outlive it).  The vertex flow of every instance runs in one persistent kernel
+ * whose CTAs take (instance, stored triple) units from an atomic counter, largest instances
+ * first; the paper's analogue is its dynamically balanced work units (Sec. 4.4). */
+sr_status sr_batch_create(int n, sr_flow* const* flows, sr_batch** out);
+
+/* Integrate every flow with Euler steps (Sec. 4.3) through the common cutoff list
+ * lambdas[0] > ... > lambdas[n_lambda-1] (host); every flow must be at lambdas[0].  With
+ * use_graph != 0 one step is captured as a CUDA graph (the cutoff is read on the device from
+ * the list) and replayed n_lambda - 1 times.  With autotune != 0 the node-block size and the
+ * CTAs per SM of the persistent kernel are first chosen by timing every candidate on the
+ * first step.  Synchronises; SR_ENONFINITE if any flow produced NaN / Inf. */
+sr_status sr_batch_run(sr_batch* batch, int n_lambda, const double* lambdas, int use_graph, int autotune);
+
+/* Chosen configuration (node-block size, CTAs per SM), its timed vertex-flow time (ms), the
+ * device time of the last sr_batch_run (ms) and the number of work units per step. */
+sr_status sr_batch_info(const sr_batch* batch, int* qc, int* ctas_per_sm, double* tune_ms, double* run_ms, long* units);
+
+/* Size classes of the batch: instances are grouped by the shared memory their vertex flow
+ * needs, and each class has its own persistent launch (CTAs per SM and node-block size
+ * chosen by the autotuner).  sr_batch_class reports one class. */
+sr_status sr_batch_classes(const sr_batch* batch, int* n_classes);
+sr_status sr_batch_class(const sr_batch* batch, int k, int* n_instances, long* units, int* smem_bytes, int* qc,
+                         int* ctas_per_sm, double* tune_ms);
+
+sr_status sr_batch_destroy(sr_batch* batch);
 
 /* ---- measurement helpers (not part of the method) ---- */
 

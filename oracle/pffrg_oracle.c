@@ -788,7 +788,7 @@ void or_dp54_tableau(double* c, double* a, double* b5, double* b4) {
 
 /* Dormand-Prince 5(4) (Dormand & Prince 1980) step of size h = lam_next - lam (negative when
  * integrating toward small cutoff).  The state advances with the fifth-order solution; the
- * return value is the error norm max_i |e_i| / (atol + rtol max(|y_i|, |y_new_i|)). */
+ * return value is the normwise scaled error max_i |e_i| / (atol + rtol max_i max(|y_i|, |y_new_i|)). */
 double or_dp54_step(OrState* st, double lam, double lam_next, double rtol, double atol) {
     const double h = lam_next - lam;
     const int N = st->N;
@@ -812,23 +812,25 @@ double or_dp54_step(OrState* st, double lam, double lam_next, double rtol, doubl
         }
         or_rhs(st, lam + DP_C[s] * h, kg[s], kG[s]);
     }
-    double err = 0.0;
+    /* normwise scaled error: max_i |h (y5_i - y4_i)| / (atol + rtol max_i max(|y0_i|, |y5_i|)) */
+    double emax = 0.0, ymax = 0.0;
     for (int i = 0; i < N; ++i) {
         double y5 = 0.0, y4 = 0.0;
         for (int r = 0; r < 7; ++r) { y5 += DP_B5[r] * kg[r][i]; y4 += DP_B4[r] * kg[r][i]; }
         double yn = y0g[i] + h * y5;
-        double e = fabs(h * (y5 - y4)) / (atol + rtol * fmax(fabs(y0g[i]), fabs(yn)));
-        if (e > err) err = e;
+        emax = fmax(emax, fabs(h * (y5 - y4)));
+        ymax = fmax(ymax, fmax(fabs(y0g[i]), fabs(yn)));
         st->gam[i] = yn;
     }
     for (size_t i = 0; i < M; ++i) {
         double y5 = 0.0, y4 = 0.0;
         for (int r = 0; r < 7; ++r) { y5 += DP_B5[r] * kG[r][i]; y4 += DP_B4[r] * kG[r][i]; }
         double yn = y0G[i] + h * y5;
-        double e = fabs(h * (y5 - y4)) / (atol + rtol * fmax(fabs(y0G[i]), fabs(yn)));
-        if (e > err) err = e;
+        emax = fmax(emax, fabs(h * (y5 - y4)));
+        ymax = fmax(ymax, fmax(fabs(y0G[i]), fabs(yn)));
         st->G[i] = yn;
     }
+    double err = emax / (atol + rtol * ymax);
     for (int i = 0; i < 7; ++i) { free(kg[i]); free(kG[i]); }
     free(y0g); free(y0G);
     return err;

@@ -72,10 +72,14 @@ def load_library():
             "sr_lattice_destroy": [vp],
             "sr_frequency_mesh_exponential": [i, d, d, dp],
             "sr_flow_init": [vp, i, dp, d, i, vp, C.POINTER(vp)],
+            "sr_flow_init_tangent": [vp, i, dp, d, i, dp, vp, C.POINTER(vp)],
+            "sr_flow_tangents": [vp, ip],
+            "sr_measure_susceptibility_tangent": [vp, i, dp, dp, dp],
             "sr_flow_sizes": [vp, lp, ip, ip],
             "sr_flow_rhs": [vp, d, vp, vp],
             "sr_flow_step": [vp, d, i, d, d, dp],
             "sr_flow_stats": [vp, dp, lp, lp, lp],
+            "sr_flow_set_step_limit": [vp, l],
             "sr_measure_susceptibility": [vp, i, dp, dp, vp],
             "sr_flow_chi_sites": [vp, ip],
             "sr_measure_susceptibility_static": [vp, i, vp, vp],
@@ -88,6 +92,12 @@ def load_library():
             "sr_flow_node_counts": [vp, ip],
             "sr_flow_lattice_sum_products": [vp, lp],
             "sr_peak_fma": [i, dp],
+            "sr_batch_create": [i, C.POINTER(vp), C.POINTER(vp)],
+            "sr_batch_run": [vp, i, dp, i, i],
+            "sr_batch_info": [vp, ip, ip, dp, dp, lp],
+            "sr_batch_destroy": [vp],
+            "sr_batch_classes": [vp, ip],
+            "sr_batch_class": [vp, i, ip, lp, ip, ip, ip, dp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -204,7 +214,10 @@ def _ptr(t):
 class Flow:
     """sr_flow_init: a flow on the current CUDA device and PyTorch stream."""
 
-    def __init__(self, lattice: Lattice, mesh, lambda_init: float, precision: int = SR_FP64, stream=None):
+    def __init__(self, lattice: Lattice, mesh, lambda_init: float, precision: int = SR_FP64, stream=None,
+                 tangents=None):
+        """tangents: optional (n_par, n_couplings, 3, 3) derivatives of the coupling matrices
+        (sr_flow_init_tangent): the flow then carries d/dtheta_p of every value."""
         import torch
         lib = load_library()
         self._lib = lib
@@ -214,8 +227,16 @@ class Flow:
             stream = torch.cuda.current_stream()
         self.stream = stream
         h = C.c_void_p()
-        _check(lib.sr_flow_init(lattice.h, len(self.mesh), _dptr(self.mesh), float(lambda_init), int(precision),
-                                C.c_void_p(stream.cuda_stream), C.byref(h)))
+        if tangents is None:
+            _check(lib.sr_flow_init(lattice.h, len(self.mesh), _dptr(self.mesh), float(lambda_init), int(precision),
+                                    C.c_void_p(stream.cuda_stream), C.byref(h)))
+            self.n_tan = 0
+        else:
+            dM = np.ascontiguousarray(tangents, dtype=np.float64)
+            npar = dM.shape[0]
+            _check(lib.sr_flow_init_tangent(lattice.h, len(self.mesh), _dptr(self.mesh), float(lambda_init), npar,
+                                            _dptr(dM.reshape(-1)), C.c_void_p(stream.cuda_stream), C.byref(h)))
+            self.n_tan = npar
         self.h = h
         ng, nf, nc = C.c_long(), C.c_int(), C.c_int()
         _check(lib.sr_flow_sizes(h, C.byref(ng), C.byref(nf), C.byref(nc)))
@@ -240,6 +261,9 @@ class Flow:
         reached = C.c_double()
         _check(self._lib.sr_flow_step(self.h, float(lam_next), int(method), float(rtol), float(atol), C.byref(reached)))
         return reached.value
+
+    def set_step_limit(self, n: int):
+        _check(self._lib.sr_flow_set_step_limit(self.h, int(n)))
 
     def stats(self):
         e, n, a, r = C.c_double(), C.c_long(), C.c_long(), C.c_long()
@@ -276,6 +300,15 @@ class Flow:
             raise ValueError("k_dev must hold 3 values per output")
         _check(self._lib.sr_measure_susceptibility_static(self.h, int(n), _ptr(k_dev), _ptr(out_dev)))
         return out_dev
+
+    def measure_tangent(self, kpts):
+        """(chi(k), d chi(k) / d theta) of a tangent flow: arrays (n_k,), (n_k, n_par)."""
+        kp = np.ascontiguousarray(kpts, dtype=np.float64).reshape(-1, 3)
+        nk = kp.shape[0]
+        chik = np.zeros(nk)
+        d = np.zeros(nk * 2)
+        _check(self._lib.sr_measure_susceptibility_tangent(self.h, nk, _dptr(kp), _dptr(chik), _dptr(d)))
+        return chik, d.reshape(nk, 2)[:, :self.n_tan]
 
     def chi_sites(self) -> np.ndarray:
         out = np.zeros((self.lattice.N_basis * self.lattice.N_tot, 4), dtype=np.int32)
@@ -315,6 +348,52 @@ class Flow:
     def close(self):
         if getattr(self, "h", None):
             self._lib.sr_flow_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """sr_batch_create / sr_batch_run: FP32-mixed flows integrated together (persistent vertex
+    kernel over all instances, CUDA-graph-captured Euler loop, autotuned launch shape)."""
+
+    def __init__(self, flows):
+        lib = load_library()
+        self._lib = lib
+        self.flows = list(flows)
+        arr = (C.c_void_p * len(self.flows))(*[f.h.value for f in self.flows])
+        h = C.c_void_p()
+        _check(lib.sr_batch_create(len(self.flows), arr, C.byref(h)))
+        self.h = h
+
+    def run(self, lambdas, use_graph: bool = True, autotune: bool = True):
+        lams = np.ascontiguousarray(lambdas, dtype=np.float64)
+        _check(self._lib.sr_batch_run(self.h, len(lams), _dptr(lams), 1 if use_graph else 0, 1 if autotune else 0))
+
+    def info(self):
+        qc, ct, tm, rm, u = C.c_int(), C.c_int(), C.c_double(), C.c_double(), C.c_long()
+        _check(self._lib.sr_batch_info(self.h, C.byref(qc), C.byref(ct), C.byref(tm), C.byref(rm), C.byref(u)))
+        return {"qc": qc.value, "ctas_per_sm": ct.value, "tune_ms": tm.value, "run_ms": rm.value, "units": u.value}
+
+    def classes(self):
+        n = C.c_int()
+        _check(self._lib.sr_batch_classes(self.h, C.byref(n)))
+        out = []
+        for k in range(n.value):
+            ni, u, sm, qc, ct, ms = C.c_int(), C.c_long(), C.c_int(), C.c_int(), C.c_int(), C.c_double()
+            _check(self._lib.sr_batch_class(self.h, k, C.byref(ni), C.byref(u), C.byref(sm), C.byref(qc), C.byref(ct),
+                                            C.byref(ms)))
+            out.append({"instances": ni.value, "units": u.value, "smem_bytes": sm.value, "node_block": qc.value,
+                        "ctas_per_sm": ct.value, "tuned_ms": ms.value})
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.sr_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

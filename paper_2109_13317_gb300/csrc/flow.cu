@@ -62,15 +62,17 @@ constexpr int kQC = 16;       // integration nodes per shared-memory block
 constexpr int kThreads = 128;
 
 // Propagator products with Sigma = -i gamma: g(a) g(b) and g(a) r(b), r = -g^2 dSigma/dLambda.
-__device__ __forceinline__ double prop_gg(const double* w, const double* invh, int N, const double* gam, double a, double b) {
-    double ga = a + interp_odd(w, invh, N, gam, a);
-    double gb = b + interp_odd(w, invh, N, gam, b);
+template <typename T>
+__device__ __forceinline__ T prop_gg(const double* w, const double* invh, int N, const T* gam, double a, double b) {
+    const T ga = a + interp_odd(w, invh, N, gam, a);
+    const T gb = b + interp_odd(w, invh, N, gam, b);
     return -1.0 / (ga * gb);
 }
-__device__ __forceinline__ double prop_gr(const double* w, const double* invh, int N, const double* gam, const double* dgam, double a, double b) {
-    double ga = a + interp_odd(w, invh, N, gam, a);
-    double gb = b + interp_odd(w, invh, N, gam, b);
-    double db = interp_odd(w, invh, N, dgam, b);
+template <typename T>
+__device__ __forceinline__ T prop_gr(const double* w, const double* invh, int N, const T* gam, const T* dgam, double a, double b) {
+    const T ga = a + interp_odd(w, invh, N, gam, a);
+    const T gb = b + interp_odd(w, invh, N, gam, b);
+    const T db = interp_odd(w, invh, N, dgam, b);
     return -db / (ga * gb * gb);
 }
 
@@ -81,131 +83,189 @@ __device__ __forceinline__ bool in_support(double lam, int ch, double v, double 
     return fabs(v + m) >= lam;
 }
 
-__device__ __forceinline__ double preg(const double* w, const double* invh, int N, const double* gam, const double* dgam, int ch, double v, double x) {
+template <typename T>
+__device__ __forceinline__ T preg(const double* w, const double* invh, int N, const T* gam, const T* dgam, int ch, double v, double x) {
     if (ch == 0) return prop_gr(w, invh, N, gam, dgam, x, v - x) + prop_gr(w, invh, N, gam, dgam, v - x, x);
     if (ch == 1) return prop_gr(w, invh, N, gam, dgam, x, x - v) + prop_gr(w, invh, N, gam, dgam, x - v, x);
     return prop_gr(w, invh, N, gam, dgam, x, v + x) + prop_gr(w, invh, N, gam, dgam, v + x, x);
 }
 
-// Integration nodes of one channel (ch = 0 s, 1 t, 2 u) at transfer frequency w[vi].
-__global__ void k_channel_nodes(Geo g, const double* __restrict__ w, const double* __restrict__ invh, const double* __restrict__ gam,
-                                const double* __restrict__ dgam, double lam, double* __restrict__ nx,
-                                double* __restrict__ nW, float* __restrict__ nWf, int* __restrict__ ncount) {
-    int id = blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= 3 * g.N) return;
+// Integration nodes of one channel (ch = 0 s, 1 t, 2 u) at transfer frequency w[vi]; one
+// block per (channel, frequency).  The regular-part points ({+-w_n} merged with the clipped
+// break points) are placed by rank, their trapezoid weights and propagator values computed
+// in parallel, then compacted in order.
+template <typename T>
+__device__ void channel_nodes_block(Geo g, const double* __restrict__ w, const double* __restrict__ invh,
+                                    const T* __restrict__ gam, const T* __restrict__ dgam, double lam,
+                                    double* __restrict__ nx, T* __restrict__ nW, float* __restrict__ nWf,
+                                    int* __restrict__ ncount, const int id, float* __restrict__ nxf = nullptr) {
+    __shared__ double pts[2 * kMaxFreq + 4];
+    __shared__ __align__(16) unsigned char val_raw[sizeof(T) * (2 * kMaxFreq + 4)];
+    T* val = reinterpret_cast<T*>(val_raw);
+    __shared__ unsigned char keep[2 * kMaxFreq + 4];
+    __shared__ double bp[4];
     const int ch = id / g.N, vi = id % g.N, N = g.N;
     const double v = w[vi];
     double* X = nx + (size_t)id * g.nmax;
-    double* Wt = nW + (size_t)id * g.nmax;
-    float* Wf = nWf + (size_t)id * g.nmax;
+    T* Wt = nW + (size_t)id * g.nmax;
+    float* Wf = nWf ? nWf + (size_t)id * g.nmax : nullptr;
     const double inv2pi = 1.0 / (2.0 * kPi);
-    int n = 0;
-    // delta points of the single-scale propagator, theta(0) = 1; a point whose partner
-    // propagator lies below the cutoff (theta = 0) contributes exactly zero
-    for (int sg = 0; sg < 2; ++sg) {
-        double L = sg == 0 ? lam : -lam;
-        double a;
-        if (ch == 0) {          // G(w) S(s - w): w = s - L;  G(s - w) S(w): w = L
-            a = v - L;
-            double val = (fabs(a) - lam >= 0.0) ? prop_gg(w, invh, N, gam, a, L) * inv2pi : 0.0;
-            X[n] = a; Wt[n] = val; ++n;
-            X[n] = L; Wt[n] = val; ++n;
-        } else if (ch == 1) {   // G(w) S(w - t): w = t + L;  G(w - t) S(w): w = L
-            a = v + L;
-            X[n] = a; Wt[n] = (fabs(a) - lam >= 0.0) ? prop_gg(w, invh, N, gam, a, L) * inv2pi : 0.0; ++n;
-            a = L - v;
-            X[n] = L; Wt[n] = (fabs(a) - lam >= 0.0) ? prop_gg(w, invh, N, gam, a, L) * inv2pi : 0.0; ++n;
-        } else {                // G(w) S(u + w): w = L - u;  G(u + w) S(w): w = L
-            a = L - v;
-            X[n] = a; Wt[n] = (fabs(a) - lam >= 0.0) ? prop_gg(w, invh, N, gam, a, L) * inv2pi : 0.0; ++n;
-            a = v + L;
-            X[n] = L; Wt[n] = (fabs(a) - lam >= 0.0) ? prop_gg(w, invh, N, gam, a, L) * inv2pi : 0.0; ++n;
+    const double wmax = w[N - 1];
+    const int m = 2 * N + 4;
+    if (threadIdx.x == 0) {
+        // delta points of the single-scale propagator, theta(0) = 1; a point whose partner
+        // propagator lies below the cutoff (theta = 0) contributes exactly zero
+        int n = 0;
+        for (int sg = 0; sg < 2; ++sg) {
+            double L = sg == 0 ? lam : -lam;
+            double a;
+            if (ch == 0) {          // G(w) S(s - w): w = s - L;  G(s - w) S(w): w = L
+                a = v - L;
+                const T vv = (fabs(a) - lam >= 0.0) ? T(prop_gg(w, invh, N, gam, a, L) * inv2pi) : T(0.0);
+                X[n] = a; Wt[n] = vv; ++n;
+                X[n] = L; Wt[n] = vv; ++n;
+            } else if (ch == 1) {   // G(w) S(w - t): w = t + L;  G(w - t) S(w): w = L
+                a = v + L;
+                X[n] = a; Wt[n] = (fabs(a) - lam >= 0.0) ? T(prop_gg(w, invh, N, gam, a, L) * inv2pi) : T(0.0); ++n;
+                a = L - v;
+                X[n] = L; Wt[n] = (fabs(a) - lam >= 0.0) ? T(prop_gg(w, invh, N, gam, a, L) * inv2pi) : T(0.0); ++n;
+            } else {                // G(w) S(u + w): w = L - u;  G(u + w) S(w): w = L
+                a = L - v;
+                X[n] = a; Wt[n] = (fabs(a) - lam >= 0.0) ? T(prop_gg(w, invh, N, gam, a, L) * inv2pi) : T(0.0); ++n;
+                a = v + L;
+                X[n] = L; Wt[n] = (fabs(a) - lam >= 0.0) ? T(prop_gg(w, invh, N, gam, a, L) * inv2pi) : T(0.0); ++n;
+            }
+        }
+        // break points, clipped to [-w_max, w_max], in ascending order (insertion order on ties)
+        double q[4];
+        if (ch == 2) { q[0] = lam; q[1] = -lam; q[2] = -v + lam; q[3] = -v - lam; }
+        else { q[0] = lam; q[1] = -lam; q[2] = v + lam; q[3] = v - lam; }
+        for (int i = 0; i < 4; ++i) {
+            double c = q[i];
+            if (c > wmax) c = wmax;
+            if (c < -wmax) c = -wmax;
+            int j = i;
+            while (j > 0 && bp[j - 1] > c) { bp[j] = bp[j - 1]; --j; }
+            bp[j] = c;
         }
     }
-    // regular Katanin part: trapezoid on {+-w_n} merged with the break points, clipped
-    double pts[2 * kMaxFreq + 4];
-    int m = 0;
-    for (int i = N - 1; i >= 0; --i) pts[m++] = -w[i];
-    for (int i = 0; i < N; ++i) pts[m++] = w[i];
-    const double wmax = w[N - 1];
-    double bp[4];
-    if (ch == 2) { bp[0] = lam; bp[1] = -lam; bp[2] = -v + lam; bp[3] = -v - lam; }
-    else { bp[0] = lam; bp[1] = -lam; bp[2] = v + lam; bp[3] = v - lam; }
-    for (int i = 0; i < 4; ++i) {
-        double q = bp[i];
-        if (q > wmax) q = wmax;
-        if (q < -wmax) q = -wmax;
-        int j = m++;
-        while (j > 0 && pts[j - 1] > q) { pts[j] = pts[j - 1]; --j; }
-        pts[j] = q;
+    __syncthreads();
+    // place every point by rank: a mesh point precedes break points of equal value
+    for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) {
+        const double x = i < N ? -w[N - 1 - i] : w[i - N];
+        int r = i;
+        for (int j = 0; j < 4; ++j) r += bp[j] < x;
+        pts[r] = x;
     }
-    for (int i = 0; i < m; ++i) {
+    for (int j = threadIdx.x; j < 4; j += blockDim.x) {
+        const double x = bp[j];
+        int lo = 0, hi = 2 * N;   // count mesh points <= x
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            const double y = mid < N ? -w[N - 1 - mid] : w[mid - N];
+            if (y <= x) lo = mid + 1; else hi = mid;
+        }
+        pts[lo + j] = x;
+    }
+    __syncthreads();
+    // trapezoid weight of each point over its supported neighbouring segments, times the
+    // regular propagator pair without theta
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
         double wgt = 0.0;
         if (i > 0 && pts[i] > pts[i - 1] && in_support(lam, ch, v, 0.5 * (pts[i] + pts[i - 1])))
             wgt += 0.5 * (pts[i] - pts[i - 1]);
         if (i + 1 < m && pts[i + 1] > pts[i] && in_support(lam, ch, v, 0.5 * (pts[i] + pts[i + 1])))
             wgt += 0.5 * (pts[i + 1] - pts[i]);
-        if (wgt == 0.0) continue;
-        X[n] = pts[i];
-        Wt[n] = wgt * preg(w, invh, N, gam, dgam, ch, v, pts[i]) * inv2pi;
-        ++n;
+        val[i] = wgt == 0.0 ? T(0.0) : T(wgt * preg(w, invh, N, gam, dgam, ch, v, pts[i]) * inv2pi);
+        keep[i] = wgt != 0.0;
     }
-    for (int i = 0; i < n; ++i) Wf[i] = (float)Wt[i];
-    ncount[id] = n;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int n = 4;
+        for (int i = 0; i < m; ++i) {
+            if (!keep[i]) continue;
+            X[n] = pts[i];
+            Wt[n] = val[i];
+            ++n;
+        }
+        if (Wf)
+            for (int i = 0; i < n; ++i) Wf[i] = (float)value_of(Wt[i]);
+        if (nxf)
+            for (int i = 0; i < n; ++i) nxf[(size_t)id * g.nmax + i] = (float)X[i];
+        ncount[id] = n;
+    }
 }
 
-// Deterministic block sum (fixed reduction tree for a fixed block size).
-template <int NV>
-__device__ void block_sum(double (&v)[NV], double* red /* NV * 32 */) {
+template <typename T>
+__global__ void k_channel_nodes(Geo g, const double* __restrict__ w, const double* __restrict__ invh,
+                                const T* __restrict__ gam, const T* __restrict__ dgam, double lam,
+                                double* __restrict__ nx, T* __restrict__ nW, float* __restrict__ nWf,
+                                int* __restrict__ ncount, float* __restrict__ nxf) {
+    channel_nodes_block<T>(g, w, invh, gam, dgam, lam, nx, nW, nWf, ncount, blockIdx.x, nxf);
+}
+
+// Deterministic block sum (fixed reduction tree for a fixed block size) of NV scalars of
+// type T (doubles or dual numbers, reduced component by component); red holds
+// NV * (sizeof(T) / 8) * 32 doubles.
+template <typename T, int NV>
+__device__ void block_sum(T (&v)[NV], double* red) {
+    constexpr int K = NV * (int)(sizeof(T) / sizeof(double));
+    double* a = reinterpret_cast<double*>(v);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
-    for (int k = 0; k < NV; ++k)
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    for (int k = 0; k < K; ++k)
+        for (int o = 16; o > 0; o >>= 1) a[k] += __shfl_down_sync(0xffffffffu, a[k], o);
     __syncthreads();
     if (lane == 0)
-        for (int k = 0; k < NV; ++k) red[k * 32 + wid] = v[k];
+        for (int k = 0; k < K; ++k) red[k * 32 + wid] = a[k];
     __syncthreads();
     if (threadIdx.x == 0)
-        for (int k = 0; k < NV; ++k) {
-            double a = 0.0;
-            for (int i = 0; i < nw; ++i) a += red[k * 32 + i];
-            v[k] = a;
+        for (int k = 0; k < K; ++k) {
+            double acc = 0.0;
+            for (int i = 0; i < nw; ++i) acc += red[k * 32 + i];
+            a[k] = acc;
         }
 }
 
 // Flow of the self-energy, one block per mesh frequency w_n:
 // dgamma(w) = -(1/2pi) sum_{w2 = +-Lambda} H(w, w2) / (w2 + gamma(w2)),
 // H = 2 sum_j Gamma^00_{ref j}(w+w2, 0, w-w2) - sum_c f_c Gamma^cc_{ref ref}(w+w2, w2-w, 0).
-__global__ void k_sigma_rhs(Geo g, Tabs tb, const double* __restrict__ w, const double* __restrict__ gam,
-                            const double* __restrict__ G, double lam, double* __restrict__ dgam) {
-    __shared__ double red[2 * 32];
-    const int n = blockIdx.x;
+template <typename T>
+__device__ void sigma_rhs_block(Geo g, Tabs tb, const double* __restrict__ w, const T* __restrict__ gam,
+                                const T* __restrict__ G, double lam, T* __restrict__ dgam, const int n) {
+    __shared__ double red[2 * 32 * (sizeof(T) / sizeof(double))];
     const double w1 = w[n];
-    double H[2] = {0.0, 0.0};
+    T H[2] = {T(0.0), T(0.0)};
     for (int sg = 0; sg < 2; ++sg) {
         const double w2 = sg == 0 ? lam : -lam;
         Desc<double> d;
         make_desc(w1 + w2, 0.0, w1 - w2, 1, 0, tb, g, d);
-        double h = 0.0;
+        T h = T(0.0);
         for (int r = threadIdx.x; r < g.Ns; r += blockDim.x) h += (double)tb.mult[r] * row_value(G, d, tb, g, r, 0);
-        h *= 2.0;
+        h = 2.0 * h;
         if (threadIdx.x == 0) {
             Desc<double> e;
             make_desc(w1 + w2, w2 - w1, 0.0, 2, 0, tb, g, e);
-            double f = 0.0;
+            T f = T(0.0);
             if (g.nc == 2) f = row_value(G, e, tb, g, 0, 0) + 3.0 * row_value(G, e, tb, g, 0, 1);
             else for (int c = 0; c < 4; ++c) f += row_value(G, e, tb, g, 0, c);
             h -= f;
         }
         H[sg] = h;
     }
-    block_sum<2>(H, red);
+    block_sum<T, 2>(H, red);
     if (threadIdx.x == 0) {
-        double acc = 0.0;
+        T acc = T(0.0);
         acc += H[0] / (lam + interp_odd(w, tb.invh, g.N, gam, lam));
         acc += H[1] / (-lam + interp_odd(w, tb.invh, g.N, gam, -lam));
         dgam[n] = -acc / (2.0 * kPi);
     }
+}
+
+template <typename T>
+__global__ void k_sigma_rhs(Geo g, Tabs tb, const double* __restrict__ w, const T* __restrict__ gam,
+                            const T* __restrict__ G, double lam, T* __restrict__ dgam) {
+    sigma_rhs_block<T>(g, tb, w, gam, G, lam, dgam, blockIdx.x);
 }
 
 // Projected products of the three channels (hand-derived from the Pauli algebra):
@@ -248,7 +308,7 @@ template <typename T>
 struct ShPtrs {
     T* acc;
     T* part;
-    Desc<T>* desc;
+    Desc<typename WeightOf<T>::type>* desc;
     T* rows;
     T* onrow;
     T* wq;
@@ -259,7 +319,7 @@ __device__ __forceinline__ ShPtrs<T> carve(unsigned char* raw, const Geo& g, con
     ShPtrs<T> p;
     size_t off = 0;
     auto take = [&](size_t bytes) { unsigned char* q = raw + off; off += (bytes + 15) & ~size_t(15); return q; };
-    p.desc = (Desc<T>*)take(sizeof(Desc<T>) * kQC * 4);
+    p.desc = (Desc<typename WeightOf<T>::type>*)take(sizeof(Desc<typename WeightOf<T>::type>) * kQC * 4);
     p.acc = (T*)take(sizeof(T) * g.Ns * NC);
     p.part = (T*)take(sizeof(T) * tb.nprod);
     p.rows = (T*)take(sizeof(T) * kQC * 2 * g.Ns * NC);
@@ -272,8 +332,8 @@ __device__ __forceinline__ ShPtrs<T> carve(unsigned char* raw, const Geo& g, con
 // row 0 / 1 of the s channel: (s, w1'-x, x-w2') and (s, x-w1, x-w2);
 // t channel: (w1+x, t, w1'-x), (x+w2', t, x-w2), on-site (w2'+x, w2-x, -t), (w1+x, x-w1', -t);
 // u channel: (w1+x, x-w2', u) and (w1'+x, w2-x, u).
-__device__ __forceinline__ void node_args(int ch, int rw, double x, double s, double t, double u, double w1p,
-                                          double w2p, double w1, double w2, double& a, double& b, double& c) {
+template <typename F = double>
+__device__ __forceinline__ void node_args(int ch, int rw, F x, F s, F t, F u, F w1p, F w2p, F w1, F w2, F& a, F& b, F& c) {
     if (ch == 0) {
         if (rw == 0) { a = s; b = w1p - x; c = x - w2p; }
         else { a = s; b = x - w1; c = x - w2; }
@@ -292,7 +352,7 @@ template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const double* __restrict__ w,
                                                         const T* __restrict__ G, const double* __restrict__ nx,
                                                         const T* __restrict__ nW, const int* __restrict__ ncount,
-                                                        double* __restrict__ dG) {
+                                                        T* __restrict__ dG) {
     extern __shared__ __align__(16) unsigned char smem[];
     ShPtrs<T> sh = carve<T, NC>(smem, g, tb);
     const int tid = threadIdx.x;
@@ -409,7 +469,7 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const do
         const int r = o / NC, c = o % NC;
         T a = (T)0;
         for (int k = tb.gath_off[o]; k < tb.gath_off[o + 1]; ++k) a += sh.part[tb.gath_idx[k]];
-        const double v = (double)sh.acc[o] - 2.0 * (double)a;
+        const T v = sh.acc[o] - 2.0 * a;
         dG[((size_t)(p * g.N + ti) * NC + c) * g.Ns + r] = v;
     }
 }
@@ -445,11 +505,11 @@ __host__ __device__ inline size_t f32_smem_bytes(int Ns, int nsp, int nc, int np
 // (SU2), the lattice sum is the per-triple contraction C[c][rA][rB] = sum_q A_q B_q in 4x4
 // register tiles, gathered through the table at the end.
 template <int NC, bool DENSE>
-__global__ void __launch_bounds__(kThreads) k_gamma_rhs_f32(Geo g, Tabs tb, const float* __restrict__ Gf,
-                                                            const float* __restrict__ Gs, const double* __restrict__ nx,
-                                                            const float* __restrict__ nW, const int* __restrict__ ncount,
-                                                            double* __restrict__ dG) {
-    extern __shared__ __align__(16) unsigned char smem[];
+__device__ void gamma_rhs_f32_triple(const Geo& g, const Tabs& tb, const float* __restrict__ Gf,
+                                     const float* __restrict__ Gs, const float* __restrict__ nx,
+                                     const float* __restrict__ nW, const int* __restrict__ ncount,
+                                     double* __restrict__ dG, const int p, const int ti, unsigned char* smem,
+                                     const int qc) {
     const int nsp = g.nsp, nsp4 = nsp >> 2, rowp = NC * nsp;
     ShF<NC, DENSE> sh;
     {
@@ -463,15 +523,15 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_f32(Geo g, Tabs tb, cons
         sh.cacc = (float*)take(sizeof(float) * (DENSE ? NC * nsp * nsp : tb.nprod));
     }
     const int tid = threadIdx.x;
-    const int ti = blockIdx.x % g.N;
-    const int p = blockIdx.x / g.N;
     int si = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
     while ((si + 1) * (si + 2) / 2 <= p) ++si;
     while (si * (si + 1) / 2 > p) --si;
     const int ui = p - si * (si + 1) / 2;
-    const double* w = tb.w;
-    const double s = w[si], t = w[ti], u = w[ui];
-    const double w1p = (s + t + u) / 2, w2p = (s - t - u) / 2, w1 = (s - t + u) / 2, w2 = (s + t - u) / 2;
+    const float* w = tb.wf;
+    __syncthreads();   // shared memory of a previous triple (persistent callers) is consumed
+    // frequencies and integration nodes in FP32 (the descriptors of this kernel are FP32)
+    const float s = w[si], t = w[ti], u = w[ui];
+    const float w1p = (s + t + u) * 0.5f, w2p = (s - t - u) * 0.5f, w1 = (s - t + u) * 0.5f, w2 = (s + t - u) * 0.5f;
     const int ncacc = DENSE ? NC * nsp * nsp : tb.nprod;
     for (int o = tid; o < g.Ns * NC; o += blockDim.x) sh.acc[o] = 0.0f;
     for (int o = tid; o < ncacc; o += blockDim.x) sh.cacc[o] = 0.0f;
@@ -480,17 +540,17 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_f32(Geo g, Tabs tb, cons
         const int vi = ch == 0 ? si : (ch == 1 ? ti : ui);
         const int cidx = ch * g.N + vi;
         const int nq = ncount[cidx];
-        const double* X = nx + (size_t)cidx * g.nmax;
+        const float* X = nx + (size_t)cidx * g.nmax;
         const float* Wp = nW + (size_t)cidx * g.nmax;
         const int nrow = ch == 1 ? 4 : 2;
-        for (int q0 = 0; q0 < nq; q0 += kQF) {
-            const int qn = min(kQF, nq - q0);
+        for (int q0 = 0; q0 < nq; q0 += qc) {
+            const int qn = min(qc, nq - q0);
             __syncthreads();
             for (int idx = tid; idx < qn * nrow; idx += blockDim.x) {
                 const int q = idx / nrow, rw = idx % nrow;
-                const double x = X[q0 + q];
-                double a, b, c;
-                node_args(ch, rw, x, s, t, u, w1p, w2p, w1, w2, a, b, c);
+                const float x = X[q0 + q];
+                float a, b, c;
+                node_args<float>(ch, rw, x, s, t, u, w1p, w2p, w1, w2, a, b, c);
                 const int exs = ch == 0 ? 0 : (ch == 2 ? 2 : (rw < 2 ? 1 : 2));
                 make_desc4(a, b, c, exs, vi, tb, g, rowp, sh.desc[q * 4 + rw]);
                 if (rw == 0) sh.wq[q] = Wp[q0 + q];
@@ -624,6 +684,15 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_f32(Geo g, Tabs tb, cons
     }
 }
 
+template <int NC, bool DENSE>
+__global__ void __launch_bounds__(kThreads) k_gamma_rhs_f32(Geo g, Tabs tb, const float* __restrict__ Gf,
+                                                            const float* __restrict__ Gs, const float* __restrict__ nx,
+                                                            const float* __restrict__ nW, const int* __restrict__ ncount,
+                                                            double* __restrict__ dG) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    gamma_rhs_f32_triple<NC, DENSE>(g, tb, Gf, Gs, nx, nW, ncount, dG, blockIdx.x / g.N, blockIdx.x % g.N, smem, kQF);
+}
+
 // FP32 shadow of the state in the padded layout, and (with_swap) the exchanged copy in which
 // entry (c, r) holds the stored value of the pair (rep_r, ref): component perm(c) of site
 // swap_r[r].  Padding sites are zero.
@@ -644,7 +713,8 @@ __global__ void k_shadow(Geo g, Tabs tb, const double* __restrict__ G, float* __
     if (with_swap) Gf[g.nentp + i] = vs;
 }
 
-__global__ void k_fill_init(Geo g, const double* __restrict__ init /* Ns * nc */, double* __restrict__ G) {
+template <typename T>
+__global__ void k_fill_init(Geo g, const T* __restrict__ init /* Ns * nc */, T* __restrict__ G) {
     long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i >= g.nent) return;
     int r = (int)(i % g.Ns);
@@ -675,34 +745,45 @@ __global__ void k_rk_stage(long n, const double* __restrict__ y0, KPtrs kp, int 
     out[i] = y0[i] + h * acc;
 }
 
-// Fifth-order solution and error norm max |h (y5 - y4)| / (atol + rtol max(|y0|, |y_new|)).
-__global__ void k_rk_final(long n, const double* __restrict__ y0, KPtrs kp, double h, double rtol, double atol,
-                           double* __restrict__ out, unsigned long long* __restrict__ errbits, int* __restrict__ flag) {
+// Fifth-order solution; the block-wise maxima of |h (y5 - y4)| and of max(|y0|, |y_new|) are
+// combined with atomicMax on their (non-negative) bit patterns, which is exact and
+// order-independent: errbits[0] = max error, errbits[1] = max magnitude.
+__global__ void k_rk_final(long n, const double* __restrict__ y0, KPtrs kp, double h, double* __restrict__ out,
+                           unsigned long long* __restrict__ errbits, int* __restrict__ flag) {
     const double b5[7] = {35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0.0};
     const double b4[7] = {5179.0 / 57600, 0.0, 7571.0 / 16695, 393.0 / 640, -92097.0 / 339200, 187.0 / 2100, 1.0 / 40};
     long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    double e = 0.0;
+    double e = 0.0, y = 0.0;
     if (i < n) {
         double y5 = 0.0, y4 = 0.0;
         for (int r = 0; r < 7; ++r) { double kv = kp.k[r][i]; y5 += b5[r] * kv; y4 += b4[r] * kv; }
         double yn = y0[i] + h * y5;
-        e = fabs(h * (y5 - y4)) / (atol + rtol * fmax(fabs(y0[i]), fabs(yn)));
+        e = fabs(h * (y5 - y4));
+        y = fmax(fabs(y0[i]), fabs(yn));
         if (!isfinite(yn) || !isfinite(e)) atomicOr(flag, 1);
         out[i] = yn;
     }
-    for (int o = 16; o > 0; o >>= 1) e = fmax(e, __shfl_down_sync(0xffffffffu, e, o));
-    if ((threadIdx.x & 31) == 0 && e > 0.0) atomicMax(errbits, (unsigned long long)__double_as_longlong(e));
+    for (int o = 16; o > 0; o >>= 1) {
+        e = fmax(e, __shfl_down_sync(0xffffffffu, e, o));
+        y = fmax(y, __shfl_down_sync(0xffffffffu, y, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (e > 0.0) atomicMax(errbits, (unsigned long long)__double_as_longlong(e));
+        if (y > 0.0) atomicMax(errbits + 1, (unsigned long long)__double_as_longlong(y));
+    }
 }
 
 // Correlations chi^{cc}_{b j} (Eq. frg:correlation), one block per (b, j): bubble (local)
 // plus the product-trapezoid vertex term with the exact G^2 weights of each segment.
-template <int NC>
-__global__ void k_chi(Geo g, Tabs tb, const double* __restrict__ w, const double* __restrict__ gam,
-                      const double* __restrict__ G, double lam, const int2* __restrict__ cmap,
-                      const int* __restrict__ onsite, int ntot, double* __restrict__ chi) {
-    __shared__ double y[kMaxFreq + 1], Wn[kMaxFreq + 1];
-    __shared__ double red[NC * 32];
+template <typename T, int NC>
+__global__ void k_chi(Geo g, Tabs tb, const double* __restrict__ w, const T* __restrict__ gam,
+                      const T* __restrict__ G, double lam, const int2* __restrict__ cmap,
+                      const int* __restrict__ onsite, int ntot, T* __restrict__ chi) {
+    __shared__ double y[kMaxFreq + 1];
+    __shared__ __align__(16) unsigned char wn_raw[sizeof(T) * (kMaxFreq + 1)];
+    __shared__ double red[NC * 32 * (sizeof(T) / sizeof(double))];
     __shared__ int Ksh;
+    T* Wn = reinterpret_cast<T*>(wn_raw);
     const int pidx = blockIdx.x;      // b * ntot + j
     const int b = pidx / ntot;
     const int on = onsite[pidx];
@@ -713,11 +794,11 @@ __global__ void k_chi(Geo g, Tabs tb, const double* __restrict__ w, const double
         int K = 0;
         y[K++] = lam;
         for (int i = 0; i < N; ++i) if (w[i] > lam) y[K++] = w[i];
-        for (int k = 0; k < K; ++k) Wn[k] = 0.0;
+        for (int k = 0; k < K; ++k) Wn[k] = T(0.0);
         for (int k = 0; k + 1 < K; ++k) {
-            double ya = y[k] + interp_odd(w, tb.invh, N, gam, y[k]);
-            double yb = y[k + 1] + interp_odd(w, tb.invh, N, gam, y[k + 1]);
-            double seg = (y[k + 1] - y[k]) / (ya * yb);
+            const T ya = y[k] + interp_odd(w, tb.invh, N, gam, y[k]);
+            const T yb = y[k + 1] + interp_odd(w, tb.invh, N, gam, y[k + 1]);
+            const T seg = (y[k + 1] - y[k]) / (ya * yb);
             Wn[k] += 0.5 * seg;
             Wn[k + 1] += 0.5 * seg;
         }
@@ -726,17 +807,17 @@ __global__ void k_chi(Geo g, Tabs tb, const double* __restrict__ w, const double
     }
     __syncthreads();
     const int K = Ksh, M = 2 * K;
-    double acc[NC];
+    T acc[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+    for (int c = 0; c < NC; ++c) acc[c] = T(0.0);
     for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
         const int pi = idx / M, qi = idx % M;
         const double xp = pi < K ? y[pi] : -y[pi - K];
         const double xq = qi < K ? y[qi] : -y[qi - K];
-        const double wpq = Wn[pi % K] * Wn[qi % K];
+        const T wpq = Wn[pi % K] * Wn[qi % K];
         Desc<double> d;
         make_desc(xp + xq, 0.0, xp - xq, 1, 0, tb, g, d);
-        double v[NC], e[NC];
+        T v[NC], e[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) v[c] = row_value(G, d, tb, g, pm.x, perm_of(pm.y, c));
         if (on) {
@@ -746,41 +827,42 @@ __global__ void k_chi(Geo g, Tabs tb, const double* __restrict__ w, const double
         }
 #pragma unroll
         for (int mu = 0; mu < NC; ++mu) {
-            double F = 4.0 * v[mu];
+            T F = 4.0 * v[mu];
             if (on) {
-                double x;
-                if (NC == 2) x = mu == 0 ? 2.0 * (e[0] + 3.0 * e[1]) : 2.0 * (e[0] - e[1]);
+                T x;
+                if (NC == 2) x = mu == 0 ? T(2.0 * (e[0] + 3.0 * e[1])) : T(2.0 * (e[0] - e[1]));
                 else {
-                    x = 0.0;
-                    for (int k = 0; k < 4; ++k) x += (mu == 0 || k == 0 || k == mu) ? 2.0 * e[k] : -2.0 * e[k];
+                    x = T(0.0);
+                    for (int k = 0; k < 4; ++k) x += (mu == 0 || k == 0 || k == mu) ? T(2.0 * e[k]) : T(-2.0 * e[k]);
                 }
                 F -= x;
             }
             acc[mu] += wpq * F;
         }
     }
-    block_sum<NC>(acc, red);
+    block_sum<T, NC>(acc, red);
     if (threadIdx.x == 0) {
-        double bub = 0.0;
+        T bub = T(0.0);
         for (int k = 0; k < K; ++k) bub += Wn[k];
-        bub /= (2.0 * kPi);
+        bub = bub / (2.0 * kPi);
         for (int mu = 0; mu < NC; ++mu)
-            chi[(size_t)pidx * NC + mu] = (on ? bub : 0.0) - acc[mu] / (16.0 * kPi * kPi);
+            chi[(size_t)pidx * NC + mu] = (on ? bub : T(0.0)) - acc[mu] / (16.0 * kPi * kPi);
     }
 }
 
 // chi(k) = (1/N_b) sum_{b, j} cos(k (r_b - r_j)) sum_{mu = x,y,z} chi^{mu mu}_{b j}.
-__global__ void k_chi_k(int nk, const double* __restrict__ kp, const double* __restrict__ chi,
-                        const double* __restrict__ dr, int npairs, int nb, int nc, double* __restrict__ out) {
+template <typename T>
+__global__ void k_chi_k(int nk, const double* __restrict__ kp, const T* __restrict__ chi,
+                        const double* __restrict__ dr, int npairs, int nb, int nc, T* __restrict__ out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nk) return;
     const double kx = kp[3 * i], ky = kp[3 * i + 1], kz = kp[3 * i + 2];
-    double acc = 0.0;
+    T acc = T(0.0);
     for (int p = 0; p < npairs; ++p) {
-        double sp = nc == 2 ? 3.0 * chi[(size_t)p * 2 + 1] : chi[(size_t)p * 4 + 1] + chi[(size_t)p * 4 + 2] + chi[(size_t)p * 4 + 3];
+        const T sp = nc == 2 ? T(3.0 * chi[(size_t)p * 2 + 1]) : T(chi[(size_t)p * 4 + 1] + chi[(size_t)p * 4 + 2] + chi[(size_t)p * 4 + 3]);
         acc += cos(kx * dr[3 * p] + ky * dr[3 * p + 1] + kz * dr[3 * p + 2]) * sp;
     }
-    out[i] = acc / nb;
+    out[i] = acc / (double)nb;
 }
 
 }  // namespace
@@ -812,11 +894,13 @@ struct sr_flow {
     cudaStream_t stream = nullptr;
     double lambda = 0.0;
     std::vector<double> mesh;
+    int ntan = 0;   // tangent directions (0: plain flow; kTan: the state holds Dual<kTan> values)
+    int ts = 1;     // doubles per state scalar
 
     DevBuf<double> w, gam, G, dgam, dG;
     DevBuf<float> Gf;
     DevBuf<double> nx, nW;
-    DevBuf<float> nWf;
+    DevBuf<float> nWf, nxf;
     DevBuf<int> ncount;
     DevBuf<int> swap_r, swap_perm, onsite_perm, mult, gath_off, gath_idx;
     DevBuf<int2> prod;
@@ -839,6 +923,8 @@ struct sr_flow {
     bool profiling = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[3];
     double last_err = 0.0, h_next = 0.0;
+    bool fsal = false;           // kg[6] / kG[6] hold the right-hand side of the current state
+    long step_limit = 1000000;   // attempted steps per sr_flow_step call
     long n_rhs = 0, n_accept = 0, n_reject = 0;
     size_t smem_rhs = 0;
 
@@ -851,11 +937,27 @@ struct sr_flow {
     }
 };
 
+// The dynamic shared-memory limit is a property of the kernel, shared by every flow: raise
+// it to the largest size any flow has asked for, never lower it.
+static std::mutex g_smem_mu;
+static std::map<std::pair<int, const void*>, int> g_smem_max;
+
+static cudaError_t ensure_smem(const void* kernel, size_t bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    int& cur = g_smem_max[{dev, kernel}];
+    if ((int)bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = (int)bytes;
+    return e;
+}
+
 static int pack_perm(const sr::Perm& p) { return p[0] | (p[1] << 2) | (p[2] << 4) | (p[3] << 6); }
 
-static size_t rhs_smem_bytes(const Geo& g, int nprod, bool fp32) {
-    size_t tsz = fp32 ? 4 : 8;
-    size_t dsz = fp32 ? sizeof(Desc<float>) : sizeof(Desc<double>);
+static size_t rhs_smem_bytes(const Geo& g, int nprod, size_t tsz) {
+    const size_t dsz = sizeof(Desc<double>);
     auto rnd = [](size_t b) { return (b + 15) & ~size_t(15); };
     return rnd(dsz * kQC * 4) + rnd(tsz * g.Ns * g.nc) + rnd(tsz * nprod) + rnd(tsz * kQC * 2 * g.Ns * g.nc) +
            rnd(tsz * kQC * 2 * g.nc) + rnd(tsz * kQC);
@@ -883,15 +985,38 @@ static sr_status run_rhs(sr_flow* f, double lam, const double* gam_s, const doub
     const Geo& g = f->g;
     Tabs tb = f->tabs();
     cudaEvent_t e0 = nullptr;
-    if (sr_status s = prof_begin(f, 0, &e0)) return s;
-    k_sigma_rhs<<<g.N, 64, 0, f->stream>>>(g, tb, f->w.p, gam_s, G_s, lam, dgam_o);
-    if (sr_status s = prof_end(f, 0, e0)) return s;
-    int nt = 3 * g.N;
-    if (sr_status s = prof_begin(f, 1, &e0)) return s;
-    k_channel_nodes<<<(nt + 63) / 64, 64, 0, f->stream>>>(g, f->w.p, f->invh.p, gam_s, dgam_o, lam, f->nx.p, f->nW.p, f->nWf.p,
-                                                           f->ncount.p);
-    if (sr_status s = prof_end(f, 1, e0)) return s;
     const int blocks = g.npair * g.N;
+    if (f->ntan) {
+        // tangent-linear flow: the same kernels on dual numbers
+        const DualT* gs = reinterpret_cast<const DualT*>(gam_s);
+        const DualT* Gd = reinterpret_cast<const DualT*>(G_s);
+        DualT* dgo = reinterpret_cast<DualT*>(dgam_o);
+        DualT* dGo = reinterpret_cast<DualT*>(dG_o);
+        DualT* nW = reinterpret_cast<DualT*>(f->nW.p);
+        if (sr_status s = prof_begin(f, 0, &e0)) return s;
+        k_sigma_rhs<DualT><<<g.N, 64, 0, f->stream>>>(g, tb, f->w.p, gs, Gd, lam, dgo);
+        if (sr_status s = prof_end(f, 0, e0)) return s;
+        if (sr_status s = prof_begin(f, 1, &e0)) return s;
+        k_channel_nodes<DualT><<<3 * g.N, 128, 0, f->stream>>>(g, f->w.p, f->invh.p, gs, dgo, lam, f->nx.p, nW, nullptr, f->ncount.p,
+                                                              nullptr);
+        if (sr_status s = prof_end(f, 1, e0)) return s;
+        if (sr_status s = prof_begin(f, 2, &e0)) return s;
+        if (g.nc == 2)
+            k_gamma_rhs<DualT, 2><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, f->w.p, Gd, f->nx.p, nW, f->ncount.p, dGo);
+        else
+            k_gamma_rhs<DualT, 4><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, f->w.p, Gd, f->nx.p, nW, f->ncount.p, dGo);
+        if (sr_status s = prof_end(f, 2, e0)) return s;
+        CK(cudaGetLastError());
+        f->n_rhs++;
+        return SR_OK;
+    }
+    if (sr_status s = prof_begin(f, 0, &e0)) return s;
+    k_sigma_rhs<double><<<g.N, 64, 0, f->stream>>>(g, tb, f->w.p, gam_s, G_s, lam, dgam_o);
+    if (sr_status s = prof_end(f, 0, e0)) return s;
+    if (sr_status s = prof_begin(f, 1, &e0)) return s;
+    k_channel_nodes<double><<<3 * g.N, 128, 0, f->stream>>>(g, f->w.p, f->invh.p, gam_s, dgam_o, lam, f->nx.p, f->nW.p, f->nWf.p,
+                                                           f->ncount.p, f->prec == SR_FP32_MIXED ? f->nxf.p : nullptr);
+    if (sr_status s = prof_end(f, 1, e0)) return s;
     if (sr_status s = prof_begin(f, 2, &e0)) return s;
     if (f->prec == SR_FP64) {
         if (g.nc == 2)
@@ -901,11 +1026,11 @@ static sr_status run_rhs(sr_flow* f, double lam, const double* gam_s, const doub
     } else {
         const float* Gs = f->has_swap ? Gf_s + g.nentp : Gf_s;
         if (g.nc == 2 && f->dense)
-            k_gamma_rhs_f32<2, true><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, Gf_s, Gs, f->nx.p, f->nWf.p, f->ncount.p, dG_o);
+            k_gamma_rhs_f32<2, true><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, Gf_s, Gs, f->nxf.p, f->nWf.p, f->ncount.p, dG_o);
         else if (g.nc == 2)
-            k_gamma_rhs_f32<2, false><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, Gf_s, Gs, f->nx.p, f->nWf.p, f->ncount.p, dG_o);
+            k_gamma_rhs_f32<2, false><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, Gf_s, Gs, f->nxf.p, f->nWf.p, f->ncount.p, dG_o);
         else
-            k_gamma_rhs_f32<4, false><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, Gf_s, Gs, f->nx.p, f->nWf.p, f->ncount.p, dG_o);
+            k_gamma_rhs_f32<4, false><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, Gf_s, Gs, f->nxf.p, f->nWf.p, f->ncount.p, dG_o);
     }
     if (sr_status s = prof_end(f, 2, e0)) return s;
     CK(cudaGetLastError());
@@ -989,8 +1114,8 @@ extern "C" sr_status sr_frequency_mesh_exponential(int n, double wmin, double wm
 
 // ----------------------------------------------------------------------------- ABI: flow
 
-extern "C" sr_status sr_flow_init(const sr_lattice* lat, int n_freq, const double* freq_pos, double lambda_init,
-                                  sr_precision precision, void* cuda_stream, sr_flow** out) {
+static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* freq_pos, double lambda_init,
+                             sr_precision precision, void* cuda_stream, int npar, const double* dM, sr_flow** out) {
     if (!lat || !freq_pos || !out) return fail(SR_EINVAL, "null argument");
     *out = nullptr;
     if (n_freq < 2 || n_freq > kMaxFreq) return fail(SR_EINVAL, "n_freq must be in [2, %d]", kMaxFreq);
@@ -1005,6 +1130,20 @@ extern "C" sr_status sr_flow_init(const sr_lattice* lat, int n_freq, const doubl
     f->lat = lat;
     f->prec = precision;
     f->stream = (cudaStream_t)cuda_stream;
+    f->ntan = npar > 0 ? kTan : 0;
+    f->ts = 1 + f->ntan;
+    const int ts = f->ts;
+    std::vector<double> init_host = lat->init_gamma;
+    if (npar > 0) {
+        std::vector<double> dinit;
+        std::string msg;
+        if (sr_status s = sr::tangent_init(lat, npar, dM, &dinit, &msg)) return fail(s, "%s", msg.c_str());
+        init_host.assign(lat->init_gamma.size() * ts, 0.0);
+        for (size_t e = 0; e < lat->init_gamma.size(); ++e) {
+            init_host[e * ts] = lat->init_gamma[e];
+            for (int p = 0; p < npar; ++p) init_host[e * ts + 1 + p] = dinit[e * npar + p];
+        }
+    }
     f->lambda = lambda_init;
     f->mesh.assign(freq_pos, freq_pos + n_freq);
     Geo& g = f->g;
@@ -1089,44 +1228,69 @@ extern "C" sr_status sr_flow_init(const sr_lattice* lat, int n_freq, const doubl
     CK(f->prod.upload(prods.data(), prods.size(), st));
     CK(f->gath_off.upload(goff.data(), goff.size(), st));
     CK(f->gath_idx.upload(gidx.data(), gidx.size(), st));
-    CK(f->init.upload(lat->init_gamma.data(), lat->init_gamma.size(), st));
+    CK(f->init.upload(init_host.data(), init_host.size(), st));
     {
         std::vector<int2> cm(lat->chi_map.size());
         for (size_t i = 0; i < cm.size(); ++i) cm[i] = make_int2(lat->chi_map[i].r, pack_perm(lat->chi_map[i].perm));
         CK(f->chi_map.upload(cm.data(), cm.size(), st));
         CK(f->chi_onsite.upload(lat->chi_onsite.data(), lat->chi_onsite.size(), st));
         CK(f->chi_dr.upload(lat->chi_dr.data(), lat->chi_dr.size(), st));
-        CK(f->chi.alloc(lat->chi_map.size() * g.nc));
+        CK(f->chi.alloc(lat->chi_map.size() * g.nc * ts));
     }
     // state
-    CK(f->gam.alloc(g.N));
-    CK(f->G.alloc(g.nent));
-    CK(f->dgam.alloc(g.N));
-    CK(f->dG.alloc(g.nent));
+    CK(f->gam.alloc((size_t)g.N * ts));
+    CK(f->G.alloc((size_t)g.nent * ts));
+    CK(f->dgam.alloc((size_t)g.N * ts));
+    CK(f->dG.alloc((size_t)g.nent * ts));
     if (precision == SR_FP32_MIXED) CK(f->Gf.alloc((size_t)g.nentp * (f->has_swap ? 2 : 1)));
     CK(f->nx.alloc((size_t)3 * g.N * g.nmax));
-    CK(f->nW.alloc((size_t)3 * g.N * g.nmax));
+    CK(f->nW.alloc((size_t)3 * g.N * g.nmax * ts));
     CK(f->nWf.alloc((size_t)3 * g.N * g.nmax));
+    CK(f->nxf.alloc((size_t)3 * g.N * g.nmax));
     CK(f->ncount.alloc((size_t)3 * g.N));
     CK(f->flag.alloc(1));
-    CK(f->errbits.alloc(1));
-    CK(cudaMemsetAsync(f->gam.p, 0, sizeof(double) * g.N, st));
-    k_fill_init<<<(unsigned)((g.nent + 255) / 256), 256, 0, st>>>(g, f->init.p, f->G.p);
+    CK(f->errbits.alloc(2));
+    CK(cudaMemsetAsync(f->gam.p, 0, sizeof(double) * g.N * ts, st));
+    if (f->ntan)
+        k_fill_init<DualT><<<(unsigned)((g.nent + 255) / 256), 256, 0, st>>>(g, reinterpret_cast<const DualT*>(f->init.p),
+                                                                            reinterpret_cast<DualT*>(f->G.p));
+    else
+        k_fill_init<double><<<(unsigned)((g.nent + 255) / 256), 256, 0, st>>>(g, f->init.p, f->G.p);
     CK(cudaGetLastError());
     if (sr_status s2 = refresh_shadow(f.get(), f->G.p, f->Gf.p)) return s2;
     f->smem_rhs = precision == SR_FP32_MIXED ? f32_smem_bytes(g.Ns, g.nsp, g.nc, f->nprod, f->dense)
-                                             : rhs_smem_bytes(g, f->nprod, false);
+                                             : rhs_smem_bytes(g, f->nprod, f->ntan ? sizeof(DualT) : sizeof(double));
     if (f->smem_rhs > 227 * 1024) return fail(SR_EUNSUPPORTED, "lattice too large for one CTA's shared memory (%zu bytes)", f->smem_rhs);
-    if (precision == SR_FP64) {
-        CK(cudaFuncSetAttribute(k_gamma_rhs<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->smem_rhs));
-        CK(cudaFuncSetAttribute(k_gamma_rhs<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->smem_rhs));
+    if (f->ntan) {
+        CK(ensure_smem((const void*)k_gamma_rhs<DualT, 2>, f->smem_rhs));
+        CK(ensure_smem((const void*)k_gamma_rhs<DualT, 4>, f->smem_rhs));
+    } else if (precision == SR_FP64) {
+        CK(ensure_smem((const void*)k_gamma_rhs<double, 2>, f->smem_rhs));
+        CK(ensure_smem((const void*)k_gamma_rhs<double, 4>, f->smem_rhs));
     } else {
-        CK(cudaFuncSetAttribute(k_gamma_rhs_f32<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->smem_rhs));
-        CK(cudaFuncSetAttribute(k_gamma_rhs_f32<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->smem_rhs));
-        CK(cudaFuncSetAttribute(k_gamma_rhs_f32<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->smem_rhs));
+        CK(ensure_smem((const void*)k_gamma_rhs_f32<2, true>, f->smem_rhs));
+        CK(ensure_smem((const void*)k_gamma_rhs_f32<2, false>, f->smem_rhs));
+        CK(ensure_smem((const void*)k_gamma_rhs_f32<4, false>, f->smem_rhs));
     }
     CK(cudaStreamSynchronize(st));
     *out = f.release();
+    return SR_OK;
+}
+
+extern "C" sr_status sr_flow_init(const sr_lattice* lat, int n_freq, const double* freq_pos, double lambda_init,
+                                  sr_precision precision, void* cuda_stream, sr_flow** out) {
+    return flow_create(lat, n_freq, freq_pos, lambda_init, precision, cuda_stream, 0, nullptr, out);
+}
+
+extern "C" sr_status sr_flow_init_tangent(const sr_lattice* lat, int n_freq, const double* freq_pos, double lambda_init,
+                                          int n_par, const double* dM, void* cuda_stream, sr_flow** out) {
+    if (n_par < 1 || n_par > kTan || !dM) return fail(SR_EINVAL, "n_par must be in [1, %d] with derivative couplings given", kTan);
+    return flow_create(lat, n_freq, freq_pos, lambda_init, SR_FP64, cuda_stream, n_par, dM, out);
+}
+
+extern "C" sr_status sr_flow_tangents(const sr_flow* f, int* n_tangent) {
+    if (!f || !n_tangent) return fail(SR_EINVAL, "null argument");
+    *n_tangent = f->ntan;
     return SR_OK;
 }
 
@@ -1142,8 +1306,8 @@ extern "C" sr_status sr_flow_rhs(sr_flow* f, double lambda, double* d_dsigma, do
     if (!f) return fail(SR_EINVAL, "null flow");
     if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(SR_EINVAL, "lambda must be positive");
     if (sr_status s = run_rhs(f, lambda, f->gam.p, f->G.p, f->Gf.p, f->dgam.p, f->dG.p)) return s;
-    if (d_dsigma) CK(cudaMemcpyAsync(d_dsigma, f->dgam.p, sizeof(double) * f->g.N, cudaMemcpyDeviceToDevice, f->stream));
-    if (d_dgamma) CK(cudaMemcpyAsync(d_dgamma, f->dG.p, sizeof(double) * f->g.nent, cudaMemcpyDeviceToDevice, f->stream));
+    if (d_dsigma) CK(cudaMemcpyAsync(d_dsigma, f->dgam.p, sizeof(double) * f->g.N * f->ts, cudaMemcpyDeviceToDevice, f->stream));
+    if (d_dgamma) CK(cudaMemcpyAsync(d_dgamma, f->dG.p, sizeof(double) * f->g.nent * f->ts, cudaMemcpyDeviceToDevice, f->stream));
     return SR_OK;
 }
 
@@ -1160,8 +1324,9 @@ static sr_status euler_step(sr_flow* f, double lam_next) {
     const double dl = f->lambda - lam_next;
     if (sr_status s = run_rhs(f, f->lambda, f->gam.p, f->G.p, f->Gf.p, f->dgam.p, f->dG.p)) return s;
     CK(cudaMemsetAsync(f->flag.p, 0, sizeof(int), f->stream));
-    k_axpy<<<1, 256, 0, f->stream>>>(g.N, f->gam.p, f->dgam.p, -dl, f->flag.p);
-    k_axpy<<<(unsigned)((g.nent + 255) / 256), 256, 0, f->stream>>>(g.nent, f->G.p, f->dG.p, -dl, f->flag.p);
+    const long nG = g.nent * f->ts;
+    k_axpy<<<1, 256, 0, f->stream>>>((long)g.N * f->ts, f->gam.p, f->dgam.p, -dl, f->flag.p);
+    k_axpy<<<(unsigned)((nG + 255) / 256), 256, 0, f->stream>>>(nG, f->G.p, f->dG.p, -dl, f->flag.p);
     CK(cudaGetLastError());
     if (sr_status s = refresh_shadow(f, f->G.p, f->Gf.p)) return s;
     if (sr_status s = check_flag(f, lam_next)) return s;
@@ -1202,6 +1367,14 @@ static sr_status dp54_step(sr_flow* f, double h, double rtol, double atol) {
     for (int s = 0; s < 7; ++s) {
         const double* sg = f->y0g.p;
         const double* sG = f->y0G.p;
+        if (s == 0 && f->fsal) {
+            // first-same-as-last: the last stage of the previous accepted step is this step's first
+            std::swap(f->kg[0].p, f->kg[6].p);
+            std::swap(f->kG[0].p, f->kG[6].p);
+            pg.k[0] = f->kg[0].p; pg.k[6] = f->kg[6].p;
+            pG.k[0] = f->kG[0].p; pG.k[6] = f->kG[6].p;
+            continue;
+        }
         if (s > 0) {
             k_rk_stage<<<1, 256, 0, st>>>(g.N, f->y0g.p, pg, s, A[s][0], A[s][1], A[s][2], A[s][3], A[s][4], A[s][5], h, f->stg.p);
             k_rk_stage<<<bG, 256, 0, st>>>(g.nent, f->y0G.p, pG, s, A[s][0], A[s][1], A[s][2], A[s][3], A[s][4], A[s][5], h, f->stG.p);
@@ -1212,19 +1385,21 @@ static sr_status dp54_step(sr_flow* f, double h, double rtol, double atol) {
         if (sr_status e = refresh_shadow(f, sG, f->Gf.p)) return e;
         if (sr_status e = run_rhs(f, f->lambda + C[s] * h, sg, sG, f->Gf.p, f->kg[s].p, f->kG[s].p)) return e;
     }
-    CK(cudaMemsetAsync(f->errbits.p, 0, sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(f->errbits.p, 0, 2 * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(f->flag.p, 0, sizeof(int), st));
-    k_rk_final<<<1, 256, 0, st>>>(g.N, f->y0g.p, pg, h, rtol, atol, f->gam.p, f->errbits.p, f->flag.p);
-    k_rk_final<<<bG, 256, 0, st>>>(g.nent, f->y0G.p, pG, h, rtol, atol, f->G.p, f->errbits.p, f->flag.p);
+    k_rk_final<<<1, 256, 0, st>>>(g.N, f->y0g.p, pg, h, f->gam.p, f->errbits.p, f->flag.p);
+    k_rk_final<<<bG, 256, 0, st>>>(g.nent, f->y0G.p, pG, h, f->G.p, f->errbits.p, f->flag.p);
     CK(cudaGetLastError());
-    unsigned long long eb = 0;
+    unsigned long long eb[2] = {0, 0};
     int fl = 0;
-    CK(cudaMemcpyAsync(&eb, f->errbits.p, sizeof(eb), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(eb, f->errbits.p, sizeof(eb), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&fl, f->flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    double err;
-    std::memcpy(&err, &eb, sizeof(err));
-    f->last_err = err;
+    double emax, ymax;
+    std::memcpy(&emax, &eb[0], sizeof(double));
+    std::memcpy(&ymax, &eb[1], sizeof(double));
+    // normwise scaled error: max_i |e_i| / (atol + rtol max_i max(|y0_i|, |y_new_i|))
+    f->last_err = emax / (atol + rtol * ymax);
     if (fl) return fail(SR_ENONFINITE, "non-finite value in a Dormand-Prince step at Lambda = %.17g", f->lambda);
     return SR_OK;
 }
@@ -1240,24 +1415,33 @@ extern "C" sr_status sr_flow_step(sr_flow* f, double lambda_next, int method, do
     if (!f) return fail(SR_EINVAL, "null flow");
     if (!(lambda_next > 0.0) || !(lambda_next < f->lambda)) return fail(SR_EINVAL, "lambda_next must lie in (0, lambda)");
     if (method == SR_EULER) {
+        f->fsal = false;
         if (sr_status s = euler_step(f, lambda_next)) return s;
+    } else if (f->ntan) {
+        return fail(SR_EUNSUPPORTED, "tangent flows step with SR_EULER only");
     } else if (method == SR_RK_FIXED) {
-        if (sr_status s = dp54_step(f, lambda_next - f->lambda, rtol, atol)) return s;
+        if (sr_status s = dp54_step(f, lambda_next - f->lambda, rtol, atol)) { f->fsal = false; return s; }
         if (sr_status s = refresh_shadow(f, f->G.p, f->Gf.p)) return s;
         f->lambda = lambda_next;
+        f->fsal = true;
         f->n_accept++;
     } else if (method == SR_RK_ADAPTIVE) {
         if (!(rtol > 0.0) || !(atol >= 0.0)) return fail(SR_EINVAL, "rtol must be positive and atol non-negative");
         double h = f->h_next < 0.0 ? f->h_next : (lambda_next - f->lambda);
-        int guard = 0;
+        long guard = 0;
         while (f->lambda > lambda_next) {
-            if (++guard > 100000) return fail(SR_ETIMEOUT, "adaptive stepping did not reach lambda_next");
+            if (++guard > f->step_limit) {
+                if (reached) *reached = f->lambda;
+                return fail(SR_ETIMEOUT, "adaptive stepping stopped at Lambda = %.17g after %ld attempted steps",
+                            f->lambda, f->step_limit);
+            }
             if (f->lambda + h < lambda_next) h = lambda_next - f->lambda;
             sr_status s = dp54_step(f, h, rtol, atol);
             if (s != SR_OK && s != SR_ENONFINITE) return s;
             double err = s == SR_ENONFINITE ? INFINITY : f->last_err;
             double fac = err == 0.0 ? 5.0 : 0.9 * std::pow(err, -0.2);
             if (err <= 1.0) {
+                f->fsal = true;
                 f->lambda += h;
                 if (std::fabs(f->lambda - lambda_next) <= 1e-14 * std::fabs(lambda_next)) f->lambda = lambda_next;
                 if (sr_status e = refresh_shadow(f, f->G.p, f->Gf.p)) return e;
@@ -1266,6 +1450,11 @@ extern "C" sr_status sr_flow_step(sr_flow* f, double lambda_next, int method, do
                 f->h_next = h;
             } else {
                 if (sr_status e = restore_y0(f)) return e;
+                // the first stage (the right-hand side at the step's start) stays valid: park it
+                // where the next attempt's first-same-as-last exchange picks it up
+                std::swap(f->kg[0].p, f->kg[6].p);
+                std::swap(f->kG[0].p, f->kG[6].p);
+                f->fsal = true;
                 f->n_reject++;
                 h *= std::max(0.2, std::min(1.0, fac));
                 if (std::fabs(h) < 1e-14 * f->lambda) return fail(SR_ENONFINITE, "step size underflow at Lambda = %.17g", f->lambda);
@@ -1278,6 +1467,12 @@ extern "C" sr_status sr_flow_step(sr_flow* f, double lambda_next, int method, do
     return SR_OK;
 }
 
+extern "C" sr_status sr_flow_set_step_limit(sr_flow* f, long max_steps) {
+    if (!f || max_steps <= 0) return fail(SR_EINVAL, "step limit must be positive");
+    f->step_limit = max_steps;
+    return SR_OK;
+}
+
 extern "C" sr_status sr_flow_stats(const sr_flow* f, double* last_err, long* n_rhs, long* n_accept, long* n_reject) {
     if (!f) return fail(SR_EINVAL, "null flow");
     if (last_err) *last_err = f->last_err;
@@ -1287,28 +1482,462 @@ extern "C" sr_status sr_flow_stats(const sr_flow* f, double* last_err, long* n_r
     return SR_OK;
 }
 
+extern "C" sr_status sr_measure_susceptibility_tangent(sr_flow* f, int n_k, const double* k_xyz, double* chi_k,
+                                                      double* dchi_k) {
+    if (!f || n_k <= 0 || !k_xyz || !chi_k || !dchi_k) return fail(SR_EINVAL, "bad arguments");
+    if (!f->ntan) return fail(SR_EINVAL, "not a tangent flow (sr_flow_init_tangent)");
+    const sr_lattice* lat = f->lat;
+    const Geo& g = f->g;
+    const int npairs = (int)lat->chi_map.size();
+    Tabs tb = f->tabs();
+    DualT* chi = reinterpret_cast<DualT*>(f->chi.p);
+    if (g.nc == 2)
+        k_chi<DualT, 2><<<npairs, 128, 0, f->stream>>>(g, tb, f->w.p, reinterpret_cast<const DualT*>(f->gam.p),
+                                                        reinterpret_cast<const DualT*>(f->G.p), f->lambda, f->chi_map.p,
+                                                        f->chi_onsite.p, lat->Ntot, chi);
+    else
+        k_chi<DualT, 4><<<npairs, 128, 0, f->stream>>>(g, tb, f->w.p, reinterpret_cast<const DualT*>(f->gam.p),
+                                                        reinterpret_cast<const DualT*>(f->G.p), f->lambda, f->chi_map.p,
+                                                        f->chi_onsite.p, lat->Ntot, chi);
+    CK(cudaGetLastError());
+    if (f->kbuf.n < (size_t)3 * n_k) CK(f->kbuf.alloc((size_t)3 * n_k));
+    if (f->chik.n < (size_t)n_k * f->ts) CK(f->chik.alloc((size_t)n_k * f->ts));
+    CK(cudaMemcpyAsync(f->kbuf.p, k_xyz, sizeof(double) * 3 * n_k, cudaMemcpyHostToDevice, f->stream));
+    k_chi_k<DualT><<<(n_k + 127) / 128, 128, 0, f->stream>>>(n_k, f->kbuf.p, chi, f->chi_dr.p, npairs, lat->nb, g.nc,
+                                                             reinterpret_cast<DualT*>(f->chik.p));
+    CK(cudaGetLastError());
+    std::vector<double> h((size_t)n_k * f->ts);
+    CK(cudaMemcpyAsync(h.data(), f->chik.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, f->stream));
+    CK(cudaStreamSynchronize(f->stream));
+    for (int i = 0; i < n_k; ++i) {
+        chi_k[i] = h[(size_t)i * f->ts];
+        for (int p = 0; p < f->ntan; ++p) dchi_k[(size_t)i * f->ntan + p] = h[(size_t)i * f->ts + 1 + p];
+    }
+    return SR_OK;
+}
+
 extern "C" sr_status sr_measure_susceptibility(sr_flow* f, int n_k, const double* k_xyz, double* chi_k, double* chi_ij) {
     if (!f) return fail(SR_EINVAL, "null flow");
+    if (f->ntan) return fail(SR_EINVAL, "tangent flows measure with sr_measure_susceptibility_tangent");
     if (n_k < 0 || (n_k > 0 && chi_k && !k_xyz)) return fail(SR_EINVAL, "bad momenta");
     const sr_lattice* lat = f->lat;
     const Geo& g = f->g;
     const int npairs = (int)lat->chi_map.size();
     Tabs tb = f->tabs();
     if (g.nc == 2)
-        k_chi<2><<<npairs, 128, 0, f->stream>>>(g, tb, f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_map.p, f->chi_onsite.p, lat->Ntot, f->chi.p);
+        k_chi<double, 2><<<npairs, 128, 0, f->stream>>>(g, tb, f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_map.p, f->chi_onsite.p, lat->Ntot, f->chi.p);
     else
-        k_chi<4><<<npairs, 128, 0, f->stream>>>(g, tb, f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_map.p, f->chi_onsite.p, lat->Ntot, f->chi.p);
+        k_chi<double, 4><<<npairs, 128, 0, f->stream>>>(g, tb, f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_map.p, f->chi_onsite.p, lat->Ntot, f->chi.p);
     CK(cudaGetLastError());
     if (chi_ij) CK(cudaMemcpyAsync(chi_ij, f->chi.p, sizeof(double) * npairs * g.nc, cudaMemcpyDeviceToDevice, f->stream));
     if (chi_k && n_k > 0) {
         if (f->kbuf.n < (size_t)3 * n_k) CK(f->kbuf.alloc((size_t)3 * n_k));
         if (f->chik.n < (size_t)n_k) CK(f->chik.alloc(n_k));
         CK(cudaMemcpyAsync(f->kbuf.p, k_xyz, sizeof(double) * 3 * n_k, cudaMemcpyHostToDevice, f->stream));
-        k_chi_k<<<(n_k + 127) / 128, 128, 0, f->stream>>>(n_k, f->kbuf.p, f->chi.p, f->chi_dr.p, npairs, lat->nb, g.nc, f->chik.p);
+        k_chi_k<double><<<(n_k + 127) / 128, 128, 0, f->stream>>>(n_k, f->kbuf.p, f->chi.p, f->chi_dr.p, npairs, lat->nb, g.nc, f->chik.p);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(chi_k, f->chik.p, sizeof(double) * n_k, cudaMemcpyDeviceToHost, f->stream));
         CK(cudaStreamSynchronize(f->stream));
     }
+    return SR_OK;
+}
+
+
+// ----------------------------------------------------------------------------- batched flows
+//
+// Many flows (instances of uneven size) integrated together: every kernel of an Euler step
+// covers all instances in one launch (blockIdx.y = instance for the small kernels); the
+// vertex flow is one persistent kernel whose CTAs pull (instance, stored triple) units from
+// an atomic counter, largest instances first.  The cutoff of step k is read on the device
+// from a list, so one captured CUDA graph of the step replays the whole loop.
+
+namespace {
+
+struct BInst {
+    Geo g;
+    Tabs tb;
+    double* gam;
+    double* G;
+    float* Gf;
+    const float* Gs;
+    double* dgam;
+    double* dG;
+    double* nx;
+    double* nW;
+    float* nWf;
+    float* nxf;
+    int* ncount;
+    long unit0;     // first work unit (stored triple) of this instance
+    int qc;         // integration nodes per shared-memory block
+    int kind;       // 0 SU2 dense, 1 SU2 product list, 2 XYZ
+    int with_swap;
+};
+
+__global__ void k_sigma_b(const BInst* __restrict__ I, const double* __restrict__ lams, const int* __restrict__ step) {
+    const BInst& B = I[blockIdx.y];
+    if ((int)blockIdx.x >= B.g.N) return;
+    sigma_rhs_block<double>(B.g, B.tb, B.tb.w, B.gam, B.G, lams[*step], B.dgam, blockIdx.x);
+}
+
+__global__ void k_nodes_b(const BInst* __restrict__ I, const double* __restrict__ lams, const int* __restrict__ step) {
+    const BInst& B = I[blockIdx.y];
+    if ((int)blockIdx.x >= 3 * B.g.N) return;
+    channel_nodes_block<double>(B.g, B.tb.w, B.tb.invh, B.gam, B.dgam, lams[*step], B.nx, B.nW, B.nWf, B.ncount, blockIdx.x,
+                                B.nxf);
+}
+
+// One size class of instances: units [u_begin, u_end) (instances [i_begin, i_end)).
+__global__ void __launch_bounds__(kThreads) k_gamma_persistent(const BInst* __restrict__ I, int i_begin, int i_end,
+                                                               long u_begin, long u_end,
+                                                               unsigned long long* __restrict__ counter) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long unit_sh;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) unit_sh = u_begin + (long)atomicAdd(counter, 1ULL);
+        __syncthreads();
+        const long u = unit_sh;
+        if (u >= u_end) break;
+        int lo = i_begin, hi = i_end - 1;   // last instance with unit0 <= u
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (I[mid].unit0 <= u) lo = mid; else hi = mid - 1;
+        }
+        const BInst& B = I[lo];
+        const long local = u - B.unit0;
+        const int p = (int)(local / B.g.N), ti = (int)(local % B.g.N);
+        if (B.kind == 0)
+            gamma_rhs_f32_triple<2, true>(B.g, B.tb, B.Gf, B.Gs, B.nxf, B.nWf, B.ncount, B.dG, p, ti, smem, B.qc);
+        else if (B.kind == 1)
+            gamma_rhs_f32_triple<2, false>(B.g, B.tb, B.Gf, B.Gs, B.nxf, B.nWf, B.ncount, B.dG, p, ti, smem, B.qc);
+        else
+            gamma_rhs_f32_triple<4, false>(B.g, B.tb, B.Gf, B.Gs, B.nxf, B.nWf, B.ncount, B.dG, p, ti, smem, B.qc);
+    }
+}
+
+// Euler update of every instance (y <- y - (Lambda_k - Lambda_k+1) f) and its FP32 shadow.
+__global__ void k_update_b(const BInst* __restrict__ I, const double* __restrict__ lams, const int* __restrict__ step,
+                           int* __restrict__ flag) {
+    const BInst& B = I[blockIdx.y];
+    const double dl = lams[*step] - lams[*step + 1];
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < B.g.N; i += stride) {
+        const double v = B.gam[i] - dl * B.dgam[i];
+        if (!isfinite(v)) atomicOr(flag, 1);
+        B.gam[i] = v;
+    }
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < B.g.nent; i += stride) {
+        const double v = B.G[i] - dl * B.dG[i];
+        if (!isfinite(v)) atomicOr(flag, 1);
+        B.G[i] = v;
+    }
+}
+
+__global__ void k_shadow_b(const BInst* __restrict__ I) {
+    const BInst& B = I[blockIdx.y];
+    const Geo& g = B.g;
+    const int rowp = g.nc * g.nsp;
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.nentp; i += stride) {
+        const long pt = i / rowp;
+        const int rem = (int)(i % rowp);
+        const int c = rem / g.nsp, r = rem % g.nsp;
+        const double* src = B.G + pt * g.nc * g.Ns;
+        float v = 0.0f, vs = 0.0f;
+        if (r < g.Ns) {
+            v = (float)src[c * g.Ns + r];
+            if (B.with_swap) vs = (float)src[perm_of(B.tb.swap_perm[r], c) * g.Ns + B.tb.swap_r[r]];
+        }
+        B.Gf[i] = v;
+        if (B.with_swap) B.Gf[g.nentp + i] = vs;
+    }
+}
+
+__global__ void k_advance(int* __restrict__ step, unsigned long long* __restrict__ counter, int ncounter) {
+    *step += 1;
+    for (int i = 0; i < ncounter; ++i) counter[i] = 0ULL;
+}
+
+}  // namespace
+
+struct BClass {
+    int i_begin, i_end;   // instances
+    long u_begin, u_end;  // work units
+    size_t smem;
+    int occ, ctas, qc;
+    double ms;            // autotuned vertex-flow time of the class
+};
+
+struct sr_batch {
+    std::vector<sr_flow*> flows;
+    std::vector<BInst> inst;         // host copy, grouped in shared-memory classes, largest first
+    std::vector<BClass> cls;
+    DevBuf<BInst> dinst;
+    DevBuf<double> lams;
+    DevBuf<int> step;
+    DevBuf<unsigned long long> counter;
+    DevBuf<int> flag;
+    cudaStream_t stream = nullptr;
+    long total = 0;
+    size_t smem = 0;
+    int nsm = 0, occ = 1, ctas = 1, qc = kQF;
+    double tune_ms = 0.0;
+    double run_ms = 0.0;
+    int n_lambda_cap = 0;
+    ~sr_batch() { if (stream) cudaStreamDestroy(stream); }
+};
+
+static void launch_class(sr_batch* b, int k) {
+    const BClass& c = b->cls[k];
+    k_gamma_persistent<<<b->nsm * c.ctas, kThreads, c.smem, b->stream>>>(b->dinst.p, c.i_begin, c.i_end, c.u_begin,
+                                                                          c.u_end, b->counter.p + k);
+}
+
+static sr_status batch_launch_step(sr_batch* b) {
+    const int ni = (int)b->inst.size();
+    int maxN = 0;
+    long maxent = 0;
+    for (const BInst& B : b->inst) { maxN = std::max(maxN, B.g.N); maxent = std::max(maxent, B.g.nentp); }
+    k_sigma_b<<<dim3(maxN, ni), 64, 0, b->stream>>>(b->dinst.p, b->lams.p, b->step.p);
+    k_nodes_b<<<dim3(3 * maxN, ni), 128, 0, b->stream>>>(b->dinst.p, b->lams.p, b->step.p);
+    for (int k = 0; k < (int)b->cls.size(); ++k) launch_class(b, k);
+    const int ub = (int)std::min<long>((maxent + 255) / 256, 4 * b->nsm);
+    k_update_b<<<dim3(ub, ni), 256, 0, b->stream>>>(b->dinst.p, b->lams.p, b->step.p, b->flag.p);
+    k_shadow_b<<<dim3(ub, ni), 256, 0, b->stream>>>(b->dinst.p);
+    k_advance<<<1, 1, 0, b->stream>>>(b->step.p, b->counter.p, (int)b->cls.size());
+    CK(cudaGetLastError());
+    return SR_OK;
+}
+
+static sr_status batch_upload(sr_batch* b) {
+    CK(cudaMemcpyAsync(b->dinst.p, b->inst.data(), sizeof(BInst) * b->inst.size(), cudaMemcpyHostToDevice, b->stream));
+    return SR_OK;
+}
+
+// Time the vertex flow of one size class (its persistent kernel alone).
+static sr_status batch_time_class(sr_batch* b, int k, double* ms) {
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+        CK(cudaMemsetAsync(b->counter.p + k, 0, sizeof(unsigned long long), b->stream));
+        CK(cudaEventRecord(e0, b->stream));
+        launch_class(b, k);
+        CK(cudaGetLastError());
+        CK(cudaEventRecord(e1, b->stream));
+        CK(cudaEventSynchronize(e1));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, e0, e1));
+        best = std::min(best, t);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = best;
+    return SR_OK;
+}
+
+// Autotuner: per size class, the node-block size and the CTAs per SM of its persistent
+// kernel, each candidate timed on the current state and node tables; the fastest is kept.
+static sr_status batch_tune(sr_batch* b) {
+    const int qcs[3] = {8, 16, 32};
+    double total = 0.0;
+    for (int k = 0; k < (int)b->cls.size(); ++k) {
+        BClass& c = b->cls[k];
+        std::vector<int> ctas_c;
+        for (int v = c.occ; v >= 1; v = v / 2) { ctas_c.push_back(v); if (v == 1) break; }
+        double best = 1e300;
+        int bq = c.qc, bc = c.ctas;
+        for (int qc : qcs)
+            for (int ct : ctas_c) {
+                for (int i = c.i_begin; i < c.i_end; ++i) b->inst[i].qc = qc;
+                c.ctas = ct;
+                if (sr_status s = batch_upload(b)) return s;
+                double ms = 0;
+                if (sr_status s = batch_time_class(b, k, &ms)) return s;
+                if (ms < best) { best = ms; bq = qc; bc = ct; }
+            }
+        for (int i = c.i_begin; i < c.i_end; ++i) b->inst[i].qc = bq;
+        c.ctas = bc;
+        c.qc = bq;
+        c.ms = best;
+        total += best;
+    }
+    b->tune_ms = total;
+    b->qc = b->cls.empty() ? kQF : b->cls[0].qc;
+    b->ctas = b->cls.empty() ? 1 : b->cls[0].ctas;
+    return batch_upload(b);
+}
+
+extern "C" sr_status sr_batch_create(int n, sr_flow* const* flows, sr_batch** out) {
+    if (n <= 0 || !flows || !out) return fail(SR_EINVAL, "need at least one flow");
+    *out = nullptr;
+    std::unique_ptr<sr_batch> b(new (std::nothrow) sr_batch());
+    if (!b) return fail(SR_ENOMEM, "out of host memory");
+    for (int i = 0; i < n; ++i) {
+        sr_flow* f = flows[i];
+        if (!f) return fail(SR_EINVAL, "null flow %d", i);
+        if (f->prec != SR_FP32_MIXED) return fail(SR_EUNSUPPORTED, "batched flows use the FP32-mixed kernels (flow %d is FP64)", i);
+        b->flows.push_back(f);
+    }
+    // instances grouped by the shared memory their vertex flow needs (each class gets a
+    // persistent launch sized for it), largest first; within a class, largest instance first
+    std::vector<size_t> sm(n);
+    for (int i = 0; i < n; ++i)
+        sm[i] = f32_smem_bytes(flows[i]->g.Ns, flows[i]->g.nsp, flows[i]->g.nc, flows[i]->nprod, flows[i]->dense);
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        if (sm[a] != sm[c]) return sm[a] > sm[c];
+        return flows[a]->g.nent > flows[c]->g.nent;
+    });
+    long unit = 0;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev));
+    for (int idx = 0; idx < n; ++idx) {
+        const int k = order[idx];
+        sr_flow* f = flows[k];
+        // a new class when the shared memory drops below 2/3 of the class's largest
+        if (b->cls.empty() || sm[k] * 3 < b->cls.back().smem * 2) {
+            BClass c{};
+            c.i_begin = idx; c.u_begin = unit; c.smem = sm[k]; c.qc = kQF;
+            if (sm[k] > 227 * 1024) return fail(SR_EUNSUPPORTED, "instance needs %zu bytes of shared memory", sm[k]);
+            CK(ensure_smem((const void*)k_gamma_persistent, sm[k]));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, k_gamma_persistent, kThreads, sm[k]));
+            if (c.occ < 1) return fail(SR_EUNSUPPORTED, "persistent kernel cannot be resident with %zu bytes", sm[k]);
+            c.ctas = c.occ;
+            b->cls.push_back(c);
+        }
+        BInst B;
+        B.g = f->g;
+        B.tb = f->tabs();
+        B.gam = f->gam.p; B.G = f->G.p; B.Gf = f->Gf.p; B.Gs = f->has_swap ? f->Gf.p + f->g.nentp : f->Gf.p;
+        B.dgam = f->dgam.p; B.dG = f->dG.p; B.nx = f->nx.p; B.nW = f->nW.p; B.nWf = f->nWf.p; B.nxf = f->nxf.p;
+        B.ncount = f->ncount.p;
+        B.unit0 = unit;
+        B.qc = kQF;
+        B.kind = f->g.nc == 4 ? 2 : (f->dense ? 0 : 1);
+        B.with_swap = f->has_swap ? 1 : 0;
+        unit += (long)f->g.npair * f->g.N;
+        b->inst.push_back(B);
+        b->cls.back().i_end = idx + 1;
+        b->cls.back().u_end = unit;
+    }
+    b->total = unit;
+    b->smem = b->cls.front().smem;
+    b->occ = b->cls.front().occ;
+    b->ctas = b->occ;
+    CK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+    CK(b->dinst.alloc(b->inst.size()));
+    CK(b->step.alloc(1));
+    CK(b->counter.alloc(b->cls.size()));
+    CK(cudaMemsetAsync(b->counter.p, 0, sizeof(unsigned long long) * b->cls.size(), b->stream));
+    CK(b->flag.alloc(1));
+    if (sr_status s = batch_upload(b.get())) return s;
+    CK(cudaStreamSynchronize(b->stream));
+    *out = b.release();
+    return SR_OK;
+}
+
+extern "C" sr_status sr_batch_run(sr_batch* b, int n_lambda, const double* lambdas, int use_graph, int autotune) {
+    if (!b || n_lambda < 2 || !lambdas) return fail(SR_EINVAL, "need a batch and at least two cutoffs");
+    for (int i = 0; i + 1 < n_lambda; ++i)
+        if (!(lambdas[i + 1] < lambdas[i]) || !(lambdas[i + 1] > 0.0)) return fail(SR_EINVAL, "cutoffs must decrease and stay positive");
+    for (sr_flow* f : b->flows) {
+        if (std::fabs(f->lambda - lambdas[0]) > 1e-12 * lambdas[0]) return fail(SR_EINVAL, "every flow must start at lambdas[0]");
+        CK(cudaStreamSynchronize(f->stream));
+    }
+    if (b->n_lambda_cap < n_lambda) { CK(b->lams.alloc(n_lambda)); b->n_lambda_cap = n_lambda; }
+    CK(cudaMemcpyAsync(b->lams.p, lambdas, sizeof(double) * n_lambda, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemsetAsync(b->step.p, 0, sizeof(int), b->stream));
+    CK(cudaMemsetAsync(b->counter.p, 0, sizeof(unsigned long long) * b->cls.size(), b->stream));
+    CK(cudaMemsetAsync(b->flag.p, 0, sizeof(int), b->stream));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int nsteps = n_lambda - 1;
+    int done = 0;
+    if (autotune) {
+        // tune on the node tables of the first step (self-energy flow and nodes of step 0),
+        // then run that step untimed with the chosen configuration
+        const int ni = (int)b->inst.size();
+        int maxN = 0;
+        for (const BInst& B : b->inst) maxN = std::max(maxN, B.g.N);
+        k_sigma_b<<<dim3(maxN, ni), 64, 0, b->stream>>>(b->dinst.p, b->lams.p, b->step.p);
+        k_nodes_b<<<dim3(3 * maxN, ni), 128, 0, b->stream>>>(b->dinst.p, b->lams.p, b->step.p);
+        CK(cudaGetLastError());
+        if (sr_status s = batch_tune(b)) return s;
+    }
+    CK(cudaEventRecord(e0, b->stream));
+    if (use_graph) {
+        cudaGraph_t graph;
+        cudaGraphExec_t exec;
+        CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        sr_status s = batch_launch_step(b);
+        cudaError_t ce = cudaStreamEndCapture(b->stream, &graph);
+        if (s != SR_OK) return s;
+        if (ce != cudaSuccess) return fail(SR_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+        CK(cudaGraphInstantiate(&exec, graph, 0));
+        for (; done < nsteps; ++done) CK(cudaGraphLaunch(exec, b->stream));
+        CK(cudaStreamSynchronize(b->stream));
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+    } else {
+        for (; done < nsteps; ++done)
+            if (sr_status s = batch_launch_step(b)) return s;
+    }
+    CK(cudaEventRecord(e1, b->stream));
+    CK(cudaEventSynchronize(e1));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, e0, e1));
+    b->run_ms = t;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int fl = 0;
+    CK(cudaMemcpy(&fl, b->flag.p, sizeof(int), cudaMemcpyDeviceToHost));
+    for (sr_flow* f : b->flows) {
+        f->lambda = lambdas[n_lambda - 1];
+        f->fsal = false;
+        f->n_rhs += nsteps;
+    }
+    if (fl) return fail(SR_ENONFINITE, "non-finite value in a batched flow");
+    return SR_OK;
+}
+
+extern "C" sr_status sr_batch_info(const sr_batch* b, int* qc, int* ctas_per_sm, double* tune_ms, double* run_ms,
+                                   long* units) {
+    if (!b) return fail(SR_EINVAL, "null batch");
+    if (qc) *qc = b->qc;
+    if (ctas_per_sm) *ctas_per_sm = b->ctas;
+    if (tune_ms) *tune_ms = b->tune_ms;
+    if (run_ms) *run_ms = b->run_ms;
+    if (units) *units = b->total;
+    return SR_OK;
+}
+
+extern "C" sr_status sr_batch_classes(const sr_batch* b, int* n_classes) {
+    if (!b || !n_classes) return fail(SR_EINVAL, "null argument");
+    *n_classes = (int)b->cls.size();
+    return SR_OK;
+}
+
+extern "C" sr_status sr_batch_class(const sr_batch* b, int k, int* n_instances, long* units, int* smem_bytes, int* qc,
+                                    int* ctas_per_sm, double* tune_ms) {
+    if (!b || k < 0 || k >= (int)b->cls.size()) return fail(SR_EINVAL, "bad class index");
+    const BClass& c = b->cls[k];
+    if (n_instances) *n_instances = c.i_end - c.i_begin;
+    if (units) *units = c.u_end - c.u_begin;
+    if (smem_bytes) *smem_bytes = (int)c.smem;
+    if (qc) *qc = c.qc;
+    if (ctas_per_sm) *ctas_per_sm = c.ctas;
+    if (tune_ms) *tune_ms = c.ms;
+    return SR_OK;
+}
+
+extern "C" sr_status sr_batch_destroy(sr_batch* b) {
+    if (b && b->stream) cudaStreamSynchronize(b->stream);
+    delete b;
     return SR_OK;
 }
 
@@ -1323,6 +1952,7 @@ static double* g_chi_static_ptr[64] = {nullptr};
 
 extern "C" sr_status sr_measure_susceptibility_static(sr_flow* f, int n_k, const double* d_k_xyz, double* d_chi_k) {
     if (!f) return fail(SR_EINVAL, "null flow");
+    if (f->ntan) return fail(SR_EINVAL, "tangent flows measure with sr_measure_susceptibility_tangent");
     if (n_k < 0 || (n_k > 0 && (!d_k_xyz || !d_chi_k))) return fail(SR_EINVAL, "bad momenta or output");
     const sr_lattice* lat = f->lat;
     const Geo& g = f->g;
@@ -1345,12 +1975,12 @@ extern "C" sr_status sr_measure_susceptibility_static(sr_flow* f, int n_k, const
     }
     Tabs tb = f->tabs();
     if (g.nc == 2)
-        k_chi<2><<<npairs, 128, 0, f->stream>>>(g, tb, f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_map.p, f->chi_onsite.p, lat->Ntot, scratch);
+        k_chi<double, 2><<<npairs, 128, 0, f->stream>>>(g, tb, f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_map.p, f->chi_onsite.p, lat->Ntot, scratch);
     else
-        k_chi<4><<<npairs, 128, 0, f->stream>>>(g, tb, f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_map.p, f->chi_onsite.p, lat->Ntot, scratch);
+        k_chi<double, 4><<<npairs, 128, 0, f->stream>>>(g, tb, f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_map.p, f->chi_onsite.p, lat->Ntot, scratch);
     CK(cudaGetLastError());
     if (n_k > 0) {
-        k_chi_k<<<(n_k + 127) / 128, 128, 0, f->stream>>>(n_k, d_k_xyz, scratch, f->chi_dr.p, npairs, lat->nb, g.nc, d_chi_k);
+        k_chi_k<double><<<(n_k + 127) / 128, 128, 0, f->stream>>>(n_k, d_k_xyz, scratch, f->chi_dr.p, npairs, lat->nb, g.nc, d_chi_k);
         CK(cudaGetLastError());
     }
     return SR_OK;
@@ -1367,19 +1997,20 @@ extern "C" sr_status sr_flow_chi_sites(const sr_flow* f, int* sites) {
 
 extern "C" sr_status sr_flow_get_state(const sr_flow* f, double* d_sigma, double* d_gamma) {
     if (!f) return fail(SR_EINVAL, "null flow");
-    if (d_sigma) CK(cudaMemcpyAsync(d_sigma, f->gam.p, sizeof(double) * f->g.N, cudaMemcpyDeviceToDevice, f->stream));
-    if (d_gamma) CK(cudaMemcpyAsync(d_gamma, f->G.p, sizeof(double) * f->g.nent, cudaMemcpyDeviceToDevice, f->stream));
+    if (d_sigma) CK(cudaMemcpyAsync(d_sigma, f->gam.p, sizeof(double) * f->g.N * f->ts, cudaMemcpyDeviceToDevice, f->stream));
+    if (d_gamma) CK(cudaMemcpyAsync(d_gamma, f->G.p, sizeof(double) * f->g.nent * f->ts, cudaMemcpyDeviceToDevice, f->stream));
     return SR_OK;
 }
 
 extern "C" sr_status sr_flow_set_state(sr_flow* f, double lambda, const double* d_sigma, const double* d_gamma) {
     if (!f) return fail(SR_EINVAL, "null flow");
     if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(SR_EINVAL, "lambda must be positive");
-    if (d_sigma) CK(cudaMemcpyAsync(f->gam.p, d_sigma, sizeof(double) * f->g.N, cudaMemcpyDeviceToDevice, f->stream));
-    if (d_gamma) CK(cudaMemcpyAsync(f->G.p, d_gamma, sizeof(double) * f->g.nent, cudaMemcpyDeviceToDevice, f->stream));
+    if (d_sigma) CK(cudaMemcpyAsync(f->gam.p, d_sigma, sizeof(double) * f->g.N * f->ts, cudaMemcpyDeviceToDevice, f->stream));
+    if (d_gamma) CK(cudaMemcpyAsync(f->G.p, d_gamma, sizeof(double) * f->g.nent * f->ts, cudaMemcpyDeviceToDevice, f->stream));
     if (sr_status s = refresh_shadow(f, f->G.p, f->Gf.p)) return s;
     f->lambda = lambda;
     f->h_next = 0.0;
+    f->fsal = false;
     return SR_OK;
 }
 

@@ -47,6 +47,55 @@ struct Tabs {
     const int* dgath_idx;    // P * nc: dense-contraction index c * nsp^2 + rA * nsp + rB (SU2)
 };
 
+// Forward-mode dual number: a value and its derivatives along P parameter directions.  The
+// flow kernels are written once for a scalar type T; with T = Dual<P> every arithmetic step
+// also propagates the tangents (the tangent-linear flow), while every decision (interval,
+// sign, support) is taken on frequencies, which carry no tangent.
+template <int P>
+struct Dual {
+    double v;
+    double d[P];
+    Dual() = default;
+    __host__ __device__ Dual(double x) : v(x) {
+        for (int i = 0; i < P; ++i) d[i] = 0.0;
+    }
+};
+template <int P> __host__ __device__ inline Dual<P> operator+(const Dual<P>& a, const Dual<P>& b) {
+    Dual<P> r; r.v = a.v + b.v; for (int i = 0; i < P; ++i) r.d[i] = a.d[i] + b.d[i]; return r; }
+template <int P> __host__ __device__ inline Dual<P> operator-(const Dual<P>& a, const Dual<P>& b) {
+    Dual<P> r; r.v = a.v - b.v; for (int i = 0; i < P; ++i) r.d[i] = a.d[i] - b.d[i]; return r; }
+template <int P> __host__ __device__ inline Dual<P> operator-(const Dual<P>& a) {
+    Dual<P> r; r.v = -a.v; for (int i = 0; i < P; ++i) r.d[i] = -a.d[i]; return r; }
+template <int P> __host__ __device__ inline Dual<P> operator*(const Dual<P>& a, const Dual<P>& b) {
+    Dual<P> r; r.v = a.v * b.v; for (int i = 0; i < P; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i]; return r; }
+template <int P> __host__ __device__ inline Dual<P> operator*(double a, const Dual<P>& b) {
+    Dual<P> r; r.v = a * b.v; for (int i = 0; i < P; ++i) r.d[i] = a * b.d[i]; return r; }
+template <int P> __host__ __device__ inline Dual<P> operator*(const Dual<P>& b, double a) { return a * b; }
+template <int P> __host__ __device__ inline Dual<P> operator/(const Dual<P>& a, const Dual<P>& b) {
+    Dual<P> r; r.v = a.v / b.v; const double ib = 1.0 / b.v;
+    for (int i = 0; i < P; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * ib; return r; }
+template <int P> __host__ __device__ inline Dual<P> operator/(double a, const Dual<P>& b) { return Dual<P>(a) / b; }
+template <int P> __host__ __device__ inline Dual<P> operator/(const Dual<P>& a, double b) {
+    Dual<P> r; r.v = a.v / b; for (int i = 0; i < P; ++i) r.d[i] = a.d[i] / b; return r; }
+template <int P> __host__ __device__ inline Dual<P> operator+(double a, const Dual<P>& b) { return Dual<P>(a) + b; }
+template <int P> __host__ __device__ inline Dual<P> operator+(const Dual<P>& b, double a) { return b + Dual<P>(a); }
+template <int P> __host__ __device__ inline Dual<P> operator-(double a, const Dual<P>& b) { return Dual<P>(a) - b; }
+template <int P> __host__ __device__ inline Dual<P> operator-(const Dual<P>& b, double a) { return b - Dual<P>(a); }
+template <int P> __host__ __device__ inline Dual<P>& operator+=(Dual<P>& a, const Dual<P>& b) { a = a + b; return a; }
+template <int P> __host__ __device__ inline Dual<P>& operator-=(Dual<P>& a, const Dual<P>& b) { a = a - b; return a; }
+template <int P> __host__ __device__ inline Dual<P>& operator*=(Dual<P>& a, const Dual<P>& b) { a = a * b; return a; }
+
+__host__ __device__ inline double value_of(double x) { return x; }
+__host__ __device__ inline float value_of(float x) { return x; }
+template <int P> __host__ __device__ inline double value_of(const Dual<P>& x) { return x.v; }
+
+// Type of interpolation weights for a state scalar T (weights carry no tangent).
+template <typename T> struct WeightOf { using type = T; };
+template <int P> struct WeightOf<Dual<P>> { using type = double; };
+
+constexpr int kTan = 2;   // tangent directions of the tangent-linear flow
+using DualT = Dual<kTan>;
+
 __device__ __forceinline__ int perm_of(int packed, int c) { return (packed >> (2 * c)) & 3; }
 
 __device__ __forceinline__ int pair_index(int si, int ui) { return si * (si + 1) / 2 + ui; }
@@ -69,14 +118,15 @@ __device__ __forceinline__ void bracket(const double* __restrict__ w, const doub
 }
 
 // gamma(x), odd, linear interpolation on |x| with constant extrapolation, gamma(0) = 0.
-__device__ __forceinline__ double interp_odd(const double* __restrict__ w, const double* __restrict__ invh, int N,
-                                             const double* __restrict__ f, double x) {
-    if (x == 0.0) return 0.0;
+template <typename T>
+__device__ __forceinline__ T interp_odd(const double* __restrict__ w, const double* __restrict__ invh, int N,
+                                        const T* __restrict__ f, double x) {
+    if (x == 0.0) return T(0.0);
     double ax = fabs(x);
     int lo; double wl, wh;
     bracket(w, invh, N, ax, lo, wl, wh);
-    double v = wl * f[lo] + wh * f[lo + 1];
-    return x < 0.0 ? -v : v;
+    T v = wl * f[lo] + wh * f[lo + 1];
+    return x < 0.0 ? T(-v) : v;
 }
 
 // Lookup descriptor of Gamma(s, t, u) for one frequency triple: the symmetry relations of
@@ -137,6 +187,22 @@ __device__ __forceinline__ void axis_weights(const Tabs& tb, const Geo& g, doubl
     }
 }
 
+// FP32 version of axis_weights for an FP32 argument (the mixed-precision vertex kernel).
+__device__ __forceinline__ void axis_weights_f(const Tabs& tb, const Geo& g, float xf, int& n, int* ix, float* wx) {
+    const int N = g.N;
+    const float* w = tb.wf;
+    if (xf <= w[0]) { n = 1; ix[0] = 0; wx[0] = 1.0f; return; }
+    if (xf >= w[N - 1]) { n = 1; ix[0] = N - 1; wx[0] = 1.0f; return; }
+    int k = interval_guess(g, xf);
+    while (k > 0 && xf < w[k]) --k;
+    while (k < N - 2 && xf >= w[k + 1]) ++k;
+    const float w1 = (xf - w[k]) * tb.invhf[k];
+    if (w1 == 0.0f) { n = 1; ix[0] = k; wx[0] = 1.0f; return; }
+    n = 2; ix[0] = k; ix[1] = k + 1;
+    wx[0] = (w[k + 1] - xf) * tb.invhf[k];
+    wx[1] = w1;
+}
+
 // Descriptor of Gamma(s, t, u).  ex_slot (0 s, 1 t, 2 u; -1 none) names an argument known
 // to be the mesh frequency w[ex_idx] (or 0, clamped to w[0]), which needs no interval search.
 template <typename T>
@@ -186,22 +252,22 @@ struct __align__(16) DescF {
     int pad[3];
 };
 
-__device__ __forceinline__ void make_desc4(double s, double t, double u, int ex_slot, int ex_idx, const Tabs& tb,
+__device__ __forceinline__ void make_desc4(float s, float t, float u, int ex_slot, int ex_idx, const Tabs& tb,
                                            const Geo& g, int rowp, DescF& d) {
     int swap = 0;
-    if (t < 0.0) t = -t;
-    if (s < 0.0) { s = -s; swap ^= 1; }
-    if (u < 0.0) { u = -u; swap ^= 1; }
+    if (t < 0.0f) t = -t;
+    if (s < 0.0f) { s = -s; swap ^= 1; }
+    if (u < 0.0f) { u = -u; swap ^= 1; }
     bool flip = false;
-    if (s < u) { double tmp = s; s = u; u = tmp; flip = true; if (ex_slot != 1) ex_slot = 2 - ex_slot; }
+    if (s < u) { float tmp = s; s = u; u = tmp; flip = true; if (ex_slot != 1) ex_slot = 2 - ex_slot; }
     int ix[3][2], nx[3];
     float wx[3][2];
-    const double arg[3] = {s, t, u};
+    const float arg[3] = {s, t, u};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (a == ex_slot) { nx[a] = 1; ix[a][0] = ex_idx; wx[a][0] = 1.0f; ix[a][1] = ex_idx; wx[a][1] = 0.0f; }
         else {
-            axis_weights<float>(tb, g, arg[a], nx[a], ix[a], wx[a]);
+            axis_weights_f(tb, g, arg[a], nx[a], ix[a], wx[a]);
             if (nx[a] == 1) { ix[a][1] = ix[a][0]; wx[a][1] = 0.0f; }
         }
     }
@@ -211,12 +277,11 @@ __device__ __forceinline__ void make_desc4(double s, double t, double u, int ex_
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         int id[3];
-        float wt = 1.0f;
         id[ea] = ix[ea][0];
         const int b0 = k & 1, b1 = k >> 1;
         id[a0] = ix[a0][b0];
         id[a1] = ix[a1][b1];
-        wt = wx[a0][b0] * wx[a1][b1];
+        const float wt = wx[a0][b0] * wx[a1][b1];
         bool neg = flip;
         int p;
         if (id[0] >= id[2]) p = pair_index(id[0], id[2]);
@@ -230,13 +295,13 @@ __device__ __forceinline__ void make_desc4(double s, double t, double u, int ex_
 }
 
 // Value of component c of the pair (ref, rep_r) at the descriptor's frequencies.
-template <typename T>
-__device__ __forceinline__ T row_value(const T* __restrict__ G, const Desc<T>& d, const Tabs& tb, const Geo& g, int r, int c) {
+template <typename T, typename W>
+__device__ __forceinline__ T row_value(const T* __restrict__ G, const Desc<W>& d, const Tabs& tb, const Geo& g, int r, int c) {
     int rs = r, cs = c;
     if (d.swap) { rs = tb.swap_r[r]; cs = perm_of(tb.swap_perm[r], c); }
     const T* base = G + cs * g.Ns + rs;
-    const T* wgt = c == 0 ? d.wd : d.ws;
-    T acc = 0;
+    const W* wgt = c == 0 ? d.wd : d.ws;
+    T acc = T(0.0);
     for (int k = 0; k < d.n; ++k) acc += wgt[k] * base[d.off[k]];
     return acc;
 }

@@ -403,3 +403,67 @@ sr_status build_lattice(const sr_lattice_desc* d, sr_lattice* lat, std::string* 
 }
 
 }  // namespace sr
+
+namespace sr {
+
+namespace {
+// Coupling matrix of the pair ((0, b1), (d, b2)) with the matrices Ms (per listed interaction):
+// sum of M over interactions from the first site to the second and of M^T over the reverse.
+std::array<double, 9> pair_coupling(const sr_lattice* lat, int b1, const SiteKey& j, const double* Ms) {
+    std::array<double, 9> acc{};
+    for (size_t c = 0; c < lat->couplings.size(); ++c) {
+        const sr_coupling& cp = lat->couplings[c];
+        const double* M = Ms + 9 * c;
+        if (cp.from[3] == b1 && cp.to[3] == j.b && cp.to[0] - cp.from[0] == j.n[0] && cp.to[1] - cp.from[1] == j.n[1] &&
+            cp.to[2] - cp.from[2] == j.n[2])
+            for (int k = 0; k < 9; ++k) acc[k] += M[k];
+        if (cp.to[3] == b1 && cp.from[3] == j.b && cp.from[0] - cp.to[0] == j.n[0] && cp.from[1] - cp.to[1] == j.n[1] &&
+            cp.from[2] - cp.to[2] == j.n[2])
+            for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) acc[3 * a + b] += M[3 * b + a];
+    }
+    return acc;
+}
+}  // namespace
+
+sr_status tangent_init(const sr_lattice* lat, int npar, const double* dM, std::vector<double>* out, std::string* msg) {
+    const int nc = lat->nc, Ns = lat->Ns;
+    const size_t ncoup = lat->couplings.size();
+    out->assign((size_t)Ns * nc * npar, 0.0);
+    for (int p = 0; p < npar; ++p) {
+        const double* Ms = dM + (size_t)p * ncoup * 9;
+        std::vector<std::array<double, 9>> rep(Ns);
+        for (int r = 0; r < Ns; ++r) rep[r] = pair_coupling(lat, 0, lat->sites[lat->rep[r]], Ms);
+        for (int r = 0; r < Ns; ++r) {
+            const auto& J = rep[r];
+            for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b)
+                if (a != b && std::fabs(J[3 * a + b]) > lat->eps) { *msg = "tangent direction has off-diagonal couplings"; return SR_EUNSUPPORTED; }
+            if (nc == 2) {
+                if (std::fabs(J[0] - J[4]) > lat->eps || std::fabs(J[0] - J[8]) > lat->eps) {
+                    *msg = "tangent direction is not of Heisenberg form (SU2 core)"; return SR_EUNSUPPORTED;
+                }
+                (*out)[((size_t)r * 2 + 1) * npar + p] = J[8] / 4.0;
+            } else {
+                for (int c = 1; c < 4; ++c) (*out)[((size_t)r * 4 + c) * npar + p] = J[4 * (c - 1)] / 4.0;
+            }
+        }
+        // every pair of every basis site must carry the value of its stored image
+        for (size_t i = 0; i < lat->chi_sites.size(); ++i) {
+            const int b = (int)(i / lat->Ntot);
+            const SiteKey& j = lat->chi_sites[i];
+            SiteKey d{{j.n[0], j.n[1], j.n[2]}, j.b};
+            const auto J = pair_coupling(lat, b, d, Ms);
+            const PairMap& pm = lat->chi_map[i];
+            for (int c = 1; c < 4; ++c) {
+                const int sc = nc == 2 ? 1 : pm.perm[c];
+                const double img = (*out)[((size_t)pm.r * nc + sc) * npar + p] * 4.0;
+                if (std::fabs(J[4 * (c - 1)] - img) > lat->eps) {
+                    *msg = "tangent direction " + std::to_string(p) + " breaks a symmetry used to reduce the lattice";
+                    return SR_ESYMMETRY;
+                }
+            }
+        }
+    }
+    return SR_OK;
+}
+
+}  // namespace sr

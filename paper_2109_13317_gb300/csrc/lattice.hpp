@@ -96,4 +96,10 @@ struct sr_lattice {
 namespace sr {
 // Builds every table; returns SR_OK or an error with a message in *msg.
 sr_status build_lattice(const sr_lattice_desc* d, sr_lattice* lat, std::string* msg);
+
+// Derivative of the initial vertex J^{cc}/4 of every irreducible site along npar coupling
+// directions dM (npar x n_couplings x 9, row-major 3x3 per coupling, in the order the
+// couplings were given): out[(r * nc + c) * npar + p].  Fails with SR_ESYMMETRY if a
+// direction is not invariant under the symmetries used for the site reduction.
+sr_status tangent_init(const sr_lattice* lat, int npar, const double* dM, std::vector<double>* out, std::string* msg);
 }  // namespace sr

@@ -129,6 +129,25 @@ def honeycomb_kitaev(J: float = 0.2, K: float = -1.0) -> Model:
     return Model(c, cps, "XYZ")
 
 
+def honeycomb_kitaev_linear():
+    """Heisenberg-Kitaev couplings as a linear function of theta = (J, K): the unit cell, the
+    coupling sites and the basis matrices B (2, n_couplings, 3, 3) with M_c = J B[0, c] +
+    K B[1, c]."""
+    c = honeycomb()
+    to = [(0, 0, 0, 1), (0, -1, 0, 1), (-1, 0, 0, 1)]
+    sites = [((0, 0, 0, 0), t) for t in to]
+    B = np.zeros((2, 3, 3, 3))
+    for i in range(3):
+        B[0, i] = I3
+        B[1, i] = _diag(i)
+    return c, sites, B
+
+
+def linear_model(cell, sites, B, theta, backend="XYZ") -> Model:
+    M = np.einsum("p,pcij->cij", np.asarray(theta, dtype=np.float64), B)
+    return Model(cell, [Coupling(f, t, M[k]) for k, (f, t) in enumerate(sites)], backend)
+
+
 @dataclass
 class FlowConfig:
     """One run configuration: model, truncation range, frequency mesh and cutoff range."""
