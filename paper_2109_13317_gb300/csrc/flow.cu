@@ -536,8 +536,29 @@ __device__ void gamma_rhs_f32_triple(const Geo& g, const Tabs& tb, const float* 
     for (int o = tid; o < g.Ns * NC; o += blockDim.x) sh.acc[o] = 0.0f;
     for (int o = tid; o < ncacc; o += blockDim.x) sh.cacc[o] = 0.0f;
 
+    // work split of the per-site and per-tile products: thread (r, group) takes every NG-th
+    // node of a block and keeps its partial sums in registers for the whole channel
+    const bool site_reg = g.Ns <= (int)blockDim.x;
+    const int NG = site_reg ? (int)blockDim.x / g.Ns : 1;
+    const int my_r = tid % g.Ns, my_g = tid / g.Ns;
+    const bool site_on = site_reg && my_g < NG;
+    const int ntile = NC * nsp4 * nsp4;
+    const size_t site_part = site_reg ? (size_t)NG * g.Ns * NC : 0;   // scratch floats of the site partials
+    const bool tile_reg = DENSE && ntile <= (int)blockDim.x &&
+                          site_part + (size_t)((int)blockDim.x / ntile) * ntile * 16 <= (size_t)kQF * 2 * rowp;
+    const int TG = tile_reg ? (int)blockDim.x / ntile : 1;
+    const int my_tile = tid % ntile, my_tg = tid / ntile;
+    const bool tile_on = tile_reg && my_tg < TG;
     for (int ch = 0; ch < 3; ++ch) {
         const int vi = ch == 0 ? si : (ch == 1 ? ti : ui);
+        float racc[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) racc[c] = 0.0f;
+        float a4[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) a4[i][j] = 0.0f;
         const int cidx = ch * g.N + vi;
         const int nq = ncount[cidx];
         const float* X = nx + (size_t)cidx * g.nmax;
@@ -598,11 +619,10 @@ __device__ void gamma_rhs_f32_triple(const Geo& g, const Tabs& tb, const float* 
             }
             __syncthreads();
             if (ch != 1) {
-                for (int r = tid; r < g.Ns; r += blockDim.x) {
-                    float o[NC], accl[NC], A[NC], B[NC];
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) accl[c] = 0.0f;
-                    for (int q = 0; q < qn; ++q) {
+                if (site_on) {
+                    const int r = my_r;
+                    for (int q = my_g; q < qn; q += NG) {
+                        float o[NC], A[NC], B[NC];
 #pragma unroll
                         for (int c = 0; c < NC; ++c) {
                             A[c] = sh.rows[(q * 2) * rowp + c * nsp + r];
@@ -610,21 +630,47 @@ __device__ void gamma_rhs_f32_triple(const Geo& g, const Tabs& tb, const float* 
                         }
                         if (ch == 0) s_product<float, NC>(A, B, o); else u_product<float, NC>(A, B, o);
 #pragma unroll
-                        for (int c = 0; c < NC; ++c) accl[c] += o[c];
+                        for (int c = 0; c < NC; ++c) racc[c] += o[c];
                     }
+                } else if (!site_reg) {
+                    for (int r = tid; r < g.Ns; r += blockDim.x) {
+                        float o[NC], accl[NC], A[NC], B[NC];
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) sh.acc[r * NC + c] += accl[c];
+                        for (int c = 0; c < NC; ++c) accl[c] = 0.0f;
+                        for (int q = 0; q < qn; ++q) {
+#pragma unroll
+                            for (int c = 0; c < NC; ++c) {
+                                A[c] = sh.rows[(q * 2) * rowp + c * nsp + r];
+                                B[c] = sh.rows[(q * 2 + 1) * rowp + c * nsp + r];
+                            }
+                            if (ch == 0) s_product<float, NC>(A, B, o); else u_product<float, NC>(A, B, o);
+#pragma unroll
+                            for (int c = 0; c < NC; ++c) accl[c] += o[c];
+                        }
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) sh.acc[r * NC + c] += accl[c];
+                    }
                 }
             } else {
-                if (DENSE) {
-                    const int ntile = NC * nsp4 * nsp4;
-                    for (int tl = tid; tl < ntile; tl += blockDim.x) {
-                        const int c = tl / (nsp4 * nsp4), ra = (tl / nsp4) % nsp4, rb = tl % nsp4;
-                        float a4[4][4];
+                if (tile_on) {
+                    const int c = my_tile / (nsp4 * nsp4), ra = (my_tile / nsp4) % nsp4, rb = my_tile % nsp4;
+                    for (int q = my_tg; q < qn; q += TG) {
+                        const float4 av = *reinterpret_cast<const float4*>(sh.rows + (q * 2) * rowp + c * nsp + 4 * ra);
+                        const float4 bv = *reinterpret_cast<const float4*>(sh.rows + (q * 2 + 1) * rowp + c * nsp + 4 * rb);
+                        const float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) a4[i][j] = 0.0f;
+                            for (int j = 0; j < 4; ++j) a4[i][j] += ar[i] * br[j];
+                    }
+                } else if (DENSE && !tile_reg) {
+                    for (int tl = tid; tl < ntile; tl += blockDim.x) {
+                        const int c = tl / (nsp4 * nsp4), ra = (tl / nsp4) % nsp4, rb = tl % nsp4;
+                        float t4[4][4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) t4[i][j] = 0.0f;
                         for (int q = 0; q < qn; ++q) {
                             const float4 av = *reinterpret_cast<const float4*>(sh.rows + (q * 2) * rowp + c * nsp + 4 * ra);
                             const float4 bv = *reinterpret_cast<const float4*>(sh.rows + (q * 2 + 1) * rowp + c * nsp + 4 * rb);
@@ -632,17 +678,17 @@ __device__ void gamma_rhs_f32_triple(const Geo& g, const Tabs& tb, const float* 
 #pragma unroll
                             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                                for (int j = 0; j < 4; ++j) a4[i][j] += ar[i] * br[j];
+                                for (int j = 0; j < 4; ++j) t4[i][j] += ar[i] * br[j];
                         }
                         float* cp = sh.cacc + c * nsp * nsp + (4 * ra) * nsp + 4 * rb;
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             float4 cv = *reinterpret_cast<float4*>(cp + i * nsp);
-                            cv.x += a4[i][0]; cv.y += a4[i][1]; cv.z += a4[i][2]; cv.w += a4[i][3];
+                            cv.x += t4[i][0]; cv.y += t4[i][1]; cv.z += t4[i][2]; cv.w += t4[i][3];
                             *reinterpret_cast<float4*>(cp + i * nsp) = cv;
                         }
                     }
-                } else {
+                } else if (!DENSE) {
                     for (int o = tid; o < tb.nprod; o += blockDim.x) {
                         const int2 pr = tb.prodp[o];
                         float a = 0.0f;
@@ -650,12 +696,11 @@ __device__ void gamma_rhs_f32_triple(const Geo& g, const Tabs& tb, const float* 
                         sh.cacc[o] += a;
                     }
                 }
-                for (int r = tid; r < g.Ns; r += blockDim.x) {
+                // on-site terms
+                if (site_on) {
+                    const int r = my_r;
                     const int pon = tb.onsite_perm[r];
-                    float accl[NC];
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) accl[c] = 0.0f;
-                    for (int q = 0; q < qn; ++q) {
+                    for (int q = my_g; q < qn; q += NG) {
                         float A[NC], B[NC], Cp[NC], D[NC];
 #pragma unroll
                         for (int c = 0; c < NC; ++c) {
@@ -666,13 +711,63 @@ __device__ void gamma_rhs_f32_triple(const Geo& g, const Tabs& tb, const float* 
                         }
 #pragma unroll
                         for (int c = 0; c < NC; ++c)
-                            accl[c] += A[c] * onsite_factor<float, NC>(Cp, c) + onsite_factor<float, NC>(D, c) * B[c];
+                            racc[c] += A[c] * onsite_factor<float, NC>(Cp, c) + onsite_factor<float, NC>(D, c) * B[c];
                     }
+                } else if (!site_reg) {
+                    for (int r = tid; r < g.Ns; r += blockDim.x) {
+                        const int pon = tb.onsite_perm[r];
+                        float accl[NC];
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) sh.acc[r * NC + c] += accl[c];
+                        for (int c = 0; c < NC; ++c) accl[c] = 0.0f;
+                        for (int q = 0; q < qn; ++q) {
+                            float A[NC], B[NC], Cp[NC], D[NC];
+#pragma unroll
+                            for (int c = 0; c < NC; ++c) {
+                                A[c] = sh.rows[(q * 2) * rowp + c * nsp + r];
+                                B[c] = sh.rows[(q * 2 + 1) * rowp + c * nsp + r];
+                                Cp[c] = sh.onrow[(q * 2) * NC + perm_of(pon, c)];
+                                D[c] = sh.onrow[(q * 2 + 1) * NC + c];
+                            }
+#pragma unroll
+                            for (int c = 0; c < NC; ++c)
+                                accl[c] += A[c] * onsite_factor<float, NC>(Cp, c) + onsite_factor<float, NC>(D, c) * B[c];
+                        }
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) sh.acc[r * NC + c] += accl[c];
+                    }
                 }
             }
         }
+        // end of the channel: combine the register partials of the node groups in a fixed order
+        // (scratch: the row buffer, free once the channel's last node block is done)
+        __syncthreads();
+        float* scr = sh.rows;
+        if (site_on) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) scr[(my_g * g.Ns + my_r) * NC + c] = racc[c];
+        }
+        float* scr2 = sh.rows + (site_reg ? NG * g.Ns * NC : 0);
+        if (ch == 1 && tile_on) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) scr2[(my_tg * ntile + my_tile) * 16 + i * 4 + j] = a4[i][j];
+        }
+        __syncthreads();
+        if (site_reg)
+            for (int o = tid; o < g.Ns * NC; o += blockDim.x) {
+                float a = 0.0f;
+                for (int k = 0; k < NG; ++k) a += scr[k * g.Ns * NC + o];
+                sh.acc[o] += a;
+            }
+        if (ch == 1 && tile_reg)
+            for (int e = tid; e < ntile * 16; e += blockDim.x) {
+                const int tl = e >> 4, ij = e & 15;
+                float a = 0.0f;
+                for (int k = 0; k < TG; ++k) a += scr2[(k * ntile + tl) * 16 + ij];
+                const int c = tl / (nsp4 * nsp4), ra = (tl / nsp4) % nsp4, rb = tl % nsp4;
+                sh.cacc[c * nsp * nsp + (4 * ra + (ij >> 2)) * nsp + 4 * rb + (ij & 3)] += a;
+            }
     }
     __syncthreads();
     const int* gidx = DENSE ? tb.dgath_idx : tb.gath_idx;
@@ -1684,13 +1779,21 @@ struct sr_batch {
     double tune_ms = 0.0;
     double run_ms = 0.0;
     int n_lambda_cap = 0;
-    ~sr_batch() { if (stream) cudaStreamDestroy(stream); }
+    std::vector<cudaStream_t> side;   // one per size class beyond the first
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    ~sr_batch() {
+        for (cudaStream_t s : side) cudaStreamDestroy(s);
+        for (cudaEvent_t e : join) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
+        if (stream) cudaStreamDestroy(stream);
+    }
 };
 
-static void launch_class(sr_batch* b, int k) {
+static void launch_class(sr_batch* b, int k, cudaStream_t st) {
     const BClass& c = b->cls[k];
-    k_gamma_persistent<<<b->nsm * c.ctas, kThreads, c.smem, b->stream>>>(b->dinst.p, c.i_begin, c.i_end, c.u_begin,
-                                                                          c.u_end, b->counter.p + k);
+    k_gamma_persistent<<<b->nsm * c.ctas, kThreads, c.smem, st>>>(b->dinst.p, c.i_begin, c.i_end, c.u_begin, c.u_end,
+                                                                   b->counter.p + k);
 }
 
 static sr_status batch_launch_step(sr_batch* b) {
@@ -1700,7 +1803,18 @@ static sr_status batch_launch_step(sr_batch* b) {
     for (const BInst& B : b->inst) { maxN = std::max(maxN, B.g.N); maxent = std::max(maxent, B.g.nentp); }
     k_sigma_b<<<dim3(maxN, ni), 64, 0, b->stream>>>(b->dinst.p, b->lams.p, b->step.p);
     k_nodes_b<<<dim3(3 * maxN, ni), 128, 0, b->stream>>>(b->dinst.p, b->lams.p, b->step.p);
-    for (int k = 0; k < (int)b->cls.size(); ++k) launch_class(b, k);
+    // size classes as parallel branches (fork / join), so a class's tail overlaps the others
+    const int nk = (int)b->cls.size();
+    if (nk > 1) {
+        CK(cudaEventRecord(b->fork, b->stream));
+        for (int k = 1; k < nk; ++k) {
+            CK(cudaStreamWaitEvent(b->side[k - 1], b->fork, 0));
+            launch_class(b, k, b->side[k - 1]);
+            CK(cudaEventRecord(b->join[k - 1], b->side[k - 1]));
+        }
+    }
+    launch_class(b, 0, b->stream);
+    for (int k = 1; k < nk; ++k) CK(cudaStreamWaitEvent(b->stream, b->join[k - 1], 0));
     const int ub = (int)std::min<long>((maxent + 255) / 256, 4 * b->nsm);
     k_update_b<<<dim3(ub, ni), 256, 0, b->stream>>>(b->dinst.p, b->lams.p, b->step.p, b->flag.p);
     k_shadow_b<<<dim3(ub, ni), 256, 0, b->stream>>>(b->dinst.p);
@@ -1723,7 +1837,7 @@ static sr_status batch_time_class(sr_batch* b, int k, double* ms) {
     for (int rep = 0; rep < 2; ++rep) {
         CK(cudaMemsetAsync(b->counter.p + k, 0, sizeof(unsigned long long), b->stream));
         CK(cudaEventRecord(e0, b->stream));
-        launch_class(b, k);
+        launch_class(b, k, b->stream);
         CK(cudaGetLastError());
         CK(cudaEventRecord(e1, b->stream));
         CK(cudaEventSynchronize(e1));
@@ -1829,6 +1943,15 @@ extern "C" sr_status sr_batch_create(int n, sr_flow* const* flows, sr_batch** ou
     b->occ = b->cls.front().occ;
     b->ctas = b->occ;
     CK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    for (size_t k = 1; k < b->cls.size(); ++k) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        b->side.push_back(st);
+        b->join.push_back(ev);
+    }
     CK(b->dinst.alloc(b->inst.size()));
     CK(b->step.alloc(1));
     CK(b->counter.alloc(b->cls.size()));
