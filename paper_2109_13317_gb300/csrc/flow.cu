@@ -573,7 +573,9 @@ __device__ void gamma_rhs_f32_triple(const Geo& g, const Tabs& tb, const float* 
                 float a, b, c;
                 node_args<float>(ch, rw, x, s, t, u, w1p, w2p, w1, w2, a, b, c);
                 const int exs = ch == 0 ? 0 : (ch == 2 ? 2 : (rw < 2 ? 1 : 2));
-                make_desc4(a, b, c, exs, vi, tb, g, rowp, sh.desc[q * 4 + rw]);
+                DescF dl;
+                make_desc4(a, b, c, exs, vi, tb, g, rowp, dl);
+                store_desc4(&sh.desc[q * 4 + rw], dl, tid & 31);
                 if (rw == 0) sh.wq[q] = Wp[q0 + q];
             }
             __syncthreads();
@@ -744,27 +746,28 @@ __device__ void gamma_rhs_f32_triple(const Geo& g, const Tabs& tb, const float* 
         float* scr = sh.rows;
         if (site_on) {
 #pragma unroll
-            for (int c = 0; c < NC; ++c) scr[(my_g * g.Ns + my_r) * NC + c] = racc[c];
+            for (int c = 0; c < NC; ++c) scr[(my_g * NC + c) * g.Ns + my_r] = racc[c];
         }
         float* scr2 = sh.rows + (site_reg ? NG * g.Ns * NC : 0);
         if (ch == 1 && tile_on) {
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) scr2[(my_tg * ntile + my_tile) * 16 + i * 4 + j] = a4[i][j];
+                for (int j = 0; j < 4; ++j) scr2[(my_tg * 16 + i * 4 + j) * ntile + my_tile] = a4[i][j];
         }
         __syncthreads();
         if (site_reg)
             for (int o = tid; o < g.Ns * NC; o += blockDim.x) {
+                const int r = o / NC, c = o % NC;
                 float a = 0.0f;
-                for (int k = 0; k < NG; ++k) a += scr[k * g.Ns * NC + o];
+                for (int k = 0; k < NG; ++k) a += scr[(k * NC + c) * g.Ns + r];
                 sh.acc[o] += a;
             }
         if (ch == 1 && tile_reg)
             for (int e = tid; e < ntile * 16; e += blockDim.x) {
-                const int tl = e >> 4, ij = e & 15;
+                const int tl = e % ntile, ij = e / ntile;
                 float a = 0.0f;
-                for (int k = 0; k < TG; ++k) a += scr2[(k * ntile + tl) * 16 + ij];
+                for (int k = 0; k < TG; ++k) a += scr2[(k * 16 + ij) * ntile + tl];
                 const int c = tl / (nsp4 * nsp4), ra = (tl / nsp4) % nsp4, rb = tl % nsp4;
                 sh.cacc[c * nsp * nsp + (4 * ra + (ij >> 2)) * nsp + 4 * rb + (ij & 3)] += a;
             }

@@ -252,6 +252,39 @@ struct __align__(16) DescF {
     int pad[3];
 };
 
+// Corners of the FP32 descriptor with the exact axis EA known at compile time, so that every
+// per-axis array index is static and the descriptor stays in registers.
+template <int EA>
+__device__ __forceinline__ void desc4_corners(float s, float t, float u, int ex_idx, bool flip, const Tabs& tb,
+                                              const Geo& g, int rowp, DescF& d) {
+    constexpr int A0 = EA == 0 ? 1 : 0, A1 = EA == 2 ? 1 : 2;
+    const float x0 = A0 == 0 ? s : t, x1 = A1 == 1 ? t : u;
+    int i0[2], i1[2], n0, n1;
+    float v0[2], v1[2];
+    axis_weights_f(tb, g, x0, n0, i0, v0);
+    if (n0 == 1) { i0[1] = i0[0]; v0[1] = 0.0f; }
+    axis_weights_f(tb, g, x1, n1, i1, v1);
+    if (n1 == 1) { i1[1] = i1[0]; v1[1] = 0.0f; }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int b0 = k & 1, b1 = k >> 1;
+        const int js = EA == 0 ? ex_idx : i0[b0];
+        const int jt = EA == 1 ? ex_idx : (A0 == 1 ? i0[b0] : i1[b1]);
+        const int ju = EA == 2 ? ex_idx : i1[b1];
+        const float wt = v0[b0] * v1[b1];
+        bool neg = flip;
+        int p;
+        if (js >= ju) p = pair_index(js, ju);
+        else { p = pair_index(ju, js); neg = !neg; }
+        d.off[k] = wt != 0.0f ? (p * g.N + jt) * rowp : 0;
+        d.wd[k] = neg ? -wt : wt;
+        d.ws[k] = wt;
+    }
+}
+
+// FP32 descriptor of Gamma(s, t, u) with one exact argument (ex_slot 0 s, 1 t, 2 u, the mesh
+// frequency w[ex_idx]): symmetry folding as in make_desc, then four corners over the other two
+// axes (zero-weight corners kept, pointing at offset 0).
 __device__ __forceinline__ void make_desc4(float s, float t, float u, int ex_slot, int ex_idx, const Tabs& tb,
                                            const Geo& g, int rowp, DescF& d) {
     int swap = 0;
@@ -260,38 +293,28 @@ __device__ __forceinline__ void make_desc4(float s, float t, float u, int ex_slo
     if (u < 0.0f) { u = -u; swap ^= 1; }
     bool flip = false;
     if (s < u) { float tmp = s; s = u; u = tmp; flip = true; if (ex_slot != 1) ex_slot = 2 - ex_slot; }
-    int ix[3][2], nx[3];
-    float wx[3][2];
-    const float arg[3] = {s, t, u};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (a == ex_slot) { nx[a] = 1; ix[a][0] = ex_idx; wx[a][0] = 1.0f; ix[a][1] = ex_idx; wx[a][1] = 0.0f; }
-        else {
-            axis_weights_f(tb, g, arg[a], nx[a], ix[a], wx[a]);
-            if (nx[a] == 1) { ix[a][1] = ix[a][0]; wx[a][1] = 0.0f; }
-        }
-    }
-    // four corners over the two non-exact axes (zero-weight corners kept, pointing at offset 0)
-    const int ea = ex_slot;  // the exact axis contributes index ix[ea][0] with weight 1
-    const int a0 = ea == 0 ? 1 : 0, a1 = ea == 2 ? 1 : 2;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        int id[3];
-        id[ea] = ix[ea][0];
-        const int b0 = k & 1, b1 = k >> 1;
-        id[a0] = ix[a0][b0];
-        id[a1] = ix[a1][b1];
-        const float wt = wx[a0][b0] * wx[a1][b1];
-        bool neg = flip;
-        int p;
-        if (id[0] >= id[2]) p = pair_index(id[0], id[2]);
-        else { p = pair_index(id[2], id[0]); neg = !neg; }
-        const bool live = wt != 0.0f;
-        d.off[k] = live ? (p * g.N + id[1]) * rowp : 0;
-        d.wd[k] = neg ? -wt : wt;
-        d.ws[k] = wt;
-    }
+    if (ex_slot == 0) desc4_corners<0>(s, t, u, ex_idx, flip, tb, g, rowp, d);
+    else if (ex_slot == 1) desc4_corners<1>(s, t, u, ex_idx, flip, tb, g, rowp, d);
+    else desc4_corners<2>(s, t, u, ex_idx, flip, tb, g, rowp, d);
     d.swap = swap;
+}
+
+// Store a descriptor built in registers to shared memory as four 16-byte chunks, chunk order
+// rotated by (lane >> 1) & 3 so that the eight lanes of a quarter warp, whose descriptors lie
+// 64 bytes apart, write eight distinct bank quads.
+__device__ __forceinline__ void store_desc4(DescF* dst, const DescF& d, int lane) {
+    const int4 c0 = *reinterpret_cast<const int4*>(d.off);
+    const int4 c1 = *reinterpret_cast<const int4*>(d.wd);
+    const int4 c2 = *reinterpret_cast<const int4*>(d.ws);
+    const int4 c3 = make_int4(d.swap, 0, 0, 0);
+    int4* out = reinterpret_cast<int4*>(dst);
+    const int rot = (lane >> 1) & 3;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int k = (j + rot) & 3;
+        const int4 v = k == 0 ? c0 : (k == 1 ? c1 : (k == 2 ? c2 : c3));
+        out[k] = v;
+    }
 }
 
 // Value of component c of the pair (ref, rep_r) at the descriptor's frequencies.
