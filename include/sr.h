@@ -201,6 +201,35 @@ sr_status sr_flow_tangents(const sr_flow* flow, int* n_tangent);
  * dchi_k n_k x 2, p fastest).  Synchronises. */
 sr_status sr_measure_susceptibility_tangent(sr_flow* flow, int n_k, const double* k_xyz, double* chi_k, double* dchi_k);
 
+/* ---- adjoint (reverse mode) of the FP64 flow ----
+ *
+ * Transposed derivatives of the discretised flow of Sec. 3 / Sec. 4.2 (the same right-hand
+ * side sr_flow_rhs evaluates) and of the Euler step of Sec. 4.3, for gradients of a scalar of
+ * the final state (e.g. chi(k_max)) with respect to the initial state.  All three use the
+ * flow's current state (set it with sr_flow_set_state: the caller keeps or recomputes the
+ * forward trajectory, e.g. from checkpoints); none changes it.  Arrays are device pointers
+ * on the flow's stream: sigma parts n_freq doubles, gamma parts n_gamma doubles (state
+ * layout); outputs are overwritten; asynchronous except where noted.  Errors:
+ * SR_EUNSUPPORTED for FP32-mixed or tangent flows and when the lattice needs more shared
+ * memory than one CTA has; SR_EINVAL for null pointers or a non-positive cutoff.
+ * Transposed lookups accumulate with atomic additions, so results are reproducible to
+ * rounding, not bit for bit. */
+
+/* (bar_sigma, bar_gamma) = (d f / d y)^T (fbar_sigma, fbar_gamma), f = sr_flow_rhs at lambda. */
+sr_status sr_flow_rhs_adjoint(sr_flow* flow, double lambda, const double* d_fbar_sigma, const double* d_fbar_gamma,
+                              double* d_bar_sigma, double* d_bar_gamma);
+
+/* Adjoint of one Euler step y' = y - (lambda_from - lambda_to) f(lambda_from, y):
+ * bar_out = bar_in - (lambda_from - lambda_to) (d f / d y)^T bar_in.  The flow's state must be
+ * the forward state at lambda_from (SR_EINVAL otherwise).  Outputs may alias the inputs. */
+sr_status sr_flow_step_adjoint(sr_flow* flow, double lambda_from, double lambda_to, const double* d_bar_sigma_in,
+                               const double* d_bar_gamma_in, double* d_bar_sigma_out, double* d_bar_gamma_out);
+
+/* Gradient of sum_i chi_bar_i chi(k_i) (sr_measure_susceptibility at the current state) with
+ * respect to the state.  k_xyz (host, 3 n_k) and chi_bar (host, n_k) are copied; synchronises. */
+sr_status sr_measure_susceptibility_adjoint(sr_flow* flow, int n_k, const double* k_xyz, const double* chi_bar,
+                                            double* d_bar_sigma, double* d_bar_gamma);
+
 /* ---- batched flows (many couplings / lattices of uneven size in one launch per stage) ---- */
 
 typedef struct sr_batch sr_batch;

@@ -1,11 +1,19 @@
 """Differentiable susceptibility: chi(k) at the end of a flow as a torch.autograd.Function of
 linear coupling parameters theta (couplings M_c = sum_p theta_p B[p, c]).
 
-The forward pass integrates the tangent-linear flow on the GPU (sr_flow_init_tangent: every
-kernel propagates d/dtheta_p exactly with dual numbers) and stores the Jacobian
-d chi(k) / d theta; the backward pass contracts it with the incoming gradient.  With two
-parameters the forward-mode Jacobian costs one flow of dual numbers and needs no stored
-trajectory (no checkpoints).
+Two ways to the same derivative:
+
+* ``susceptibility_adjoint`` (reverse mode): the forward pass integrates the FP64 flow with
+  Euler steps and keeps the state every ``every`` steps; the backward pass starts from
+  d chi / d state at the final cutoff (sr_measure_susceptibility_adjoint), walks the steps
+  backwards (sr_flow_step_adjoint), recomputing the states of one checkpoint segment at a
+  time, and contracts the adjoint of the initial vertex with d Gamma_init / d theta (the
+  initial vertex is J / 4, linear in the couplings).  Memory: one state per checkpoint plus
+  one segment; cost: one extra forward flow plus the adjoint steps, independent of the
+  number of parameters.
+* ``susceptibility`` (forward mode): the tangent-linear flow (sr_flow_init_tangent: every
+  kernel propagates d/dtheta_p with dual numbers) gives the Jacobian d chi(k) / d theta in the
+  forward pass; cheap for the two parameters of a coupling sweep, no stored trajectory.
 """
 from __future__ import annotations
 
@@ -41,3 +49,63 @@ def susceptibility(theta: torch.Tensor, cell, sites, B, L: int, mesh, lambdas, k
     return SusceptibilityFn.apply(theta, cell, sites, np.asarray(B, dtype=np.float64), L,
                                   np.asarray(mesh, dtype=np.float64), np.asarray(lambdas, dtype=np.float64),
                                   np.asarray(kpts, dtype=np.float64), backend)
+
+
+def _initial_vertex_derivative(lat, mesh, lam0, B):
+    """d Gamma_init / d theta_p in the state layout (n_par, n_gamma): the tangent part of a
+    tangent flow's initial state."""
+    fl = Flow(lat, mesh, float(lam0), SR_FP64, tangents=B)
+    _, G = fl.get_state()
+    fl.close()
+    return G.view(-1, 3)[:, 1:1 + B.shape[0]].t().contiguous()
+
+
+class SusceptibilityAdjointFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, theta, cell, sites, B, L, mesh, lambdas, kpts, backend, every):
+        th = theta.detach().cpu().double().numpy()
+        M = np.einsum("p,pcij->cij", th, B)
+        coups = [(f, t, M[c]) for c, (f, t) in enumerate(sites)]
+        lat = Lattice(cell.prim, cell.basis, cell.bonds, coups, L, backend)
+        fl = Flow(lat, mesh, float(lambdas[0]), SR_FP64)
+        ckpt = {0: tuple(x.clone() for x in fl.get_state())}
+        nstep = len(lambdas) - 1
+        for n in range(1, nstep + 1):
+            fl.step(float(lambdas[n]), SR_EULER)
+            if n % every == 0 and n < nstep:
+                ckpt[n] = tuple(x.clone() for x in fl.get_state())
+        chi, _ = fl.measure(kpts, want_ij=False)
+        final = tuple(x.clone() for x in fl.get_state())
+        ctx.state = (lat, fl, ckpt, final, B, mesh, lambdas, kpts, every)
+        return torch.as_tensor(chi, dtype=theta.dtype)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        lat, fl, ckpt, final, B, mesh, lambdas, kpts, every = ctx.state
+        nstep = len(lambdas) - 1
+        fl.set_state(float(lambdas[-1]), *final)
+        bar_s, bar_G = fl.measure_adjoint(kpts, grad_out.detach().cpu().double().numpy())
+        for start in sorted(ckpt, reverse=True):
+            end = min(start + every, nstep)
+            states = [ckpt[start]]
+            fl.set_state(float(lambdas[start]), *ckpt[start])
+            for n in range(start + 1, end):
+                fl.step(float(lambdas[n]), SR_EULER)
+                states.append(tuple(x.clone() for x in fl.get_state()))
+            for n in range(end - 1, start - 1, -1):
+                fl.set_state(float(lambdas[n]), *states[n - start])
+                fl.step_adjoint(float(lambdas[n]), float(lambdas[n + 1]), bar_s, bar_G)
+        dG0 = _initial_vertex_derivative(lat, mesh, lambdas[0], B)
+        grad = (dG0 @ bar_G).to(device="cpu", dtype=grad_out.dtype)
+        return (grad, None, None, None, None, None, None, None, None, None)
+
+
+def susceptibility_adjoint(theta: torch.Tensor, cell, sites, B, L: int, mesh, lambdas, kpts,
+                           backend: int = SR_XYZ, every: int = 20):
+    """chi(k) (tensor of len(kpts)) differentiable in theta by the reverse-mode adjoint flow
+    with a checkpoint every `every` Euler steps."""
+    if every < 1:
+        raise ValueError("every must be >= 1")
+    return SusceptibilityAdjointFn.apply(theta, cell, sites, np.asarray(B, dtype=np.float64), L,
+                                         np.asarray(mesh, dtype=np.float64), np.asarray(lambdas, dtype=np.float64),
+                                         np.asarray(kpts, dtype=np.float64), backend, int(every))

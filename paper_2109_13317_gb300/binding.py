@@ -19,6 +19,7 @@ from . import build as _build
 SR_SU2, SR_XYZ, SR_TRI = 0, 1, 2
 SR_FP64, SR_FP32_MIXED = 0, 1
 SR_EULER, SR_RK_ADAPTIVE, SR_RK_FIXED = 0, 1, 2
+SR_OK, SR_EINVAL, SR_ENOMEM, SR_ECUDA, SR_ESYMMETRY, SR_ENONFINITE, SR_ETIMEOUT, SR_EUNSUPPORTED = range(8)
 _STATUS = {0: "SR_OK", 1: "SR_EINVAL", 2: "SR_ENOMEM", 3: "SR_ECUDA", 4: "SR_ESYMMETRY",
            5: "SR_ENONFINITE", 6: "SR_ETIMEOUT", 7: "SR_EUNSUPPORTED"}
 
@@ -87,6 +88,9 @@ def load_library():
             "sr_flow_set_state": [vp, d, vp, vp],
             "sr_flow_lambda": [vp, dp],
             "sr_flow_destroy": [vp],
+            "sr_flow_rhs_adjoint": [vp, d, vp, vp, vp, vp],
+            "sr_flow_step_adjoint": [vp, d, d, vp, vp, vp, vp],
+            "sr_measure_susceptibility_adjoint": [vp, i, dp, dp, vp, vp],
             "sr_flow_profile_enable": [vp, i],
             "sr_flow_profile_read": [vp, dp, lp],
             "sr_flow_node_counts": [vp, ip],
@@ -231,12 +235,14 @@ class Flow:
             _check(lib.sr_flow_init(lattice.h, len(self.mesh), _dptr(self.mesh), float(lambda_init), int(precision),
                                     C.c_void_p(stream.cuda_stream), C.byref(h)))
             self.n_tan = 0
+            self.ts = 1
         else:
             dM = np.ascontiguousarray(tangents, dtype=np.float64)
             npar = dM.shape[0]
             _check(lib.sr_flow_init_tangent(lattice.h, len(self.mesh), _dptr(self.mesh), float(lambda_init), npar,
                                             _dptr(dM.reshape(-1)), C.c_void_p(stream.cuda_stream), C.byref(h)))
             self.n_tan = npar
+            self.ts = 3      # (value, d/dtheta_1, d/dtheta_2) per state scalar
         self.h = h
         ng, nf, nc = C.c_long(), C.c_int(), C.c_int()
         _check(lib.sr_flow_sizes(h, C.byref(ng), C.byref(nf), C.byref(nc)))
@@ -251,9 +257,9 @@ class Flow:
         import torch
         dev = torch.device("cuda", torch.cuda.current_device())
         if dsigma is None:
-            dsigma = torch.empty(self.N, dtype=torch.float64, device=dev)
+            dsigma = torch.empty(self.N * self.ts, dtype=torch.float64, device=dev)
         if dgamma is None:
-            dgamma = torch.empty(self.n_gamma, dtype=torch.float64, device=dev)
+            dgamma = torch.empty(self.n_gamma * self.ts, dtype=torch.float64, device=dev)
         _check(self._lib.sr_flow_rhs(self.h, float(lam), _ptr(dsigma), _ptr(dgamma)))
         return dsigma, dgamma
 
@@ -316,14 +322,51 @@ class Flow:
         return out.reshape(self.lattice.N_basis, self.lattice.N_tot, 4)
 
     def get_state(self):
+        """(sigma, gamma) as CUDA tensors; tangent flows interleave (value, d1, d2)."""
         import torch
-        g = torch.empty(self.N, dtype=torch.float64, device="cuda")
-        G = torch.empty(self.n_gamma, dtype=torch.float64, device="cuda")
+        g = torch.empty(self.N * self.ts, dtype=torch.float64, device="cuda")
+        G = torch.empty(self.n_gamma * self.ts, dtype=torch.float64, device="cuda")
         _check(self._lib.sr_flow_get_state(self.h, _ptr(g), _ptr(G)))
         return g, G
 
     def set_state(self, lam: float, sigma=None, gamma=None):
         _check(self._lib.sr_flow_set_state(self.h, float(lam), _ptr(sigma), _ptr(gamma)))
+
+    # ---- adjoint (FP64 plain flows) ----
+    def rhs_adjoint(self, lam: float, fbar_sigma, fbar_gamma):
+        """sr_flow_rhs_adjoint: (J^T fbar) of the right-hand side at the current state, as new
+        CUDA tensors (sigma part, gamma part)."""
+        import torch
+        gs = torch.empty(self.N, dtype=torch.float64, device="cuda")
+        gG = torch.empty(self.n_gamma, dtype=torch.float64, device="cuda")
+        _check(self._lib.sr_flow_rhs_adjoint(self.h, float(lam), _ptr(fbar_sigma), _ptr(fbar_gamma), _ptr(gs),
+                                             _ptr(gG)))
+        return gs, gG
+
+    def step_adjoint(self, lam_from: float, lam_to: float, bar_sigma, bar_gamma, out_sigma=None, out_gamma=None):
+        """sr_flow_step_adjoint: the adjoint of one Euler step from lam_from (the flow's state)
+        to lam_to.  Outputs may alias the inputs."""
+        if out_sigma is None:
+            out_sigma = bar_sigma
+        if out_gamma is None:
+            out_gamma = bar_gamma
+        _check(self._lib.sr_flow_step_adjoint(self.h, float(lam_from), float(lam_to), _ptr(bar_sigma), _ptr(bar_gamma),
+                                              _ptr(out_sigma), _ptr(out_gamma)))
+        return out_sigma, out_gamma
+
+    def measure_adjoint(self, kpts, chi_bar):
+        """sr_measure_susceptibility_adjoint: d (sum_k chi_bar_k chi(k)) / d state, as new CUDA
+        tensors (sigma part, gamma part)."""
+        import torch
+        kp = np.ascontiguousarray(kpts, dtype=np.float64).reshape(-1, 3)
+        cb = np.ascontiguousarray(chi_bar, dtype=np.float64).reshape(-1)
+        if cb.shape[0] != kp.shape[0]:
+            raise ValueError("one chi_bar value per momentum")
+        gs = torch.empty(self.N, dtype=torch.float64, device="cuda")
+        gG = torch.empty(self.n_gamma, dtype=torch.float64, device="cuda")
+        _check(self._lib.sr_measure_susceptibility_adjoint(self.h, kp.shape[0], _dptr(kp), _dptr(cb), _ptr(gs),
+                                                           _ptr(gG)))
+        return gs, gG
 
     def profile_enable(self, on: bool = True):
         _check(self._lib.sr_flow_profile_enable(self.h, 1 if on else 0))

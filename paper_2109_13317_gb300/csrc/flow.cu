@@ -98,8 +98,10 @@ template <typename T>
 __device__ void channel_nodes_block(Geo g, const double* __restrict__ w, const double* __restrict__ invh,
                                     const T* __restrict__ gam, const T* __restrict__ dgam, double lam,
                                     double* __restrict__ nx, T* __restrict__ nW, float* __restrict__ nWf,
-                                    int* __restrict__ ncount, const int id, float* __restrict__ nxf = nullptr) {
+                                    int* __restrict__ ncount, const int id, float* __restrict__ nxf = nullptr,
+                                    double* __restrict__ ntw = nullptr) {
     __shared__ double pts[2 * kMaxFreq + 4];
+    __shared__ double twt[2 * kMaxFreq + 4];
     __shared__ __align__(16) unsigned char val_raw[sizeof(T) * (2 * kMaxFreq + 4)];
     T* val = reinterpret_cast<T*>(val_raw);
     __shared__ unsigned char keep[2 * kMaxFreq + 4];
@@ -178,6 +180,7 @@ __device__ void channel_nodes_block(Geo g, const double* __restrict__ w, const d
             wgt += 0.5 * (pts[i + 1] - pts[i]);
         val[i] = wgt == 0.0 ? T(0.0) : T(wgt * preg(w, invh, N, gam, dgam, ch, v, pts[i]) * inv2pi);
         keep[i] = wgt != 0.0;
+        twt[i] = wgt;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -186,6 +189,7 @@ __device__ void channel_nodes_block(Geo g, const double* __restrict__ w, const d
             if (!keep[i]) continue;
             X[n] = pts[i];
             Wt[n] = val[i];
+            if (ntw) ntw[(size_t)id * g.nmax + n] = twt[i];
             ++n;
         }
         if (Wf)
@@ -200,8 +204,8 @@ template <typename T>
 __global__ void k_channel_nodes(Geo g, const double* __restrict__ w, const double* __restrict__ invh,
                                 const T* __restrict__ gam, const T* __restrict__ dgam, double lam,
                                 double* __restrict__ nx, T* __restrict__ nW, float* __restrict__ nWf,
-                                int* __restrict__ ncount, float* __restrict__ nxf) {
-    channel_nodes_block<T>(g, w, invh, gam, dgam, lam, nx, nW, nWf, ncount, blockIdx.x, nxf);
+                                int* __restrict__ ncount, float* __restrict__ nxf, double* __restrict__ ntw = nullptr) {
+    channel_nodes_block<T>(g, w, invh, gam, dgam, lam, nx, nW, nWf, ncount, blockIdx.x, nxf, ntw);
 }
 
 // Deterministic block sum (fixed reduction tree for a fixed block size) of NV scalars of
@@ -965,6 +969,8 @@ __global__ void k_chi_k(int nk, const double* __restrict__ kp, const T* __restri
 
 }  // namespace
 
+#include "adjoint.cuh"
+
 // ----------------------------------------------------------------------------- objects
 
 template <typename T>
@@ -1025,6 +1031,14 @@ struct sr_flow {
     long step_limit = 1000000;   // attempted steps per sr_flow_step call
     long n_rhs = 0, n_accept = 0, n_reject = 0;
     size_t smem_rhs = 0;
+    // lattice-sum tables on the host (the adjoint inverts them on first use)
+    std::vector<int2> h_prod;
+    std::vector<int> h_goff, h_gidx;
+    // adjoint work space (allocated on first use)
+    bool adj_ready = false;
+    size_t smem_adj = 0;
+    DevBuf<int> pinv_off, pinv_out, ainv_off, ainv_idx, binv_off, binv_idx;
+    DevBuf<double> ntw, Wbar, dgbar, tg, tG, chibar, kbar;
 
     Tabs tabs() const {
         Tabs t;
@@ -1281,6 +1295,9 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
         goff[lat->Ns * lat->nc] = (int)gidx.size();
     }
     f->nprod = (int)prods.size();
+    f->h_prod = prods;
+    f->h_goff = goff;
+    f->h_gidx = gidx;
     // padded-layout products, site-exchange map, dense (SU2) gather indices
     {
         const int nsp = g.nsp;
@@ -1640,6 +1657,145 @@ extern "C" sr_status sr_measure_susceptibility(sr_flow* f, int n_k, const double
     return SR_OK;
 }
 
+// ----------------------------------------------------------------------------- adjoint
+//
+// Reverse-mode derivatives of the FP64 flow (plain, non-tangent flows): the transpose of the
+// right-hand side's Jacobian at the current state, the transpose of one Euler step, and the
+// gradient of a weighted sum of chi(k) with respect to the state.  The caller keeps (or
+// recomputes from checkpoints) the forward states and sets each with sr_flow_set_state.
+
+static sr_status adj_prepare(sr_flow* f) {
+    if (f->adj_ready) return SR_OK;
+    const Geo& g = f->g;
+    const int row = g.Ns * g.nc, np = f->nprod;
+    std::vector<int> poff(np + 1, 0), pout(f->h_gidx.size());
+    for (int o = 0; o < row; ++o)
+        for (int k = f->h_goff[o]; k < f->h_goff[o + 1]; ++k) poff[f->h_gidx[k] + 1]++;
+    for (int i = 0; i < np; ++i) poff[i + 1] += poff[i];
+    {
+        std::vector<int> fill(poff.begin(), poff.end() - 1);
+        for (int o = 0; o < row; ++o)
+            for (int k = f->h_goff[o]; k < f->h_goff[o + 1]; ++k) pout[fill[f->h_gidx[k]]++] = o;
+    }
+    std::vector<int> aoff(row + 1, 0), aidx(np), boff(row + 1, 0), bidx(np);
+    for (int i = 0; i < np; ++i) { aoff[f->h_prod[i].x + 1]++; boff[f->h_prod[i].y + 1]++; }
+    for (int e = 0; e < row; ++e) { aoff[e + 1] += aoff[e]; boff[e + 1] += boff[e]; }
+    {
+        std::vector<int> fa(aoff.begin(), aoff.end() - 1), fb(boff.begin(), boff.end() - 1);
+        for (int i = 0; i < np; ++i) { aidx[fa[f->h_prod[i].x]++] = i; bidx[fb[f->h_prod[i].y]++] = i; }
+    }
+    cudaStream_t st = f->stream;
+    auto up = [&](DevBuf<int>& b, const std::vector<int>& v) { return v.empty() ? b.alloc(1) : b.upload(v.data(), v.size(), st); };
+    CK(up(f->pinv_off, poff));
+    CK(up(f->pinv_out, pout));
+    CK(up(f->ainv_off, aoff));
+    CK(up(f->ainv_idx, aidx));
+    CK(up(f->binv_off, boff));
+    CK(up(f->binv_idx, bidx));
+    CK(f->ntw.alloc((size_t)3 * g.N * g.nmax));
+    CK(f->Wbar.alloc((size_t)3 * g.N * g.nmax));
+    CK(f->dgbar.alloc((size_t)g.N));
+    CK(f->tg.alloc((size_t)g.N));
+    CK(f->tG.alloc((size_t)g.nent));
+    f->smem_adj = adj_smem_bytes(g.Ns, g.nc, np);
+    if (f->smem_adj > 227 * 1024) return fail(SR_EUNSUPPORTED, "lattice too large for the adjoint kernel (%zu bytes)", f->smem_adj);
+    CK(ensure_smem(g.nc == 2 ? (const void*)k_gamma_adj<2> : (const void*)k_gamma_adj<4>, f->smem_adj));
+    CK(cudaStreamSynchronize(st));
+    f->adj_ready = true;
+    return SR_OK;
+}
+
+static sr_status adj_check(const sr_flow* f) {
+    if (!f) return fail(SR_EINVAL, "null flow");
+    if (f->ntan) return fail(SR_EUNSUPPORTED, "the adjoint is defined for plain flows, not tangent flows");
+    if (f->prec != SR_FP64) return fail(SR_EUNSUPPORTED, "the adjoint is defined for FP64 flows");
+    return SR_OK;
+}
+
+// (gbar_o, Gbar_o) = J^T (fbar_g, fbar_G) at the current state and cutoff lam.
+static sr_status rhs_adjoint(sr_flow* f, double lam, const double* fbar_g, const double* fbar_G, double* gbar_o,
+                             double* Gbar_o) {
+    if (sr_status s = adj_prepare(f)) return s;
+    const Geo& g = f->g;
+    Tabs tb = f->tabs();
+    AdjTabs at{f->pinv_off.p, f->pinv_out.p, f->ainv_off.p, f->ainv_idx.p, f->binv_off.p, f->binv_idx.p};
+    cudaStream_t st = f->stream;
+    // forward quantities the derivatives need: dgamma, the node positions and weights
+    k_sigma_rhs<double><<<g.N, 64, 0, st>>>(g, tb, f->w.p, f->gam.p, f->G.p, lam, f->dgam.p);
+    k_channel_nodes<double><<<3 * g.N, 128, 0, st>>>(g, f->w.p, f->invh.p, f->gam.p, f->dgam.p, lam, f->nx.p, f->nW.p,
+                                                     nullptr, f->ncount.p, nullptr, f->ntw.p);
+    CK(cudaMemsetAsync(gbar_o, 0, sizeof(double) * g.N, st));
+    CK(cudaMemsetAsync(Gbar_o, 0, sizeof(double) * g.nent, st));
+    CK(cudaMemsetAsync(f->Wbar.p, 0, sizeof(double) * 3 * g.N * g.nmax, st));
+    CK(cudaMemsetAsync(f->dgbar.p, 0, sizeof(double) * g.N, st));
+    const int blocks = g.npair * g.N;
+    if (g.nc == 2)
+        k_gamma_adj<2><<<blocks, kThreads, f->smem_adj, st>>>(g, tb, at, f->w.p, f->G.p, f->nx.p, f->nW.p, f->ncount.p,
+                                                              fbar_G, Gbar_o, f->Wbar.p);
+    else
+        k_gamma_adj<4><<<blocks, kThreads, f->smem_adj, st>>>(g, tb, at, f->w.p, f->G.p, f->nx.p, f->nW.p, f->ncount.p,
+                                                              fbar_G, Gbar_o, f->Wbar.p);
+    k_nodes_adj<<<3 * g.N, 128, 0, st>>>(g, f->w.p, f->invh.p, f->gam.p, f->dgam.p, lam, f->nx.p, f->ntw.p, f->ncount.p,
+                                         f->Wbar.p, gbar_o, f->dgbar.p);
+    k_axmy<<<1, 256, 0, st>>>((long)g.N, f->dgbar.p, fbar_g, -1.0, f->dgbar.p);
+    k_sigma_adj<<<g.N, 64, 0, st>>>(g, tb, f->w.p, f->gam.p, f->G.p, lam, f->dgbar.p, gbar_o, Gbar_o);
+    CK(cudaGetLastError());
+    return SR_OK;
+}
+
+extern "C" sr_status sr_flow_rhs_adjoint(sr_flow* f, double lambda, const double* d_fbar_sigma, const double* d_fbar_gamma,
+                                         double* d_bar_sigma, double* d_bar_gamma) {
+    if (sr_status s = adj_check(f)) return s;
+    if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(SR_EINVAL, "lambda must be positive");
+    if (!d_fbar_sigma || !d_fbar_gamma || !d_bar_sigma || !d_bar_gamma) return fail(SR_EINVAL, "null buffer");
+    return rhs_adjoint(f, lambda, d_fbar_sigma, d_fbar_gamma, d_bar_sigma, d_bar_gamma);
+}
+
+extern "C" sr_status sr_flow_step_adjoint(sr_flow* f, double lambda_from, double lambda_to, const double* d_bar_sigma_in,
+                                          const double* d_bar_gamma_in, double* d_bar_sigma_out, double* d_bar_gamma_out) {
+    if (sr_status s = adj_check(f)) return s;
+    if (!d_bar_sigma_in || !d_bar_gamma_in || !d_bar_sigma_out || !d_bar_gamma_out) return fail(SR_EINVAL, "null buffer");
+    if (!(lambda_from > 0.0) || !(lambda_to > 0.0) || !std::isfinite(lambda_from) || !std::isfinite(lambda_to))
+        return fail(SR_EINVAL, "cutoffs must be positive");
+    if (f->lambda != lambda_from)
+        return fail(SR_EINVAL, "the flow's state is at Lambda = %.17g, not at lambda_from = %.17g", f->lambda, lambda_from);
+    if (sr_status s = adj_prepare(f)) return s;
+    const Geo& g = f->g;
+    if (sr_status s = rhs_adjoint(f, lambda_from, d_bar_sigma_in, d_bar_gamma_in, f->tg.p, f->tG.p)) return s;
+    const double dl = lambda_from - lambda_to;
+    k_axmy<<<1, 256, 0, f->stream>>>((long)g.N, d_bar_sigma_in, f->tg.p, dl, d_bar_sigma_out);
+    k_axmy<<<(unsigned)((g.nent + 255) / 256), 256, 0, f->stream>>>(g.nent, d_bar_gamma_in, f->tG.p, dl, d_bar_gamma_out);
+    CK(cudaGetLastError());
+    return SR_OK;
+}
+
+extern "C" sr_status sr_measure_susceptibility_adjoint(sr_flow* f, int n_k, const double* k_xyz, const double* chi_bar,
+                                                       double* d_bar_sigma, double* d_bar_gamma) {
+    if (sr_status s = adj_check(f)) return s;
+    if (n_k <= 0 || !k_xyz || !chi_bar || !d_bar_sigma || !d_bar_gamma) return fail(SR_EINVAL, "bad arguments");
+    const sr_lattice* lat = f->lat;
+    const Geo& g = f->g;
+    const int npairs = (int)lat->chi_map.size();
+    cudaStream_t st = f->stream;
+    if (f->kbar.n < (size_t)4 * n_k) CK(f->kbar.alloc((size_t)4 * n_k));
+    if (f->chibar.n < (size_t)npairs * g.nc) CK(f->chibar.alloc((size_t)npairs * g.nc));
+    CK(cudaMemcpyAsync(f->kbar.p, k_xyz, sizeof(double) * 3 * n_k, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(f->kbar.p + 3 * n_k, chi_bar, sizeof(double) * n_k, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(d_bar_sigma, 0, sizeof(double) * g.N, st));
+    CK(cudaMemsetAsync(d_bar_gamma, 0, sizeof(double) * g.nent, st));
+    k_chik_adj<<<(npairs + 127) / 128, 128, 0, st>>>(n_k, f->kbar.p, f->kbar.p + 3 * n_k, f->chi_dr.p, npairs, lat->nb, g.nc,
+                                                     f->chibar.p);
+    Tabs tb = f->tabs();
+    if (g.nc == 2)
+        k_chi_adj<2><<<npairs, 128, 0, st>>>(g, tb, f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_map.p, f->chi_onsite.p,
+                                             lat->Ntot, f->chibar.p, d_bar_sigma, d_bar_gamma);
+    else
+        k_chi_adj<4><<<npairs, 128, 0, st>>>(g, tb, f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_map.p, f->chi_onsite.p,
+                                             lat->Ntot, f->chibar.p, d_bar_sigma, d_bar_gamma);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    return SR_OK;
+}
 
 // ----------------------------------------------------------------------------- batched flows
 //
@@ -1685,32 +1841,50 @@ __global__ void k_nodes_b(const BInst* __restrict__ I, const double* __restrict_
 }
 
 // One size class of instances: units [u_begin, u_end) (instances [i_begin, i_end)).
-__global__ void __launch_bounds__(kThreads) k_gamma_persistent(const BInst* __restrict__ I, int i_begin, int i_end,
+template <int NC, bool DENSE>
+__global__ void __launch_bounds__(kThreads, 6) k_gamma_persistent(const BInst* __restrict__ I, int i_begin, int i_end,
                                                                long u_begin, long u_end,
                                                                unsigned long long* __restrict__ counter) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long unit_sh;
+    __shared__ int inst_sh;
+    __shared__ __align__(16) BInst B;   // the unit's instance, staged once per unit
+    int cur = -1;
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) unit_sh = u_begin + (long)atomicAdd(counter, 1ULL);
+        if (threadIdx.x == 0) {
+            const long u = u_begin + (long)atomicAdd(counter, 1ULL);
+            int lo = i_begin, hi = i_end - 1;   // last instance with unit0 <= u
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (I[mid].unit0 <= u) lo = mid; else hi = mid - 1;
+            }
+            unit_sh = u;
+            inst_sh = lo;
+        }
         __syncthreads();
         const long u = unit_sh;
         if (u >= u_end) break;
-        int lo = i_begin, hi = i_end - 1;   // last instance with unit0 <= u
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (I[mid].unit0 <= u) lo = mid; else hi = mid - 1;
+        if (inst_sh != cur) {
+            cur = inst_sh;
+            static_assert(sizeof(BInst) % sizeof(int) == 0, "BInst copied as ints");
+            const int* src = reinterpret_cast<const int*>(I + cur);
+            for (int i = threadIdx.x; i < (int)(sizeof(BInst) / sizeof(int)); i += blockDim.x)
+                reinterpret_cast<int*>(&B)[i] = src[i];
+            __syncthreads();
         }
-        const BInst& B = I[lo];
         const long local = u - B.unit0;
         const int p = (int)(local / B.g.N), ti = (int)(local % B.g.N);
-        if (B.kind == 0)
-            gamma_rhs_f32_triple<2, true>(B.g, B.tb, B.Gf, B.Gs, B.nxf, B.nWf, B.ncount, B.dG, p, ti, smem, B.qc);
-        else if (B.kind == 1)
-            gamma_rhs_f32_triple<2, false>(B.g, B.tb, B.Gf, B.Gs, B.nxf, B.nWf, B.ncount, B.dG, p, ti, smem, B.qc);
-        else
-            gamma_rhs_f32_triple<4, false>(B.g, B.tb, B.Gf, B.Gs, B.nxf, B.nWf, B.ncount, B.dG, p, ti, smem, B.qc);
+        gamma_rhs_f32_triple<NC, DENSE>(B.g, B.tb, B.Gf, B.Gs, B.nxf, B.nWf, B.ncount, B.dG, p, ti, smem, B.qc);
     }
+}
+
+// Persistent kernel of an instance kind (0: SU2 dense lattice sum, 1: SU2 product list, 2: XYZ);
+// every size class holds instances of one kind.
+static const void* persistent_fn(int kind) {
+    if (kind == 0) return (const void*)k_gamma_persistent<2, true>;
+    if (kind == 1) return (const void*)k_gamma_persistent<2, false>;
+    return (const void*)k_gamma_persistent<4, false>;
 }
 
 // Euler update of every instance (y <- y - (Lambda_k - Lambda_k+1) f) and its FP32 shadow.
@@ -1759,6 +1933,7 @@ __global__ void k_advance(int* __restrict__ step, unsigned long long* __restrict
 }  // namespace
 
 struct BClass {
+    int kind;             // instance kind (persistent_fn)
     int i_begin, i_end;   // instances
     long u_begin, u_end;  // work units
     size_t smem;
@@ -1795,8 +1970,14 @@ struct sr_batch {
 
 static void launch_class(sr_batch* b, int k, cudaStream_t st) {
     const BClass& c = b->cls[k];
-    k_gamma_persistent<<<b->nsm * c.ctas, kThreads, c.smem, st>>>(b->dinst.p, c.i_begin, c.i_end, c.u_begin, c.u_end,
-                                                                   b->counter.p + k);
+    const dim3 grid(b->nsm * c.ctas);
+    unsigned long long* ctr = b->counter.p + k;
+    if (c.kind == 0)
+        k_gamma_persistent<2, true><<<grid, kThreads, c.smem, st>>>(b->dinst.p, c.i_begin, c.i_end, c.u_begin, c.u_end, ctr);
+    else if (c.kind == 1)
+        k_gamma_persistent<2, false><<<grid, kThreads, c.smem, st>>>(b->dinst.p, c.i_begin, c.i_end, c.u_begin, c.u_end, ctr);
+    else
+        k_gamma_persistent<4, false><<<grid, kThreads, c.smem, st>>>(b->dinst.p, c.i_begin, c.i_end, c.u_begin, c.u_end, ctr);
 }
 
 static sr_status batch_launch_step(sr_batch* b) {
@@ -1897,14 +2078,19 @@ extern "C" sr_status sr_batch_create(int n, sr_flow* const* flows, sr_batch** ou
         if (f->prec != SR_FP32_MIXED) return fail(SR_EUNSUPPORTED, "batched flows use the FP32-mixed kernels (flow %d is FP64)", i);
         b->flows.push_back(f);
     }
-    // instances grouped by the shared memory their vertex flow needs (each class gets a
-    // persistent launch sized for it), largest first; within a class, largest instance first
+    // instances grouped by kind and by the shared memory their vertex flow needs (each class
+    // gets a persistent launch sized for it), largest first; within a class, largest instance
+    // first
     std::vector<size_t> sm(n);
-    for (int i = 0; i < n; ++i)
+    std::vector<int> kind(n);
+    for (int i = 0; i < n; ++i) {
         sm[i] = f32_smem_bytes(flows[i]->g.Ns, flows[i]->g.nsp, flows[i]->g.nc, flows[i]->nprod, flows[i]->dense);
+        kind[i] = flows[i]->g.nc == 4 ? 2 : (flows[i]->dense ? 0 : 1);
+    }
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        if (kind[a] != kind[c]) return kind[a] < kind[c];
         if (sm[a] != sm[c]) return sm[a] > sm[c];
         return flows[a]->g.nent > flows[c]->g.nent;
     });
@@ -1915,13 +2101,15 @@ extern "C" sr_status sr_batch_create(int n, sr_flow* const* flows, sr_batch** ou
     for (int idx = 0; idx < n; ++idx) {
         const int k = order[idx];
         sr_flow* f = flows[k];
-        // a new class when the shared memory drops below 2/3 of the class's largest
-        if (b->cls.empty() || sm[k] * 3 < b->cls.back().smem * 2) {
+        // a new class for a new kind, or when the shared memory drops below 2/3 of the
+        // class's largest
+        if (b->cls.empty() || b->cls.back().kind != kind[k] || sm[k] * 3 < b->cls.back().smem * 2) {
             BClass c{};
+            c.kind = kind[k];
             c.i_begin = idx; c.u_begin = unit; c.smem = sm[k]; c.qc = kQF;
             if (sm[k] > 227 * 1024) return fail(SR_EUNSUPPORTED, "instance needs %zu bytes of shared memory", sm[k]);
-            CK(ensure_smem((const void*)k_gamma_persistent, sm[k]));
-            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, k_gamma_persistent, kThreads, sm[k]));
+            CK(ensure_smem(persistent_fn(c.kind), sm[k]));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, persistent_fn(c.kind), kThreads, sm[k]));
             if (c.occ < 1) return fail(SR_EUNSUPPORTED, "persistent kernel cannot be resident with %zu bytes", sm[k]);
             c.ctas = c.occ;
             b->cls.push_back(c);
@@ -1934,7 +2122,7 @@ extern "C" sr_status sr_batch_create(int n, sr_flow* const* flows, sr_batch** ou
         B.ncount = f->ncount.p;
         B.unit0 = unit;
         B.qc = kQF;
-        B.kind = f->g.nc == 4 ? 2 : (f->dense ? 0 : 1);
+        B.kind = kind[k];
         B.with_swap = f->has_swap ? 1 : 0;
         unit += (long)f->g.npair * f->g.N;
         b->inst.push_back(B);
