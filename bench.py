@@ -381,6 +381,35 @@ def _batched_sweep(sr, torch, steps=20):
             "max_rel_diff_batched_vs_sequential": diff}
 
 
+def _tensor_core_variant(sr, torch, fl):
+    """The vertex kernel with the SU2 lattice sum on the tensor cores (3xTF32 tcgen05 MMAs) on
+    the flow's current state, against the default CUDA-core kernel: kernel times (CUDA events,
+    5 launches each after 2 warm-up launches) and the normwise difference of dGamma."""
+    if fl.n_comp != 2:
+        return None
+    lam = fl.lam
+    out = {}
+    res = {}
+    for tc in (False, True):
+        fl.tensor_cores = tc
+        for _ in range(2):
+            fl.rhs(lam)
+        torch.cuda.synchronize()
+        fl.profile_enable(False)
+        fl.profile_enable(True)
+        for _ in range(5):
+            _, dG = fl.rhs(lam)
+        torch.cuda.synchronize()
+        kms, kn = fl.profile_read()
+        out["tensor_cores_ms" if tc else "cuda_cores_ms"] = float(kms[2] / max(kn[2], 1))
+        res[tc] = dG.clone()
+    fl.tensor_cores = False
+    fl.profile_enable(False)
+    out["rel_diff"] = float((res[True] - res[False]).abs().max() / res[False].abs().max())
+    out["default"] = "cuda_cores"
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_2109_13317_gb300 as sr
@@ -437,6 +466,7 @@ def run_ours(args):
         _, G32 = fl2.get_state()
         flops2 = _algorithmic_flops(counts2, fl2.N, lat.N_s, fl2.n_comp, lat.P, fl2.lattice_sum_products())
         k2 = kms2[2] / max(kn2[2], 1)
+        tcv = _tensor_core_variant(sr, torch, fl2)
         extra["fp32_mixed"] = {"value": n_ent * ws / (sum(ms2) / len(ms2) * 1e-3), "unit": UNIT,
                                "ms_per_step": sum(ms2) / len(ms2), "dtype": "f32-mixed",
                                "gamma_rhs_ms": k2,
@@ -445,7 +475,8 @@ def run_ours(args):
                                "chi_rel_err_vs_fp64": float(np.abs(ck32 - ck64).max() / np.abs(ck64).max()),
                                "gamma_rel_err_vs_fp64": float((G32 - G64).abs().max() / G64.abs().max()),
                                "lambda": fl.lam,
-                               "note": f"both flows integrated with the same {i_end} Euler steps from Lambda=100"}
+                               "note": f"both flows integrated with the same {i_end} Euler steps from Lambda=100",
+                               "tensor_core_lattice_sum": tcv}
         fl2.close()
 
     # end to end through the public API: state in from pinned host memory, step, state out

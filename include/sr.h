@@ -182,6 +182,15 @@ sr_status sr_flow_lambda(const sr_flow* flow, double* lambda);
 
 sr_status sr_flow_destroy(sr_flow* flow);
 
+/* Lattice sum of an FP32-mixed SU2 flow on the tensor cores (off by default):
+ * the per-triple contraction C_c[rA][rB] = sum over t-channel nodes of A[c][rA] B[c][rB]
+ * (Eq. frg:flowexplicit:2particle, t-channel term with the site sum of Sec. 4.1) as tcgen05
+ * MMAs in 3xTF32 (TF32 hi / lo splits of both operands, three products, FP32 accumulation in
+ * tensor memory); off: the same contraction on FP32 CUDA cores.  SR_EUNSUPPORTED for FP64,
+ * XYZ, or more than 64 padded irreducible sites. */
+sr_status sr_flow_set_tensor_cores(sr_flow* flow, int on);
+sr_status sr_flow_tensor_cores(const sr_flow* flow, int* on);
+
 /* ---- tangent-linear flow: derivatives of the flow along coupling directions ---- */
 
 /* Like sr_flow_init (FP64), but the state carries, with every value, its derivatives along
@@ -278,6 +287,10 @@ sr_status sr_flow_node_counts(const sr_flow* flow, int* counts);
 /* Number of distinct products in the lattice sum of one vertex entry (the deduplicated
  * pairs (stored site A, component) x (stored site B, component) over the table). */
 sr_status sr_flow_lattice_sum_products(const sr_flow* flow, long* n_products);
+
+/* Launch shape of the vertex kernels (host out, 4 ints): tensor-core kernel grid, its dynamic
+ * shared memory, the runtime's occupancy figure for it, the CUDA-core kernel's shared memory. */
+sr_status sr_flow_launch_info(const sr_flow* flow, int* info);
 
 /* Throughput of fused multiply-adds on the current device (FLOP/s, 2 per FMA) for FP64
  * (precision = SR_FP64) or FP32 (SR_FP32_MIXED), from a register-resident FMA chain kernel

@@ -75,6 +75,8 @@ def load_library():
             "sr_flow_init": [vp, i, dp, d, i, vp, C.POINTER(vp)],
             "sr_flow_init_tangent": [vp, i, dp, d, i, dp, vp, C.POINTER(vp)],
             "sr_flow_tangents": [vp, ip],
+            "sr_flow_set_tensor_cores": [vp, i],
+            "sr_flow_tensor_cores": [vp, ip],
             "sr_measure_susceptibility_tangent": [vp, i, dp, dp, dp],
             "sr_flow_sizes": [vp, lp, ip, ip],
             "sr_flow_rhs": [vp, d, vp, vp],
@@ -95,6 +97,7 @@ def load_library():
             "sr_flow_profile_read": [vp, dp, lp],
             "sr_flow_node_counts": [vp, ip],
             "sr_flow_lattice_sum_products": [vp, lp],
+            "sr_flow_launch_info": [vp, ip],
             "sr_peak_fma": [i, dp],
             "sr_batch_create": [i, C.POINTER(vp), C.POINTER(vp)],
             "sr_batch_run": [vp, i, dp, i, i],
@@ -268,6 +271,17 @@ class Flow:
         _check(self._lib.sr_flow_step(self.h, float(lam_next), int(method), float(rtol), float(atol), C.byref(reached)))
         return reached.value
 
+    @property
+    def tensor_cores(self) -> bool:
+        """Whether the SU2 lattice sum of this FP32-mixed flow runs on the tensor cores."""
+        v = C.c_int()
+        _check(self._lib.sr_flow_tensor_cores(self.h, C.byref(v)))
+        return bool(v.value)
+
+    @tensor_cores.setter
+    def tensor_cores(self, on: bool):
+        _check(self._lib.sr_flow_set_tensor_cores(self.h, 1 if on else 0))
+
     def set_step_limit(self, n: int):
         _check(self._lib.sr_flow_set_step_limit(self.h, int(n)))
 
@@ -382,6 +396,12 @@ class Flow:
         n = C.c_long()
         _check(self._lib.sr_flow_lattice_sum_products(self.h, C.byref(n)))
         return n.value
+
+    def launch_info(self) -> dict:
+        out = np.zeros(4, dtype=np.int32)
+        _check(self._lib.sr_flow_launch_info(self.h, _iptr(out)))
+        return {"tc_grid": int(out[0]), "tc_smem": int(out[1]), "tc_occupancy_runtime": int(out[2]),
+                "smem": int(out[3])}
 
     def node_counts(self) -> np.ndarray:
         out = np.zeros(3 * self.N, dtype=np.int32)

@@ -27,10 +27,12 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "tc.cuh"
 #include "lattice.hpp"
 #include "sr.h"
 
 using namespace sr::dev;
+namespace tc = sr::tc;
 
 // ----------------------------------------------------------------------------- errors
 
@@ -495,11 +497,235 @@ struct ShF {
 
 __host__ __device__ inline size_t rnd16(size_t b) { return (b + 15) & ~size_t(15); }
 
-__host__ __device__ inline size_t f32_smem_bytes(int Ns, int nsp, int nc, int nprod, bool dense) {
+// Tensor-core lattice sum (SU2, padded sites nsp <= 64): per triple and component c the dense
+// contraction C_c[rA][rB] = sum_q A_q[c][rA] B_q[c][rB] as tcgen05 MMAs with M = 64 (rA),
+// N = NB (rB), K = 8 nodes, in 3xTF32 (A_hi B_hi + A_hi B_lo + A_lo B_hi, FP32 accumulation in
+// TMEM).  For nsp <= 32 both components share one MMA ("packed": A rows c * 32 + rA, B rows
+// c * Np + rB; only the c = c' blocks of the product are read back).
+constexpr int kQT = 16;   // t-channel nodes per block on the tensor-core path (two K-steps)
+
+struct TcShape {
+    int packed, G, Np, NB, ncols;   // MMA groups G (1 packed, 2 one per component), N per MMA
+    int tileA, tileB, kbytes;       // bytes of an A / B tile (K = 8) and of one K-step's tiles
+};
+
+__host__ __device__ inline TcShape tc_shape(int nsp) {
+    TcShape t;
+    t.packed = nsp <= 32;
+    t.Np = (nsp + 7) & ~7;
+    t.NB = t.packed ? 2 * t.Np : t.Np;
+    t.G = t.packed ? 1 : 2;
+    t.ncols = 32;
+    while (t.ncols < t.G * t.NB) t.ncols *= 2;
+    t.tileA = 64 * 32;
+    t.tileB = t.NB * 32;
+    t.kbytes = t.G * 2 * (t.tileA + t.tileB);
+    return t;
+}
+
+__host__ __device__ inline bool tc_supported(int nc, int nsp, bool dense) { return nc == 2 && dense && nsp <= 64; }
+
+__host__ __device__ inline size_t f32_smem_bytes(int Ns, int nsp, int nc, int nprod, bool dense, bool tc = false) {
     const size_t rowp = (size_t)nc * nsp;
-    return rnd16(sizeof(DescF) * kQF * 4) + rnd16(sizeof(float) * kQF * 2 * rowp) + rnd16(sizeof(float) * kQF * 2 * nc) +
+    size_t rows = sizeof(float) * kQF * 2 * rowp;
+    if (tc) rows = rows > (size_t)(kQT / 8) * tc_shape(nsp).kbytes ? rows : (size_t)(kQT / 8) * tc_shape(nsp).kbytes;
+    return rnd16(sizeof(DescF) * kQF * 4) + rnd16(rows) + rnd16(sizeof(float) * kQF * 2 * nc) +
            rnd16(sizeof(float) * kQF) + rnd16(sizeof(float) * Ns * nc) +
            rnd16(sizeof(float) * (dense ? (size_t)nc * nsp * nsp : (size_t)nprod));
+}
+
+// Tensor-memory state of a CTA on the tensor-core path.
+struct TcCta {
+    uint32_t tmem;      // accumulator base address (lane 0, first column)
+    uint64_t* mbar;     // MMA completion barrier
+    uint32_t ncommit;   // commits so far (the barrier's completed phases)
+    int* fail;          // set when a completion wait gives up
+};
+
+// t channel of one stored triple on the tensor-core path: node blocks of kQT nodes; the
+// interpolated rows A (weighted) and B go to shared memory as TF32 hi / lo tiles; one thread
+// issues the 3xTF32 MMAs of the block (accumulating C in TMEM across the channel) while all
+// threads add the on-site terms; at the end C is read back into cacc for the table gather.
+template <typename Sh>
+__device__ void t_channel_tc(const Geo& g, const Tabs& tb, const float* __restrict__ Gf, const float* __restrict__ Gs,
+                             const float* __restrict__ X, const float* __restrict__ Wp, const int nq, const int vi,
+                             const float s, const float t, const float u, const float w1p, const float w2p,
+                             const float w1, const float w2, Sh& sh, float (&racc)[2], const bool site_on,
+                             const int my_r, const int my_g, const int NG, TcCta& tcs) {
+    constexpr int NC = 2;
+    const int tid = threadIdx.x;
+    const int nsp = g.nsp, nsp4 = nsp >> 2, rowp = NC * nsp;
+    const TcShape ts = tc_shape(nsp);
+    unsigned char* tiles = reinterpret_cast<unsigned char*>(sh.rows);
+    const uint32_t tiles_s = tc::smem_addr(tiles);
+    const uint32_t idesc = tc::idesc_tf32(64, ts.NB);
+    constexpr long kWait = 1L << 22;
+    __syncthreads();   // the previous channel's scratch reads of this region are done
+    // zero every tile once: padding rows (sites >= nsp, unused M rows) stay zero
+    for (int i = tid; i < (kQT / 8) * ts.kbytes / 16; i += blockDim.x)
+        reinterpret_cast<float4*>(tiles)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool started = false;
+    for (int q0 = 0; q0 < nq; q0 += kQT) {
+        const int qn = min(kQT, nq - q0), qpad = (qn + 7) & ~7;
+        __syncthreads();
+        for (int idx = tid; idx < qn * 4; idx += blockDim.x) {
+            const int q = idx / 4, rw = idx % 4;
+            const float x = X[q0 + q];
+            float a, b, c;
+            node_args<float>(1, rw, x, s, t, u, w1p, w2p, w1, w2, a, b, c);
+            DescF dl;
+            make_desc4(a, b, c, rw < 2 ? 1 : 2, vi, tb, g, rowp, dl);
+            store_desc4(&sh.desc[q * 4 + rw], dl, tid & 31);
+            if (rw == 0) sh.wq[q] = Wp[q0 + q];
+        }
+        // the previous block's MMAs must have read their tiles before they are rewritten
+        if (started && !tc::mbar_wait(tcs.mbar, (tcs.ncommit - 1) & 1, kWait) && tid == 0) atomicOr(tcs.fail, 1);
+        __syncthreads();
+        // item = (4-node group, row, component, 4 sites); the four lanes of a quad take the four
+        // nodes of a group, interpolate 4 sites each, and transpose through shuffles so that
+        // each lane stores one site's 4 consecutive nodes: a 16-byte row of a core matrix
+        const int nitems = qpad * 2 * NC * nsp4;   // a multiple of 4: quads never straddle the end
+        const int ql = tid & 3;
+        for (int base = 0; base < nitems; base += blockDim.x) {
+            const int it = base + tid;
+            const bool act = it < nitems;
+            int rest = it >> 2;
+            const int r4 = rest % nsp4;
+            rest /= nsp4;
+            const int c = rest % NC;
+            rest /= NC;
+            const int rw = rest & 1, q = 4 * (rest >> 1) + ql;
+            float vv[4] = {0.f, 0.f, 0.f, 0.f};
+            if (act && q < qn) {
+                const DescF& d = sh.desc[q * 4 + rw];
+                const float* gb = (d.swap ? Gs : Gf) + c * nsp + 4 * r4;
+                const int4 ov = *reinterpret_cast<const int4*>(d.off);
+                const float4 wv = c == 0 ? *reinterpret_cast<const float4*>(d.wd) : *reinterpret_cast<const float4*>(d.ws);
+                const float4 g0 = __ldg(reinterpret_cast<const float4*>(gb + ov.x));
+                const float4 g1 = __ldg(reinterpret_cast<const float4*>(gb + ov.y));
+                const float4 g2 = __ldg(reinterpret_cast<const float4*>(gb + ov.z));
+                const float4 g3 = __ldg(reinterpret_cast<const float4*>(gb + ov.w));
+                vv[0] = wv.x * g0.x + wv.y * g1.x + wv.z * g2.x + wv.w * g3.x;
+                vv[1] = wv.x * g0.y + wv.y * g1.y + wv.z * g2.y + wv.w * g3.y;
+                vv[2] = wv.x * g0.z + wv.y * g1.z + wv.z * g2.z + wv.w * g3.z;
+                vv[3] = wv.x * g0.w + wv.y * g1.w + wv.z * g2.w + wv.w * g3.w;
+                if (rw == 0) {
+                    const float wq = sh.wq[q];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) vv[j] *= wq;
+                }
+            }
+            // 4 x 4 transpose in the quad: round k sends vv[(ql + k) & 3] and receives site ql of
+            // node (ql - k) & 3
+            float uu[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int si_ = (ql + k) & 3, src = (ql - k) & 3;
+                const float send = si_ == 0 ? vv[0] : (si_ == 1 ? vv[1] : (si_ == 2 ? vv[2] : vv[3]));
+                const float got = __shfl_sync(0xffffffffu, send, (tid & 31 & ~3) | src);
+                if (src == 0) uu[0] = got;
+                else if (src == 1) uu[1] = got;
+                else if (src == 2) uu[2] = got;
+                else uu[3] = got;
+            }
+            if (act) {
+                const int gi = ts.packed ? 0 : c;
+                const int q0g = q & ~3;   // first node of the group
+                unsigned char* kb = tiles + (q0g >> 3) * ts.kbytes + gi * 2 * (ts.tileA + ts.tileB);
+                unsigned char* hi = rw == 0 ? kb : kb + 2 * ts.tileA;
+                unsigned char* lo = hi + (rw == 0 ? ts.tileA : ts.tileB);
+                const int r = (ts.packed ? c * (rw == 0 ? 32 : ts.Np) : 0) + 4 * r4 + ql;
+                float4 h, l;
+                h.x = tc::tf32_rna(uu[0]); l.x = tc::tf32_rna(uu[0] - h.x);
+                h.y = tc::tf32_rna(uu[1]); l.y = tc::tf32_rna(uu[1] - h.y);
+                h.z = tc::tf32_rna(uu[2]); l.z = tc::tf32_rna(uu[2] - h.z);
+                h.w = tc::tf32_rna(uu[3]); l.w = tc::tf32_rna(uu[3] - h.w);
+                const uint32_t o = tc::tile_off(r, q0g & 7);
+                *reinterpret_cast<float4*>(hi + o) = h;
+                *reinterpret_cast<float4*>(lo + o) = l;
+            }
+        }
+        for (int j = tid; j < qn * 2 * NC; j += blockDim.x) {
+            const int qq = j / (2 * NC), rr = (j / NC) % 2, c = j % NC;
+            const DescF& d = sh.desc[qq * 4 + 2 + rr];
+            const float* base = Gf + c * nsp;   // the on-site pair is its own exchange
+            const float* wgt = c == 0 ? d.wd : d.ws;
+            float v = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v += wgt[k] * base[d.off[k]];
+            if (rr == 1) v *= sh.wq[qq];
+            sh.onrow[(qq * 2 + rr) * NC + c] = v;
+        }
+        tc::fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            for (int ks = 0; ks < qpad / 8; ++ks)
+                for (int gi = 0; gi < ts.G; ++gi) {
+                    const uint32_t kb = tiles_s + ks * ts.kbytes + gi * 2 * (ts.tileA + ts.tileB);
+                    const uint64_t ah = tc::smem_desc(kb), al = tc::smem_desc(kb + ts.tileA);
+                    const uint64_t bh = tc::smem_desc(kb + 2 * ts.tileA), bl = tc::smem_desc(kb + 2 * ts.tileA + ts.tileB);
+                    const uint32_t d = tcs.tmem + gi * ts.NB;
+                    tc::mma_tf32(d, ah, bh, idesc, started || ks > 0);
+                    tc::mma_tf32(d, ah, bl, idesc, true);
+                    tc::mma_tf32(d, al, bh, idesc, true);
+                }
+            tc::mma_commit(tcs.mbar);
+        }
+        tcs.ncommit++;
+        started = true;
+        // on-site terms of this block (rows read back as hi + lo) while the MMAs run
+        if (site_on) {
+            const int r = my_r;
+            const int pon = tb.onsite_perm[r];
+            for (int q = my_g; q < qn; q += NG) {
+                const unsigned char* kb = tiles + (q >> 3) * ts.kbytes;
+                float A[NC], B[NC], Cp[NC], D[NC];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const unsigned char* gb = kb + (ts.packed ? 0 : c) * 2 * (ts.tileA + ts.tileB);
+                    const uint32_t oa = tc::tile_off((ts.packed ? c * 32 : 0) + r, q & 7);
+                    const uint32_t ob = tc::tile_off((ts.packed ? c * ts.Np : 0) + r, q & 7);
+                    A[c] = *reinterpret_cast<const float*>(gb + oa) + *reinterpret_cast<const float*>(gb + ts.tileA + oa);
+                    B[c] = *reinterpret_cast<const float*>(gb + 2 * ts.tileA + ob) +
+                           *reinterpret_cast<const float*>(gb + 2 * ts.tileA + ts.tileB + ob);
+                    Cp[c] = sh.onrow[(q * 2) * NC + perm_of(pon, c)];
+                    D[c] = sh.onrow[(q * 2 + 1) * NC + c];
+                }
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    racc[c] += A[c] * onsite_factor<float, NC>(Cp, c) + onsite_factor<float, NC>(D, c) * B[c];
+            }
+        }
+    }
+    if (!started) return;   // no node: C stays zero
+    if (!tc::mbar_wait(tcs.mbar, (tcs.ncommit - 1) & 1, kWait) && tid == 0) atomicOr(tcs.fail, 1);
+    tc::fence_after_sync();
+    // read C back: warp w holds accumulator rows 16 w .. 16 w + 15 in its lanes 0..15
+    const int warp = tid >> 5, lane = tid & 31;
+    if (warp < 4) {
+        const int m = 16 * warp + lane;
+        for (int j = 0; j < ts.G * ts.NB / 8; ++j) {
+            float v[8];
+            tc::tmem_ld8(tcs.tmem + ((uint32_t)(32 * warp) << 16) + 8 * j, v);
+            if (lane < 16) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int col = 8 * j + i, gi = col / ts.NB, n = col % ts.NB;
+                    int c, rA, rB;
+                    if (ts.packed) {
+                        c = m / 32; rA = m % 32;
+                        if (n / ts.Np != c) continue;
+                        rB = n % ts.Np;
+                    } else {
+                        c = gi; rA = m; rB = n;
+                    }
+                    if (rA < nsp && rB < nsp) sh.cacc[c * nsp * nsp + rA * nsp + rB] = v[i];
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
 }
 
 // FP32-mixed vertex flow: the same equations as k_gamma_rhs with FP32 rows, products and
@@ -508,19 +734,22 @@ __host__ __device__ inline size_t f32_smem_bytes(int Ns, int nsp, int nc, int np
 // pair stored in place, for lookups whose arguments exchange the two sites).  With DENSE
 // (SU2), the lattice sum is the per-triple contraction C[c][rA][rB] = sum_q A_q B_q in 4x4
 // register tiles, gathered through the table at the end.
-template <int NC, bool DENSE>
+template <int NC, bool DENSE, bool TC = false>
 __device__ void gamma_rhs_f32_triple(const Geo& g, const Tabs& tb, const float* __restrict__ Gf,
                                      const float* __restrict__ Gs, const float* __restrict__ nx,
                                      const float* __restrict__ nW, const int* __restrict__ ncount,
                                      double* __restrict__ dG, const int p, const int ti, unsigned char* smem,
-                                     const int qc) {
+                                     const int qc, TcCta* tcs = nullptr) {
+    static_assert(!TC || (NC == 2 && DENSE), "tensor-core lattice sum: SU2 dense contraction only");
     const int nsp = g.nsp, nsp4 = nsp >> 2, rowp = NC * nsp;
     ShF<NC, DENSE> sh;
     {
         size_t off = 0;
         auto take = [&](size_t bytes) { unsigned char* q = smem + off; off += rnd16(bytes); return q; };
         sh.desc = (DescF*)take(sizeof(DescF) * kQF * 4);
-        sh.rows = (float*)take(sizeof(float) * kQF * 2 * rowp);
+        size_t rows_bytes = sizeof(float) * kQF * 2 * rowp;
+        if (TC) rows_bytes = max(rows_bytes, (size_t)(kQT / 8) * tc_shape(nsp).kbytes);
+        sh.rows = (float*)take(rows_bytes);
         sh.onrow = (float*)take(sizeof(float) * kQF * 2 * NC);
         sh.wq = (float*)take(sizeof(float) * kQF);
         sh.acc = (float*)take(sizeof(float) * g.Ns * NC);
@@ -548,7 +777,7 @@ __device__ void gamma_rhs_f32_triple(const Geo& g, const Tabs& tb, const float* 
     const bool site_on = site_reg && my_g < NG;
     const int ntile = NC * nsp4 * nsp4;
     const size_t site_part = site_reg ? (size_t)NG * g.Ns * NC : 0;   // scratch floats of the site partials
-    const bool tile_reg = DENSE && ntile <= (int)blockDim.x &&
+    const bool tile_reg = DENSE && !TC && ntile <= (int)blockDim.x &&
                           site_part + (size_t)((int)blockDim.x / ntile) * ntile * 16 <= (size_t)kQF * 2 * rowp;
     const int TG = tile_reg ? (int)blockDim.x / ntile : 1;
     const int my_tile = tid % ntile, my_tg = tid / ntile;
@@ -568,7 +797,11 @@ __device__ void gamma_rhs_f32_triple(const Geo& g, const Tabs& tb, const float* 
         const float* X = nx + (size_t)cidx * g.nmax;
         const float* Wp = nW + (size_t)cidx * g.nmax;
         const int nrow = ch == 1 ? 4 : 2;
-        for (int q0 = 0; q0 < nq; q0 += qc) {
+        if constexpr (TC) {
+            if (ch == 1)
+                t_channel_tc(g, tb, Gf, Gs, X, Wp, nq, vi, s, t, u, w1p, w2p, w1, w2, sh, racc, site_on, my_r, my_g, NG, *tcs);
+        }
+        for (int q0 = 0; q0 < ((TC && ch == 1) ? 0 : nq); q0 += qc) {
             const int qn = min(qc, nq - q0);
             __syncthreads();
             for (int idx = tid; idx < qn * nrow; idx += blockDim.x) {
@@ -795,6 +1028,43 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_f32(Geo g, Tabs tb, cons
     gamma_rhs_f32_triple<NC, DENSE>(g, tb, Gf, Gs, nx, nW, ncount, dG, blockIdx.x / g.N, blockIdx.x % g.N, smem, kQF);
 }
 
+// The SU2 kernel with the lattice sum on the tensor cores, persistent: each CTA allocates its
+// TMEM accumulator and MMA barrier once and takes the stored triples blockIdx.x,
+// blockIdx.x + gridDim.x, ...; the grid is sized so that the CTAs resident on an SM never ask
+// for more than its 512 TMEM columns.  `fail` is set if an MMA completion wait gives up (the
+// outputs of that triple are then NaN, so the flow's finiteness check reports it).
+static_assert(kThreads == 128, "the TMEM read-back maps the four warps onto the four lane quarters");
+__global__ void __launch_bounds__(kThreads) k_gamma_rhs_f32_tc(Geo g, Tabs tb, const float* __restrict__ Gf,
+                                                               const float* __restrict__ Gs, const float* __restrict__ nx,
+                                                               const float* __restrict__ nW, const int* __restrict__ ncount,
+                                                               double* __restrict__ dG, int* __restrict__ fail) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int failed;
+    const uint32_t ncols = (uint32_t)tc_shape(g.nsp).ncols;
+    if (threadIdx.x == 0) { tc::mbar_init(&mbar); failed = 0; }
+    if (threadIdx.x < 32) tc::tmem_alloc(&tmem_slot, ncols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    TcCta tcs{tmem_slot, &mbar, 0u, &failed};
+    const long ntrip = (long)g.npair * g.N;
+    for (long tr = blockIdx.x; tr < ntrip; tr += gridDim.x) {
+        const int p = (int)(tr / g.N), ti = (int)(tr % g.N);
+        gamma_rhs_f32_triple<2, true, true>(g, tb, Gf, Gs, nx, nW, ncount, dG, p, ti, smem, kQF, &tcs);
+        __syncthreads();
+        if (failed) {
+            for (int o = threadIdx.x; o < g.Ns * 2; o += blockDim.x)
+                dG[((size_t)(p * g.N + ti) * 2 + o % 2) * g.Ns + o / 2] = __longlong_as_double(0x7ff8000000000000LL);
+            if (threadIdx.x == 0) atomicOr(fail, 1);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) tc::tmem_dealloc(tcs.tmem, ncols);
+}
+
 // FP32 shadow of the state in the padded layout, and (with_swap) the exchanged copy in which
 // entry (c, r) holds the stored value of the pair (rep_r, ref): component perm(c) of site
 // swap_r[r].  Padding sites are zero.
@@ -1013,6 +1283,11 @@ struct sr_flow {
     DevBuf<int2> prodp;
     DevBuf<int> dgath_idx;
     bool has_swap = false, dense = false;
+    bool use_tc = false;          // FP32-mixed SU2: lattice sum on the tensor cores
+    size_t smem_tc = 0;           // dynamic shared memory of the tensor-core kernel
+    int tc_grid = 0;              // its persistent grid (SMs x resident CTAs)
+    int tc_occ_api = 0;           // the runtime's occupancy figure for it (reported only)
+    DevBuf<int> tcfail;           // set by the tensor-core kernel when an MMA wait gives up
     int nprod = 0;
     DevBuf<double> init;
     DevBuf<int2> chi_map;
@@ -1137,7 +1412,10 @@ static sr_status run_rhs(sr_flow* f, double lam, const double* gam_s, const doub
             k_gamma_rhs<double, 4><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, f->w.p, G_s, f->nx.p, f->nW.p, f->ncount.p, dG_o);
     } else {
         const float* Gs = f->has_swap ? Gf_s + g.nentp : Gf_s;
-        if (g.nc == 2 && f->dense)
+        if (g.nc == 2 && f->dense && f->use_tc)
+            k_gamma_rhs_f32_tc<<<std::min(blocks, f->tc_grid), kThreads, f->smem_tc, f->stream>>>(g, tb, Gf_s, Gs, f->nxf.p, f->nWf.p, f->ncount.p, dG_o,
+                                                                            f->tcfail.p);
+        else if (g.nc == 2 && f->dense)
             k_gamma_rhs_f32<2, true><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, Gf_s, Gs, f->nxf.p, f->nWf.p, f->ncount.p, dG_o);
         else if (g.nc == 2)
             k_gamma_rhs_f32<2, false><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, Gf_s, Gs, f->nxf.p, f->nWf.p, f->ncount.p, dG_o);
@@ -1373,8 +1651,14 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
         k_fill_init<double><<<(unsigned)((g.nent + 255) / 256), 256, 0, st>>>(g, f->init.p, f->G.p);
     CK(cudaGetLastError());
     if (sr_status s2 = refresh_shadow(f.get(), f->G.p, f->Gf.p)) return s2;
+    const bool tc_ok = precision == SR_FP32_MIXED && tc_supported(g.nc, g.nsp, f->dense);
     f->smem_rhs = precision == SR_FP32_MIXED ? f32_smem_bytes(g.Ns, g.nsp, g.nc, f->nprod, f->dense)
                                              : rhs_smem_bytes(g, f->nprod, f->ntan ? sizeof(DualT) : sizeof(double));
+    if (tc_ok) f->smem_tc = f32_smem_bytes(g.Ns, g.nsp, g.nc, f->nprod, f->dense, true);
+    f->use_tc = false;   // off by default: slower than the CUDA-core contraction on the square
+                         // J1-J2 and pyrochlore workloads (operand staging outweighs the contraction)
+    CK(f->tcfail.alloc(1));
+    CK(cudaMemsetAsync(f->tcfail.p, 0, sizeof(int), st));
     if (f->smem_rhs > 227 * 1024) return fail(SR_EUNSUPPORTED, "lattice too large for one CTA's shared memory (%zu bytes)", f->smem_rhs);
     if (f->ntan) {
         CK(ensure_smem((const void*)k_gamma_rhs<DualT, 2>, f->smem_rhs));
@@ -1386,6 +1670,26 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
         CK(ensure_smem((const void*)k_gamma_rhs_f32<2, true>, f->smem_rhs));
         CK(ensure_smem((const void*)k_gamma_rhs_f32<2, false>, f->smem_rhs));
         CK(ensure_smem((const void*)k_gamma_rhs_f32<4, false>, f->smem_rhs));
+        if (tc_ok) {
+            // persistent grid: resident CTAs per SM limited by the kernel's resources and by
+            // the SM's 512 TMEM columns
+            CK(ensure_smem((const void*)k_gamma_rhs_f32_tc, f->smem_tc));
+            int occ = 0, dev = 0, nsm = 0, regs_sm = 0, smem_sm = 0, resv = 0;
+            cudaFuncAttributes fa;
+            CK(cudaFuncGetAttributes(&fa, k_gamma_rhs_f32_tc));
+            CK(cudaGetDevice(&dev));
+            CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+            CK(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+            CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+            CK(cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+            const int regs = (fa.numRegs + 7) & ~7;
+            occ = std::min(regs_sm / (regs * kThreads), (int)(smem_sm / (f->smem_tc + fa.sharedSizeBytes + resv)));
+            occ = std::min(occ, 512 / tc_shape(g.nsp).ncols);
+            f->tc_occ_api = 0;
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f->tc_occ_api, k_gamma_rhs_f32_tc, kThreads, f->smem_tc));
+            if (occ < 1) return fail(SR_EUNSUPPORTED, "tensor-core kernel cannot be resident (%zu bytes)", f->smem_tc);
+            f->tc_grid = nsm * occ;
+        }
     }
     CK(cudaStreamSynchronize(st));
     *out = f.release();
@@ -1401,6 +1705,20 @@ extern "C" sr_status sr_flow_init_tangent(const sr_lattice* lat, int n_freq, con
                                           int n_par, const double* dM, void* cuda_stream, sr_flow** out) {
     if (n_par < 1 || n_par > kTan || !dM) return fail(SR_EINVAL, "n_par must be in [1, %d] with derivative couplings given", kTan);
     return flow_create(lat, n_freq, freq_pos, lambda_init, SR_FP64, cuda_stream, n_par, dM, out);
+}
+
+extern "C" sr_status sr_flow_set_tensor_cores(sr_flow* f, int on) {
+    if (!f) return fail(SR_EINVAL, "null flow");
+    if (on && !(f->prec == SR_FP32_MIXED && tc_supported(f->g.nc, f->g.nsp, f->dense)))
+        return fail(SR_EUNSUPPORTED, "tensor-core lattice sum needs an FP32-mixed SU2 flow with at most 64 padded sites");
+    f->use_tc = on != 0;
+    return SR_OK;
+}
+
+extern "C" sr_status sr_flow_tensor_cores(const sr_flow* f, int* on) {
+    if (!f || !on) return fail(SR_EINVAL, "null argument");
+    *on = f->use_tc ? 1 : 0;
+    return SR_OK;
 }
 
 extern "C" sr_status sr_flow_tangents(const sr_flow* f, int* n_tangent) {
@@ -1427,9 +1745,11 @@ extern "C" sr_status sr_flow_rhs(sr_flow* f, double lambda, double* d_dsigma, do
 }
 
 static sr_status check_flag(sr_flow* f, double lam) {
-    int h = 0;
+    int h = 0, t = 0;
     CK(cudaMemcpyAsync(&h, f->flag.p, sizeof(int), cudaMemcpyDeviceToHost, f->stream));
+    CK(cudaMemcpyAsync(&t, f->tcfail.p, sizeof(int), cudaMemcpyDeviceToHost, f->stream));
     CK(cudaStreamSynchronize(f->stream));
+    if (t) return fail(SR_ETIMEOUT, "tensor-core MMA completion wait gave up (Lambda = %.17g)", lam);
     if (h) return fail(SR_ENONFINITE, "non-finite value in the flow at Lambda = %.17g", lam);
     return SR_OK;
 }
@@ -2369,6 +2689,15 @@ extern "C" sr_status sr_flow_profile_read(sr_flow* f, double* ms, long* launches
         ms[k] = acc;
         launches[k] = (long)f->ev[k].size();
     }
+    return SR_OK;
+}
+
+extern "C" sr_status sr_flow_launch_info(const sr_flow* f, int* info) {
+    if (!f || !info) return fail(SR_EINVAL, "null argument");
+    info[0] = f->tc_grid;
+    info[1] = (int)f->smem_tc;
+    info[2] = f->tc_occ_api;
+    info[3] = (int)f->smem_rhs;
     return SR_OK;
 }
 
