@@ -41,7 +41,7 @@ UNIT = "entries/s"
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
@@ -53,7 +53,8 @@ def _args():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms during the timed region (the
+    sampler is running before the region starts; samples taken before it are dropped)."""
 
     FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
@@ -68,13 +69,17 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.idx), "-lms", "200"], stdout=subprocess.PIPE,
+                                          "-i", str(self.idx), "-lms", "50"], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        t0 = time.time()
+        while not self.samples and time.time() - t0 < 5.0:
+            time.sleep(0.01)
+        self.samples.clear()
 
     def _read(self):
         for line in self.proc.stdout:
@@ -111,19 +116,22 @@ def _dist():
 
 
 def _algorithmic_flops(counts: np.ndarray, N: int, Ns: int, nc: int, P: int, nprod: int) -> float:
-    """Floating-point operations of one vertex-flow launch.  Per stored triple (s, t, u) and
-    integration node: every vertex row needed by the flow equations is interpolated over all
-    irreducible sites and components; one of the three frequency arguments of every row is a
-    mesh frequency, so an interpolated value is 4 corners = 8 flop.  The s and u channels need
-    two rows and the projected product (14 flop per site SU2, 36 XYZ); the t channel needs two
-    rows, two on-site rows (n_c values), the on-site terms (9 flop per site and component)
-    and the lattice sum, evaluated as 3 flop (W A B + acc) per distinct product of table
+    """Floating-point operations of one vertex-flow launch, counted as the natural evaluation
+    of the flow equations (an FMA = 2 flop).  Per stored triple (s, t, u) and integration node:
+    every vertex row the equations need is interpolated over all irreducible sites and
+    components; one of the three frequency arguments of every row is a mesh frequency, so an
+    interpolated value is 4 corners = 4 FMA = 8 flop, and the node weight multiplies one row
+    (1 flop per value).  s and u channels: two rows and the projected product (SU2 11 flop per
+    site: A1 B1, its multiples and three FMAs plus two accumulations; XYZ 32).  t channel: two
+    rows, two on-site rows (n_c values each), the on-site terms (SU2 6 flop per site and
+    component, XYZ 7) and the lattice sum as one FMA (2 flop) per distinct product of table
     rows.  Per triple, the lattice sum's table gather adds P n_c flop."""
     row = Ns * nc
-    prod = 14 if nc == 2 else 36
-    per_s = 2 * row * 8 + Ns * prod
+    prod = 11 if nc == 2 else 32
+    onsite = 6 if nc == 2 else 7
+    per_s = 2 * row * 8 + row + Ns * prod
     per_u = per_s
-    per_t = (2 * row + 2 * nc) * 8 + 3 * nprod + 9 * row
+    per_t = (2 * row + 2 * nc) * 8 + row + nc + 2 * nprod + onsite * row
     ns, nt, nu = counts[0].astype(np.float64), counts[1].astype(np.float64), counts[2].astype(np.float64)
     cs = np.arange(1, N + 1, dtype=np.float64)   # number of u_i <= s_i
     tot = N * float(np.sum(ns * cs)) * per_s                   # s channel: node count depends on s_i
@@ -242,13 +250,19 @@ def run_reference(args):
 
 
 def _measure_precision(sr, torch, cfg, lat, mesh, prec, steps, warmup, lams, flush, kgrid, sampler=None):
-    """Advance to mid-flow, warm up, then time `steps` Euler steps (+ chi) with CUDA events."""
+    """Advance to mid-flow, warm up, then time `steps` Euler steps (+ chi) with CUDA events.
+    From Lambda ~ 1 on, the steps follow a fine log grid (2000 steps per four decades), so any
+    number of timed steps stays mid-flow."""
     fl = sr.Flow(lat, mesh, lams[0], prec)
     i = 0
     # untimed advance to mid-flow
     while lams[i] > 1.0:
         fl.step(lams[i + 1], sr.SR_EULER)
         i += 1
+    n_adv = i
+    ratio = (cfg.lam_min / cfg.lam_max) ** (1.0 / 2000)
+    lams = [lams[i] * ratio ** k for k in range(warmup + steps + 1)]
+    i = 0
     for _ in range(warmup):
         fl.step(lams[i + 1], sr.SR_EULER)
         fl.measure(kgrid, want_ij=False)
@@ -277,7 +291,7 @@ def _measure_precision(sr, torch, cfg, lat, mesh, prec, steps, warmup, lams, flu
     kms, kn = fl.profile_read()
     counts = fl.node_counts()
     fl.profile_enable(False)
-    return fl, ms, kms, kn, counts, (lam_start, lams[i]), i
+    return fl, ms, kms, kn, counts, (lam_start, lams[i]), n_adv + i
 
 
 def _full_flow(sr, torch, cfg, lat, mesh, prec, kgrid, method="euler", n_steps=200, n_out=50, budget_s=40.0):
@@ -511,7 +525,7 @@ def run_ours(args):
         e32["chi_max_rel_err_vs_fp64_all_outputs"] = float(np.abs(cm32 - cm64).max() / np.abs(cm64).max())
         e32["speedup_vs_fp64"] = e64["seconds"] / e32["seconds"]
         ff["euler"] = {"fp64": e64, "fp32_mixed": e32}
-        a64, _, _ = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP64, kgrid, "rk", budget_s=30.0)
+        a64, _, _ = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP64, kgrid, "rk", budget_s=90.0)
         a32, _, _ = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP32_MIXED, kgrid, "rk", budget_s=30.0)
         ff["adaptive"] = {"fp64": a64, "fp32_mixed": a32}
         extra["full_flow"] = ff

@@ -1302,6 +1302,7 @@ struct sr_flow {
     bool profiling = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[3];
     double last_err = 0.0, h_next = 0.0;
+    double err_prev = 1e-4;      // error norm of the last accepted adaptive step (controller memory)
     bool fsal = false;           // kg[6] / kG[6] hold the right-hand side of the current state
     long step_limit = 1000000;   // attempted steps per sr_flow_step call
     long n_rhs = 0, n_accept = 0, n_reject = 0;
@@ -1862,28 +1863,40 @@ extern "C" sr_status sr_flow_step(sr_flow* f, double lambda_next, int method, do
         f->n_accept++;
     } else if (method == SR_RK_ADAPTIVE) {
         if (!(rtol > 0.0) || !(atol >= 0.0)) return fail(SR_EINVAL, "rtol must be positive and atol non-negative");
+        // step-size control (Hairer, Norsett & Wanner, Solving ODEs I, Sec. II.4, with the
+        // stabilised PI variant for DOPRI5): accepted steps scale h by
+        // 0.9 err^-0.17 err_prev^0.04 within [0.2, 5], never growing right after a rejection;
+        // rejected steps by max(0.2, 0.9 err^-0.2).  A step cut short to land on lambda_next
+        // does not shrink the proposal for the next call.
         double h = f->h_next < 0.0 ? f->h_next : (lambda_next - f->lambda);
         long guard = 0;
+        bool rejected = false;
         while (f->lambda > lambda_next) {
             if (++guard > f->step_limit) {
                 if (reached) *reached = f->lambda;
                 return fail(SR_ETIMEOUT, "adaptive stepping stopped at Lambda = %.17g after %ld attempted steps",
                             f->lambda, f->step_limit);
             }
-            if (f->lambda + h < lambda_next) h = lambda_next - f->lambda;
+            const double h_prop = h;
+            const bool cut = f->lambda + h < lambda_next;
+            if (cut) h = lambda_next - f->lambda;
             sr_status s = dp54_step(f, h, rtol, atol);
             if (s != SR_OK && s != SR_ENONFINITE) return s;
             double err = s == SR_ENONFINITE ? INFINITY : f->last_err;
-            double fac = err == 0.0 ? 5.0 : 0.9 * std::pow(err, -0.2);
             if (err <= 1.0) {
                 f->fsal = true;
                 f->lambda += h;
                 if (std::fabs(f->lambda - lambda_next) <= 1e-14 * std::fabs(lambda_next)) f->lambda = lambda_next;
                 if (sr_status e = refresh_shadow(f, f->G.p, f->Gf.p)) return e;
                 f->n_accept++;
-                h *= std::min(5.0, std::max(0.2, fac));
+                double fac = err == 0.0 ? 5.0 : 0.9 * std::pow(err, -0.17) * std::pow(f->err_prev, 0.04);
+                fac = std::min(rejected ? 1.0 : 5.0, std::max(0.2, fac));
+                f->err_prev = std::max(err, 1e-4);
+                h = cut ? h_prop : h * fac;
                 f->h_next = h;
+                rejected = false;
             } else {
+                const double fac = 0.9 * std::pow(err, -0.2);
                 if (sr_status e = restore_y0(f)) return e;
                 // the first stage (the right-hand side at the step's start) stays valid: park it
                 // where the next attempt's first-same-as-last exchange picks it up
@@ -1891,6 +1904,7 @@ extern "C" sr_status sr_flow_step(sr_flow* f, double lambda_next, int method, do
                 std::swap(f->kG[0].p, f->kG[6].p);
                 f->fsal = true;
                 f->n_reject++;
+                rejected = true;
                 h *= std::max(0.2, std::min(1.0, fac));
                 if (std::fabs(h) < 1e-14 * f->lambda) return fail(SR_ENONFINITE, "step size underflow at Lambda = %.17g", f->lambda);
             }
@@ -2644,6 +2658,7 @@ extern "C" sr_status sr_flow_set_state(sr_flow* f, double lambda, const double* 
     if (sr_status s = refresh_shadow(f, f->G.p, f->Gf.p)) return s;
     f->lambda = lambda;
     f->h_next = 0.0;
+    f->err_prev = 1e-4;
     f->fsal = false;
     return SR_OK;
 }

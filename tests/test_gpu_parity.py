@@ -239,22 +239,31 @@ def test_nonfinite_state_is_reported():
 
 
 def _oracle_adaptive(of, lam0, lam1, rtol, atol, h0):
-    """Dormand-Prince 5(4) with the standard controller (h <- h clamp(0.9 err^-1/5, 0.2, 5)),
-    driven on the oracle's fixed step; returns the accepted cutoffs."""
+    """Dormand-Prince 5(4) with the stabilised PI controller of Hairer, Norsett & Wanner
+    (accepted: h <- h clamp(0.9 err^-0.17 err_prev^0.04, 0.2, 5), no growth right after a
+    rejection; rejected: h <- h max(0.2, 0.9 err^-0.2)), driven on the oracle's fixed step;
+    returns the accepted cutoffs."""
     lam, h, acc = lam0, h0, [lam0]
+    err_prev, rejected = 1e-4, False
     while lam > lam1:
-        if lam + h < lam1:
+        h_prop = h
+        cut = lam + h < lam1
+        if cut:
             h = lam1 - lam
         g0, G0 = of.get_state()
         err = of.dp54(lam, lam + h, rtol, atol)
-        fac = 5.0 if err == 0 else 0.9 * err ** -0.2
         if err <= 1.0:
             lam = lam + h
             acc.append(lam)
-            h *= min(5.0, max(0.2, fac))
+            fac = 5.0 if err == 0 else 0.9 * err ** -0.17 * err_prev ** 0.04
+            fac = min(1.0 if rejected else 5.0, max(0.2, fac))
+            err_prev = max(err, 1e-4)
+            h = h_prop if cut else h * fac
+            rejected = False
         else:
             of.set_state(g0, G0)
-            h *= max(0.2, min(1.0, fac))
+            h *= max(0.2, min(1.0, 0.9 * err ** -0.2))
+            rejected = True
     return acc
 
 
