@@ -24,6 +24,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "kernels.cuh"
@@ -300,6 +301,40 @@ __device__ __forceinline__ void u_product(const T* A, const T* B, T* o) {
         o[3] = A[0] * B[3] + A[3] * B[0] + (A[1] * B[2] + A[2] * B[1]);
     }
 }
+// a * b + c as one fused multiply-add (for dual numbers: the same value, tangents by the
+// product rule)
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
+template <int P>
+__device__ __forceinline__ Dual<P> fmadd(const Dual<P>& a, const Dual<P>& b, const Dual<P>& c) { return a * b + c; }
+template <int P>
+__device__ __forceinline__ Dual<P> fmadd(const Dual<P>& a, double b, const Dual<P>& c) { return a * b + c; }
+
+// acc += s_product(A, B) (SGN = -1) or u_product(A, B) (SGN = +1) as chains of fused
+// multiply-adds into the accumulators.
+template <typename T, int NC, int SGN>
+__device__ __forceinline__ void su_product_acc(const T* A, const T* B, T* acc) {
+    if (NC == 2) {
+        const T t = A[1] * B[1];
+        acc[0] = fmadd(A[0], B[0], acc[0]);
+        acc[0] = fmadd(t, (T)3, acc[0]);
+        acc[1] = fmadd(A[0], B[1], acc[1]);
+        acc[1] = fmadd(A[1], B[0], acc[1]);
+        acc[1] = fmadd(t, (T)(2 * SGN), acc[1]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[0] = fmadd(A[k], B[k], acc[0]);
+#pragma unroll
+        for (int c = 1; c < 4; ++c) {
+            const int p = c == 1 ? 2 : 1, q = c == 3 ? 2 : 3;   // the two other spin components
+            acc[c] = fmadd(A[0], B[c], acc[c]);
+            acc[c] = fmadd(A[c], B[0], acc[c]);
+            acc[c] = fmadd(SGN > 0 ? A[p] : -A[p], B[q], acc[c]);
+            acc[c] = fmadd(SGN > 0 ? A[q] : -A[q], B[p], acc[c]);
+        }
+    }
+}
+
 // On-site factor sum_k s(k, c) C_k with s = -1 iff k and c are distinct spin components.
 template <typename T, int NC>
 __device__ __forceinline__ T onsite_factor(const T* C, int c) {
@@ -392,12 +427,21 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const do
                 double a, b, c;
                 node_args(ch, rw, x, s, t, u, w1p, w2p, w1, w2, a, b, c);
                 const int exs = ch == 0 ? 0 : (ch == 2 ? 2 : (rw < 2 ? 1 : 2));
-                make_desc(a, b, c, exs, vi, tb, g, sh.desc[q * 4 + rw]);
+                Desc<typename WeightOf<T>::type>& d = sh.desc[q * 4 + rw];
+                make_desc(a, b, c, exs, vi, tb, g, d);
                 if (rw == 0) sh.wq[q] = Wp[q0 + q];
+                if constexpr (std::is_same<T, double>::value) {
+                    // FP64: the node weight goes into the corner weights of its rows
+                    if (rw == 0 || rw == 3) {
+                        const double wn = Wp[q0 + q];
+                        for (int k = 0; k < d.n; ++k) { d.wd[k] *= wn; d.ws[k] *= wn; }
+                    }
+                }
             }
             __syncthreads();
             // phase 2: interpolated rows over all irreducible sites (and the on-site rows); the
             // first row of every node (and the second on-site row) carries the node weight
+            constexpr bool kWeighted = std::is_same<T, double>::value;   // already in the corners
             {
                 const int nfull = qn * 2 * row;
                 int q = tid / (2 * row), rem = tid % (2 * row);
@@ -405,7 +449,7 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const do
                 for (int idx = tid; idx < nfull; idx += blockDim.x) {
                     const int r = e / NC, c = e % NC;
                     T v = row_value(G, sh.desc[q * 4 + rw], tb, g, r, c);
-                    if (rw == 0) v *= sh.wq[q];
+                    if (!kWeighted && rw == 0) v *= sh.wq[q];
                     sh.rows[(q * 2 + rw) * row + e] = v;
                     e += blockDim.x;
                     while (e >= row) { e -= row; if (++rw == 2) { rw = 0; ++q; } }
@@ -414,7 +458,7 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const do
                     for (int j = tid; j < qn * 2 * NC; j += blockDim.x) {
                         const int qq = j / (2 * NC), rr = (j / NC) % 2, c = j % NC;
                         T v = row_value(G, sh.desc[qq * 4 + 2 + rr], tb, g, 0, c);
-                        if (rr == 1) v *= sh.wq[qq];
+                        if (!kWeighted && rr == 1) v *= sh.wq[qq];
                         sh.onrow[(qq * 2 + rr) * NC + c] = v;
                     }
                 }
@@ -423,15 +467,13 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const do
             // phase 3: products
             if (ch != 1) {
                 for (int r = tid; r < g.Ns; r += blockDim.x) {
-                    T o[NC], accl[NC];
+                    T accl[NC];
 #pragma unroll
                     for (int c = 0; c < NC; ++c) accl[c] = (T)0;
                     for (int q = 0; q < qn; ++q) {
                         const T* A = sh.rows + (q * 2) * row + r * NC;
                         const T* B = sh.rows + (q * 2 + 1) * row + r * NC;
-                        if (ch == 0) s_product<T, NC>(A, B, o); else u_product<T, NC>(A, B, o);
-#pragma unroll
-                        for (int c = 0; c < NC; ++c) accl[c] += o[c];
+                        if (ch == 0) su_product_acc<T, NC, -1>(A, B, accl); else su_product_acc<T, NC, 1>(A, B, accl);
                     }
 #pragma unroll
                     for (int c = 0; c < NC; ++c) sh.acc[r * NC + c] += accl[c];
@@ -462,7 +504,7 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const do
                         for (int k = 0; k < NC; ++k) Cp[k] = C0[perm_of(pon, k)];
 #pragma unroll
                         for (int c = 0; c < NC; ++c)
-                            accl[c] += A[c] * onsite_factor<T, NC>(Cp, c) + onsite_factor<T, NC>(D, c) * B[c];
+                            accl[c] = fmadd(A[c], onsite_factor<T, NC>(Cp, c), fmadd(onsite_factor<T, NC>(D, c), B[c], accl[c]));
                     }
 #pragma unroll
                     for (int c = 0; c < NC; ++c) sh.acc[r * NC + c] += accl[c];
@@ -694,7 +736,7 @@ __device__ void t_channel_tc(const Geo& g, const Tabs& tb, const float* __restri
                 }
 #pragma unroll
                 for (int c = 0; c < NC; ++c)
-                    racc[c] += A[c] * onsite_factor<float, NC>(Cp, c) + onsite_factor<float, NC>(D, c) * B[c];
+                    racc[c] = fmadd(A[c], onsite_factor<float, NC>(Cp, c), fmadd(onsite_factor<float, NC>(D, c), B[c], racc[c]));
             }
         }
     }
@@ -861,19 +903,17 @@ __device__ void gamma_rhs_f32_triple(const Geo& g, const Tabs& tb, const float* 
                 if (site_on) {
                     const int r = my_r;
                     for (int q = my_g; q < qn; q += NG) {
-                        float o[NC], A[NC], B[NC];
+                        float A[NC], B[NC];
 #pragma unroll
                         for (int c = 0; c < NC; ++c) {
                             A[c] = sh.rows[(q * 2) * rowp + c * nsp + r];
                             B[c] = sh.rows[(q * 2 + 1) * rowp + c * nsp + r];
                         }
-                        if (ch == 0) s_product<float, NC>(A, B, o); else u_product<float, NC>(A, B, o);
-#pragma unroll
-                        for (int c = 0; c < NC; ++c) racc[c] += o[c];
+                        if (ch == 0) su_product_acc<float, NC, -1>(A, B, racc); else su_product_acc<float, NC, 1>(A, B, racc);
                     }
                 } else if (!site_reg) {
                     for (int r = tid; r < g.Ns; r += blockDim.x) {
-                        float o[NC], accl[NC], A[NC], B[NC];
+                        float accl[NC], A[NC], B[NC];
 #pragma unroll
                         for (int c = 0; c < NC; ++c) accl[c] = 0.0f;
                         for (int q = 0; q < qn; ++q) {
@@ -882,9 +922,7 @@ __device__ void gamma_rhs_f32_triple(const Geo& g, const Tabs& tb, const float* 
                                 A[c] = sh.rows[(q * 2) * rowp + c * nsp + r];
                                 B[c] = sh.rows[(q * 2 + 1) * rowp + c * nsp + r];
                             }
-                            if (ch == 0) s_product<float, NC>(A, B, o); else u_product<float, NC>(A, B, o);
-#pragma unroll
-                            for (int c = 0; c < NC; ++c) accl[c] += o[c];
+                            if (ch == 0) su_product_acc<float, NC, -1>(A, B, accl); else su_product_acc<float, NC, 1>(A, B, accl);
                         }
 #pragma unroll
                         for (int c = 0; c < NC; ++c) sh.acc[r * NC + c] += accl[c];
@@ -950,7 +988,7 @@ __device__ void gamma_rhs_f32_triple(const Geo& g, const Tabs& tb, const float* 
                         }
 #pragma unroll
                         for (int c = 0; c < NC; ++c)
-                            racc[c] += A[c] * onsite_factor<float, NC>(Cp, c) + onsite_factor<float, NC>(D, c) * B[c];
+                            racc[c] = fmadd(A[c], onsite_factor<float, NC>(Cp, c), fmadd(onsite_factor<float, NC>(D, c), B[c], racc[c]));
                     }
                 } else if (!site_reg) {
                     for (int r = tid; r < g.Ns; r += blockDim.x) {
@@ -969,7 +1007,7 @@ __device__ void gamma_rhs_f32_triple(const Geo& g, const Tabs& tb, const float* 
                             }
 #pragma unroll
                             for (int c = 0; c < NC; ++c)
-                                accl[c] += A[c] * onsite_factor<float, NC>(Cp, c) + onsite_factor<float, NC>(D, c) * B[c];
+                                accl[c] = fmadd(A[c], onsite_factor<float, NC>(Cp, c), fmadd(onsite_factor<float, NC>(D, c), B[c], accl[c]));
                         }
 #pragma unroll
                         for (int c = 0; c < NC; ++c) sh.acc[r * NC + c] += accl[c];

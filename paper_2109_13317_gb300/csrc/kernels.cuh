@@ -203,8 +203,45 @@ __device__ __forceinline__ void axis_weights_f(const Tabs& tb, const Geo& g, flo
     wx[1] = w1;
 }
 
-// Descriptor of Gamma(s, t, u).  ex_slot (0 s, 1 t, 2 u; -1 none) names an argument known
-// to be the mesh frequency w[ex_idx] (or 0, clamped to w[0]), which needs no interval search.
+// Corners of a descriptor whose exact axis EA (0 s, 1 t, 2 u) is known at compile time, so
+// that every per-axis index is static (the descriptor arithmetic stays in registers).
+// Corners are enumerated with the s axis outermost and the u axis innermost.
+template <int EA, typename T>
+__device__ __forceinline__ void desc_corners(double s, double t, double u, int ex_idx, bool flip, const Tabs& tb,
+                                             const Geo& g, Desc<T>& d) {
+    constexpr int A0 = EA == 0 ? 1 : 0, A1 = EA == 2 ? 1 : 2;
+    const double x0 = A0 == 0 ? s : t, x1 = A1 == 1 ? t : u;
+    int i0[2], i1[2], n0, n1;
+    T v0[2], v1[2];
+    axis_weights<T>(tb, g, x0, n0, i0, v0);
+    axis_weights<T>(tb, g, x1, n1, i1, v1);
+    const int row = g.nc * g.Ns;
+    int k = 0;
+#pragma unroll
+    for (int b0 = 0; b0 < 2; ++b0) {
+        if (b0 >= n0) break;
+#pragma unroll
+        for (int b1 = 0; b1 < 2; ++b1) {
+            if (b1 >= n1) break;
+            const int js = EA == 0 ? ex_idx : i0[b0];
+            const int jt = EA == 1 ? ex_idx : (A0 == 1 ? i0[b0] : i1[b1]);
+            const int ju = EA == 2 ? ex_idx : i1[b1];
+            const T wt = v0[b0] * v1[b1];
+            bool neg = flip;
+            int p;
+            if (js >= ju) p = pair_index(js, ju);
+            else { p = pair_index(ju, js); neg = !neg; }
+            d.off[k] = (p * g.N + jt) * row;
+            d.wd[k] = neg ? -wt : wt;
+            d.ws[k] = wt;
+            ++k;
+        }
+    }
+    d.n = k;
+}
+
+// Descriptor of Gamma(s, t, u).  ex_slot (0 s, 1 t, 2 u) names an argument known to be the
+// mesh frequency w[ex_idx] (or 0, clamped to w[0]), which needs no interval search.
 template <typename T>
 __device__ __forceinline__ void make_desc(double s, double t, double u, int ex_slot, int ex_idx, const Tabs& tb,
                                           const Geo& g, Desc<T>& d) {
@@ -213,32 +250,10 @@ __device__ __forceinline__ void make_desc(double s, double t, double u, int ex_s
     if (s < 0.0) { s = -s; swap ^= 1; }
     if (u < 0.0) { u = -u; swap ^= 1; }
     bool flip = false;
-    if (s < u) { double tmp = s; s = u; u = tmp; flip = true; if (ex_slot != 1 && ex_slot >= 0) ex_slot = 2 - ex_slot; }
-    int ix[3][2], nx[3];
-    T wx[3][2];
-    const double arg[3] = {s, t, u};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (a == ex_slot) { nx[a] = 1; ix[a][0] = ex_idx; wx[a][0] = (T)1; }
-        else axis_weights<T>(tb, g, arg[a], nx[a], ix[a], wx[a]);
-    }
-    const int row = g.nc * g.Ns;
-    int k = 0;
-    for (int a = 0; a < nx[0]; ++a)
-        for (int b = 0; b < nx[1]; ++b)
-            for (int c = 0; c < nx[2]; ++c) {
-                const int si = ix[0][a], ti = ix[1][b], ui = ix[2][c];
-                const T wt = wx[0][a] * wx[1][b] * wx[2][c];
-                bool neg = flip;
-                int p;
-                if (si >= ui) p = pair_index(si, ui);
-                else { p = pair_index(ui, si); neg = !neg; }
-                d.off[k] = (p * g.N + ti) * row;
-                d.wd[k] = neg ? -wt : wt;
-                d.ws[k] = wt;
-                ++k;
-            }
-    d.n = k;
+    if (s < u) { double tmp = s; s = u; u = tmp; flip = true; if (ex_slot != 1) ex_slot = 2 - ex_slot; }
+    if (ex_slot == 0) desc_corners<0, T>(s, t, u, ex_idx, flip, tb, g, d);
+    else if (ex_slot == 1) desc_corners<1, T>(s, t, u, ex_idx, flip, tb, g, d);
+    else desc_corners<2, T>(s, t, u, ex_idx, flip, tb, g, d);
     d.swap = swap;
 }
 
