@@ -390,7 +390,7 @@ __device__ __forceinline__ void node_args(int ch, int rw, F x, F s, F t, F u, F 
 }
 
 template <typename T, int NC>
-__global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const double* __restrict__ w,
+__global__ void __launch_bounds__(kThreads, std::is_same<T, double>::value ? 6 : 1) k_gamma_rhs(Geo g, Tabs tb, const double* __restrict__ w,
                                                         const T* __restrict__ G, const double* __restrict__ nx,
                                                         const T* __restrict__ nW, const int* __restrict__ ncount,
                                                         T* __restrict__ dG) {
@@ -409,6 +409,20 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const do
 
     for (int o = tid; o < row; o += blockDim.x) sh.acc[o] = (T)0;
     for (int o = tid; o < tb.nprod; o += blockDim.x) sh.part[o] = (T)0;
+    // per-site products: thread (site my_r, node group my_g) takes every NG-th node of a block
+    // and keeps its partial sums in registers for the whole channel
+    const bool site_reg = g.Ns <= (int)blockDim.x;
+    const int NG = site_reg ? min((int)blockDim.x / g.Ns, kQC) : 1;
+    const int my_r = tid % g.Ns, my_g = tid / g.Ns;
+    const bool site_on = site_reg && my_g < NG;
+    // FP64: lattice-sum integrals of the products tid + k blockDim held in registers across the
+    // t channel when every thread owns at most kPR products
+    constexpr int kPR = 8;
+    constexpr bool kRegT = std::is_same<T, double>::value;
+    const bool preg = kRegT && tb.nprod <= kPR * (int)blockDim.x;
+    double pacc[kPR];
+#pragma unroll
+    for (int k = 0; k < kPR; ++k) pacc[k] = 0.0;
 
     for (int ch = 0; ch < 3; ++ch) {
         const int vi = ch == 0 ? si : (ch == 1 ? ti : ui);
@@ -417,6 +431,9 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const do
         const double* X = nx + (size_t)cidx * g.nmax;
         const T* Wp = nW + (size_t)cidx * g.nmax;
         const int nrow = ch == 1 ? 4 : 2;
+        T racc[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) racc[c] = (T)0;
         for (int q0 = 0; q0 < nq; q0 += kQC) {
             const int qn = min(kQC, nq - q0);
             __syncthreads();
@@ -466,7 +483,13 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const do
             __syncthreads();
             // phase 3: products
             if (ch != 1) {
-                for (int r = tid; r < g.Ns; r += blockDim.x) {
+                if (site_on)
+                    for (int q = my_g; q < qn; q += NG) {
+                        const T* A = sh.rows + (q * 2) * row + my_r * NC;
+                        const T* B = sh.rows + (q * 2 + 1) * row + my_r * NC;
+                        if (ch == 0) su_product_acc<T, NC, -1>(A, B, racc); else su_product_acc<T, NC, 1>(A, B, racc);
+                    }
+                for (int r = site_reg ? g.Ns : tid; r < g.Ns; r += blockDim.x) {
                     T accl[NC];
 #pragma unroll
                     for (int c = 0; c < NC; ++c) accl[c] = (T)0;
@@ -481,7 +504,27 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const do
             } else {
                 // lattice sum: every distinct product (row A entry, row B entry) integrated over
                 // the nodes of this block; each product is owned by one thread across blocks
-                for (int o = tid; o < tb.nprod; o += blockDim.x) {
+                if constexpr (kRegT) {
+                    if (preg) {
+                        int ia[kPR], ib[kPR];
+#pragma unroll
+                        for (int k = 0; k < kPR; ++k) {
+                            const int o = tid + k * (int)blockDim.x;
+                            const int2 pr = o < tb.nprod ? tb.prod[o] : make_int2(-1, 0);
+                            ia[k] = pr.x;
+                            ib[k] = pr.y;
+                        }
+#pragma unroll 1
+                        for (int q = 0; q < qn; ++q) {
+                            const double* Ar = reinterpret_cast<const double*>(sh.rows) + (q * 2) * row;
+                            const double* Br = Ar + row;
+#pragma unroll
+                            for (int k = 0; k < kPR; ++k)
+                                if (ia[k] >= 0) pacc[k] = fma(Ar[ia[k]], Br[ib[k]], pacc[k]);
+                        }
+                    }
+                }
+                for (int o = preg ? tb.nprod : tid; o < tb.nprod; o += blockDim.x) {
                     const int2 pr = tb.prod[o];
                     T a = (T)0;
                     for (int q = 0; q < qn; ++q)
@@ -489,7 +532,22 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const do
                     sh.part[o] += a;
                 }
                 // on-site terms
-                for (int r = tid; r < g.Ns; r += blockDim.x) {
+                if (site_on) {
+                    const int pon = tb.onsite_perm[my_r];
+                    for (int q = my_g; q < qn; q += NG) {
+                        const T* A = sh.rows + (q * 2) * row + my_r * NC;
+                        const T* B = sh.rows + (q * 2 + 1) * row + my_r * NC;
+                        const T* C0 = sh.onrow + (q * 2) * NC;
+                        const T* D = sh.onrow + (q * 2 + 1) * NC;
+                        T Cp[NC];
+#pragma unroll
+                        for (int k = 0; k < NC; ++k) Cp[k] = C0[perm_of(pon, k)];
+#pragma unroll
+                        for (int c = 0; c < NC; ++c)
+                            racc[c] = fmadd(A[c], onsite_factor<T, NC>(Cp, c), fmadd(onsite_factor<T, NC>(D, c), B[c], racc[c]));
+                    }
+                }
+                for (int r = site_reg ? g.Ns : tid; r < g.Ns; r += blockDim.x) {
                     const int pon = tb.onsite_perm[r];
                     T accl[NC];
 #pragma unroll
@@ -511,7 +569,28 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs(Geo g, Tabs tb, const do
                 }
             }
         }
+        if (site_reg) {
+            // combine the node groups' register partials in a fixed order (scratch: the rows)
+            __syncthreads();
+            T* scr = sh.rows;
+            if (site_on)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) scr[(my_g * NC + c) * g.Ns + my_r] = racc[c];
+            __syncthreads();
+            for (int o = tid; o < row; o += blockDim.x) {
+                const int r = o / NC, c = o % NC;
+                T a = (T)0;
+                for (int k = 0; k < NG; ++k) a += scr[(k * NC + c) * g.Ns + r];
+                sh.acc[o] += a;
+            }
+        }
     }
+    if (preg)
+#pragma unroll
+        for (int k = 0; k < kPR; ++k) {
+            const int o = tid + k * (int)blockDim.x;
+            if (o < tb.nprod) sh.part[o] = (T)pacc[k];
+        }
     __syncthreads();
     for (int o = tid; o < row; o += blockDim.x) {
         const int r = o / NC, c = o % NC;
