@@ -863,6 +863,9 @@ __device__ void gamma_rhs_f32_triple(const Geo& g, const Tabs& tb, const float* 
                                      const int qc, TcCta* tcs = nullptr) {
     static_assert(!TC || (NC == 2 && DENSE), "tensor-core lattice sum: SU2 dense contraction only");
     const int nsp = g.nsp, nsp4 = nsp >> 2, rowp = NC * nsp;
+    // n / nsp4 as __umulhi(n, div4) with div4 = ceil(2^32 / nsp4): exact for n nsp4 < 2^32
+    // (nsp4 = 1 is taken separately: its multiplier does not fit 32 bits)
+    const unsigned div4 = nsp4 > 1 ? (unsigned)((0x100000000ULL + (unsigned long long)nsp4 - 1) / (unsigned long long)nsp4) : 0u;
     ShF<NC, DENSE> sh;
     {
         size_t off = 0;
@@ -933,15 +936,20 @@ __device__ void gamma_rhs_f32_triple(const Geo& g, const Tabs& tb, const float* 
                 const int exs = ch == 0 ? 0 : (ch == 2 ? 2 : (rw < 2 ? 1 : 2));
                 DescF dl;
                 make_desc4(a, b, c, exs, vi, tb, g, rowp, dl);
+                if (rw == 0 || rw == 3) {   // the node weight goes into the corner weights
+                    const float wn = Wp[q0 + q];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) { dl.wd[k] *= wn; dl.ws[k] *= wn; }
+                }
                 store_desc4(&sh.desc[q * 4 + rw], dl, tid & 31);
-                if (rw == 0) sh.wq[q] = Wp[q0 + q];
             }
             __syncthreads();
-            // rows: four padded sites per item; row 0 carries the node weight
+            // rows: four padded sites per item; row 0 (and on-site row 1) carry the node weight
             const int nitems = qn * 2 * NC * nsp4;
             for (int it = tid; it < nitems; it += blockDim.x) {
-                const int r4 = it % nsp4;
-                int t2 = it / nsp4;
+                const int t2f = nsp4 > 1 ? (int)__umulhi((unsigned)it, div4) : it;   // it / nsp4
+                const int r4 = it - t2f * nsp4;
+                int t2 = t2f;
                 const int c = t2 % NC;
                 t2 /= NC;
                 const int rw = t2 & 1, q = t2 >> 1;
@@ -958,10 +966,6 @@ __device__ void gamma_rhs_f32_triple(const Geo& g, const Tabs& tb, const float* 
                 v.y = wv.x * g0.y + wv.y * g1.y + wv.z * g2.y + wv.w * g3.y;
                 v.z = wv.x * g0.z + wv.y * g1.z + wv.z * g2.z + wv.w * g3.z;
                 v.w = wv.x * g0.w + wv.y * g1.w + wv.z * g2.w + wv.w * g3.w;
-                if (rw == 0) {
-                    const float wq = sh.wq[q];
-                    v.x *= wq; v.y *= wq; v.z *= wq; v.w *= wq;
-                }
                 *reinterpret_cast<float4*>(sh.rows + (q * 2 + rw) * rowp + c * nsp + 4 * r4) = v;
             }
             if (ch == 1) {
@@ -973,7 +977,6 @@ __device__ void gamma_rhs_f32_triple(const Geo& g, const Tabs& tb, const float* 
                     float v = 0.0f;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) v += wgt[k] * base[d.off[k]];
-                    if (rr == 1) v *= sh.wq[qq];
                     sh.onrow[(qq * 2 + rr) * NC + c] = v;
                 }
             }
