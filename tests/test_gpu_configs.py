@@ -98,3 +98,69 @@ def test_honeycomb_hk_L5_xyz_rhs():
         for c in range(fl.n_comp):
             assert _rel(got[:, :, c], exp[:, :, c]) < tol
         fl.close()
+
+
+def _sampled_parity(of, lat, fl, lam, tol, n_random=40, seed=0):
+    """The GPU right-hand side at cutoff lam against the oracle's values of sampled stored
+    entries (the mesh corners, the s = u diagonal and random triples, random sites)."""
+    dg, dG = fl.rhs(lam)
+    torch.cuda.synchronize()
+    dG = dG.cpu().numpy().reshape(fl.npair, fl.N, fl.n_comp, lat.N_s)
+    reps = lat.representatives()
+    rng = np.random.default_rng(seed)
+    N = fl.N
+    picks = [(0, 0, 0), (N - 1, N - 1, N - 1), (N - 1, 0, 0), (N - 1, N - 1, 0), (N // 2, N // 2, 1)]
+    picks += [tuple(sorted(rng.integers(0, N, 2))[::-1]) + (int(rng.integers(0, N)),) for _ in range(n_random)]
+    ent, rs = [], []
+    for (si, ui, ti) in picks:
+        r = int(rng.integers(0, lat.N_s))
+        k = of.find(0, reps[r][:3], int(reps[r][3]))
+        assert k >= 0
+        ent.append((0, k, si, ti, ui))
+        rs.append(r)
+    ent = np.array(ent)
+    out = of.rhs_entries(lam, ent)
+    dg_o = of.prepare(lam)
+    assert _rel(dg.cpu().numpy(), dg_o) < max(tol, 1e-10)
+    cm = gpu_comp_map(fl.n_comp)
+    scale = np.abs(out).max()
+    assert scale > 0
+    for (b, k, si, ti, ui), r, o in zip(ent, rs, out):
+        p = si * (si + 1) // 2 + ui
+        for c, oc in enumerate(cm):
+            assert abs(dG[p, ti, c, r] - o[oc]) <= tol * scale, (si, ti, ui, r, c, dG[p, ti, c, r], o[oc])
+
+
+@pytest.mark.parametrize("prec,tol", [(sr.SR_FP64, 1e-10), (sr.SR_FP32_MIXED, 1e-3)])
+def test_pyrochlore_full_range_sampled(prec, tol):
+    """Pyrochlore J1 at the configuration's full range L = 6 (N_s = 48, N_tot = 459) with the
+    frequency mesh reduced to 8 points (0.001..100) so that the oracle's unreduced storage fits:
+    sampled entries of the right-hand side on a synthetic symmetric state."""
+    from tests.helpers import synthetic_state
+    cfg = W.config("pyrochlore_L6")
+    mesh = O.mesh_exponential(8, cfg.w_min, cfg.w_max)
+    of = O.OracleFlow(cfg.model, cfg.L, mesh)
+    gam, G = synthetic_state(of, cfg.model, seed=4)
+    of.set_state(gam, G)
+    lat = sr.Lattice.from_model(cfg.model, cfg.L)
+    assert lat.N_s == 48 and lat.N_tot == 459
+    fl = sr.Flow(lat, mesh, 1.0, prec)
+    _load(fl, lat, of, 1.0)
+    _sampled_parity(of, lat, fl, 0.9, tol)
+    fl.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(sr.SR_FP64, 1e-10), (sr.SR_FP32_MIXED, 1e-3)])
+def test_heisenberg_kitaev_full_size_sampled(prec, tol):
+    """Honeycomb Heisenberg-Kitaev (XYZ) at the configuration's full size (L = 5, N = 32,
+    0.005..50): the first right-hand side of the flow (bare vertex at Lambda = 50, computed
+    independently by both sides) on sampled entries."""
+    cfg = W.config("honeycomb_hk_L5")
+    mesh = O.mesh_exponential(cfg.n_freq, cfg.w_min, cfg.w_max)
+    of = O.OracleFlow(cfg.model, cfg.L, mesh)
+    lat = sr.Lattice.from_model(cfg.model, cfg.L)
+    fl = sr.Flow(lat, mesh, cfg.lam_max, prec)
+    _sampled_parity(of, lat, fl, cfg.lam_max, tol, seed=1)
+    # and after a quarter of the cutoff range, on the same bare vertex
+    _sampled_parity(of, lat, fl, 0.25 * cfg.lam_max, tol, seed=2)
+    fl.close()
