@@ -115,6 +115,28 @@ def _dist():
     return ws, rank, local
 
 
+def _sync_all(torch, ws: int, cuda: bool = True):
+    """Barrier over the ranks (one flow replica per GPU) and a device synchronize."""
+    if ws > 1:
+        torch.distributed.barrier()
+    if cuda:
+        torch.cuda.synchronize()
+
+
+def _max_over_ranks(torch, value: float, ws: int, device="cuda") -> float:
+    """The largest per-rank value (the job's time is its slowest rank's)."""
+    if ws == 1:
+        return value
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_throughput(units_per_rank: float, ws: int, t_ms: float) -> float:
+    """Whole-job units per second: every rank processed units_per_rank in t_ms (the max)."""
+    return units_per_rank * ws / (t_ms * 1e-3)
+
+
 def _algorithmic_flops(counts: np.ndarray, N: int, Ns: int, nc: int, P: int, nprod: int) -> float:
     """Floating-point operations of one vertex-flow launch, counted as the natural evaluation
     of the flow equations (an FMA = 2 flop).  Per stored triple (s, t, u) and integration node:
@@ -255,7 +277,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def _measure_precision(sr, torch, cfg, lat, mesh, prec, steps, warmup, lams, flush, kgrid, sampler=None):
+def _measure_precision(sr, torch, cfg, lat, mesh, prec, steps, warmup, lams, flush, kgrid, sampler=None, sync=None):
     """Advance to mid-flow, warm up, then time `steps` Euler steps (+ chi) with CUDA events.
     From Lambda ~ 1 on, the steps follow a fine log grid (2000 steps per four decades), so any
     number of timed steps stays mid-flow."""
@@ -276,6 +298,8 @@ def _measure_precision(sr, torch, cfg, lat, mesh, prec, steps, warmup, lams, flu
     stream = torch.cuda.current_stream()
     fl.profile_enable(True)
     ev = []
+    if sync:
+        sync()
     torch.cuda.synchronize()
     if sampler:
         sampler.start()
@@ -291,6 +315,8 @@ def _measure_precision(sr, torch, cfg, lat, mesh, prec, steps, warmup, lams, flu
         ev.append((a, b))
         i += 1
     torch.cuda.synchronize()
+    if sync:
+        sync()
     if sampler:
         sampler.stop()
     ms = [a.elapsed_time(b) for a, b in ev]
@@ -449,21 +475,13 @@ def run_ours(args):
     prec = sr.SR_FP64 if args.precision == "fp64" else sr.SR_FP32_MIXED
     sampler = ClockSampler(local) if rank == 0 else None
 
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
+    # the timed steps are bracketed by a barrier over the ranks and a synchronize on both sides
     fl, ms, kms, kn, counts, lam_rng, i_end = _measure_precision(sr, torch, cfg, lat, mesh, prec, args.steps,
-                                                                 args.warmup, lams, flush, kgrid, sampler)
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    t_step = sum(ms) / len(ms)  # ms
-    if ws > 1:
-        t = torch.tensor([t_step], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(t.item())
+                                                                 args.warmup, lams, flush, kgrid, sampler,
+                                                                 sync=lambda: _sync_all(torch, ws))
+    t_step = _max_over_ranks(torch, sum(ms) / len(ms), ws)  # ms
     n_ent = fl.n_gamma
-    value = n_ent * ws / (t_step * 1e-3)
+    value = _job_throughput(n_ent, ws, t_step)
 
     # roofline of the dominant kernel (vertex flow)
     flops = _algorithmic_flops(counts, fl.N, lat.N_s, fl.n_comp, lat.P, fl.lattice_sum_products())
