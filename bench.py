@@ -549,7 +549,7 @@ def run_ours(args):
         e32["chi_max_rel_err_vs_fp64_all_outputs"] = float(np.abs(cm32 - cm64).max() / np.abs(cm64).max())
         e32["speedup_vs_fp64"] = e64["seconds"] / e32["seconds"]
         ff["euler"] = {"fp64": e64, "fp32_mixed": e32}
-        a64, _, _ = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP64, kgrid, "rk", budget_s=90.0)
+        a64, _, _ = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP64, kgrid, "rk", budget_s=110.0)
         a32, _, _ = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP32_MIXED, kgrid, "rk", budget_s=30.0)
         ff["adaptive"] = {"fp64": a64, "fp32_mixed": a32}
         extra["full_flow"] = ff

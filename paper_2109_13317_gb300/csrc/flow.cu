@@ -865,7 +865,7 @@ __device__ void gamma_rhs_f32_triple(const Geo& g, const Tabs& tb, const float* 
     const int nsp = g.nsp, nsp4 = nsp >> 2, rowp = NC * nsp;
     // n / nsp4 as __umulhi(n, div4) with div4 = ceil(2^32 / nsp4): exact for n nsp4 < 2^32
     // (nsp4 = 1 is taken separately: its multiplier does not fit 32 bits)
-    const unsigned div4 = nsp4 > 1 ? (unsigned)((0x100000000ULL + (unsigned long long)nsp4 - 1) / (unsigned long long)nsp4) : 0u;
+    const unsigned div4 = g.div4;
     ShF<NC, DENSE> sh;
     {
         size_t off = 0;
@@ -880,7 +880,7 @@ __device__ void gamma_rhs_f32_triple(const Geo& g, const Tabs& tb, const float* 
         sh.cacc = (float*)take(sizeof(float) * (DENSE ? NC * nsp * nsp : tb.nprod));
     }
     const int tid = threadIdx.x;
-    int si = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
+    int si = (int)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);   // guess, corrected below
     while ((si + 1) * (si + 2) / 2 <= p) ++si;
     while (si * (si + 1) / 2 > p) --si;
     const int ui = p - si * (si + 1) / 2;
@@ -1666,6 +1666,10 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
     g.nent = (long)g.npair * n_freq * g.nc * g.Ns;
     g.nsp = (g.Ns + 3) & ~3;
     g.nentp = (long)g.npair * n_freq * g.nc * g.nsp;
+    {
+        const unsigned long long d = (unsigned long long)(g.nsp / 4);
+        g.div4 = d > 1 ? (unsigned)((0x100000000ULL + d - 1) / d) : 0u;
+    }
     if ((long)g.npair * n_freq * g.nc * g.Ns >= (1L << 31)) return fail(SR_EINVAL, "vertex too large for 32-bit offsets");
 
     // lattice tables

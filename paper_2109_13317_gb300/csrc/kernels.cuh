@@ -27,6 +27,7 @@ struct Geo {
     long nentp;       // entries of the padded FP32 shadow
     float log2w0;     // log2(w[0])
     float inv_dlog2;  // (N - 1) / log2(w[N-1] / w[0]): interval guess for a log-spaced mesh
+    unsigned div4;    // ceil(2^32 / (nsp / 4)) (0 when nsp = 4): n / (nsp / 4) = __umulhi(n, div4)
 };
 
 // Tables of the lattice (device pointers).

@@ -120,6 +120,16 @@ def square_j1j2(J1: float = 1.0, J2: float = 0.5) -> Model:
     return m
 
 
+def cubic_j1j2(J1: float = 1.0, J2: float = 0.0) -> Model:
+    """Simple-cubic J1-J2 Heisenberg model of the paper's first worked example: J1 on the three
+    bonds of the unit cell, J2 on the six face diagonals per cell."""
+    m = nn_heisenberg(cubic(), J1)
+    if J2 != 0.0:
+        m.couplings += [Coupling((0, 0, 0, 0), (d0, d1, d2, 0), J2 * I3)
+                        for (d0, d1, d2) in ((0, 1, -1), (0, 1, 1), (1, -1, 0), (1, 0, -1), (1, 0, 1), (1, 1, 0))]
+    return m
+
+
 def honeycomb_kitaev(J: float = 0.2, K: float = -1.0) -> Model:
     """Heisenberg-Kitaev model of the paper's model listing: Heisenberg J on the three bonds,
     Kitaev K as xx, yy, zz on the three bond directions."""
@@ -166,7 +176,7 @@ class FlowConfig:
 
 
 def config(name: str) -> FlowConfig:
-    """The five workload configurations, by short name."""
+    """The workload configurations, by short name."""
     if name == "square_j1_L3":
         return FlowConfig(name, nn_heisenberg(square(), 1.0), 3, 16, 0.005, 50.0, 50.0, 0.05, 100)
     if name == "square_j1j2_L7":
@@ -174,6 +184,9 @@ def config(name: str) -> FlowConfig:
                           method="rk", rtol=1e-6, atol=1e-10)
     if name == "pyrochlore_L6":
         return FlowConfig(name, nn_heisenberg(pyrochlore(), 1.0), 6, 64, 0.001, 100.0, 100.0, 0.01, 400)
+    if name == "cubic_j1j2_L7":
+        # the paper's first worked example (J2 = 0); cutoff ratio 0.98 per step from 50 to 0.01
+        return FlowConfig(name, cubic_j1j2(1.0, 0.0), 7, 64, 0.005, 50.0, 50.0, 0.01, 422)
     if name == "honeycomb_hk_L5":
         return FlowConfig(name, honeycomb_kitaev(0.2, -1.0), 5, 32, 0.005, 50.0, 50.0, 0.05, 200)
     raise KeyError(name)
@@ -194,6 +207,13 @@ def batched_instances(seed: int = 0, n: int = 64):
             L = int(rng.integers(4, 9))
             out.append(FlowConfig(f"kg{i}", nn_heisenberg(kagome(), 1.0), L, nw, 0.005, 50.0, 50.0, 0.05, 100))
     return out
+
+
+def lambda_geometric(lam_max: float, lam_min: float, step: float) -> np.ndarray:
+    """The paper's exponential cutoff discretisation with a fixed ratio: lam_max step^n for
+    n = 0, 1, ... while the value is >= lam_min."""
+    n = int(math.floor(math.log(lam_min / lam_max) / math.log(step) + 1e-9))
+    return lam_max * step ** np.arange(n + 1)
 
 
 def lambda_list(lam_max: float, lam_min: float, n_steps: int) -> np.ndarray:
