@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from paper_2109_13317_gb300.analysis import flow_breakdown
+from paper_2109_13317_gb300.analysis import flow_breakdown, log_slope
 
 LAMS = 50.0 * 0.98 ** np.arange(1, 422)
 
@@ -22,17 +22,25 @@ def test_peak_is_detected_at_its_cutoff():
     assert abs(got - LAMS[LAMS <= lc][0]) < 1e-12
 
 
-def test_kink_is_detected():
+def test_kink_without_decrease_is_not_a_peak():
     lc = 0.3
-    # growing flow whose slope changes abruptly at lc but keeps growing (no peak)
+    # growing flow whose slope changes abruptly at lc but keeps growing: no peak
     chi = np.where(LAMS > lc, 1.0 / (LAMS + 0.1), 1.0 / (lc + 0.1) + 0.2 * (lc - LAMS))
-    got = flow_breakdown(LAMS, chi)
-    assert got is not None and abs(np.log(got / lc)) < 0.05
+    assert flow_breakdown(LAMS, chi) is None
+    s = log_slope(LAMS, chi)
+    assert s.shape == (LAMS.size - 1,)
+    above, below = s[LAMS[1:] > 1.2 * lc], s[LAMS[1:] < 0.8 * lc]
+    assert above.min() > 2 * below.max() > 0
 
 
-def test_noise_below_the_margin_is_not_a_peak():
+def test_log_slope_of_a_power_law():
+    chi = LAMS ** -1.5
+    np.testing.assert_allclose(log_slope(LAMS, chi), 1.5, rtol=1e-12)
+
+
+def test_wiggles_below_the_drop_margin_are_not_a_peak():
     chi = 1.0 / (LAMS + 0.2)
-    chi = chi * (1 + 1e-6 * np.cos(np.arange(LAMS.size)))
+    chi = chi * (1 + 5e-3 * np.cos(np.arange(LAMS.size)))
     assert flow_breakdown(LAMS, chi) is None
 
 
@@ -40,4 +48,4 @@ def test_bad_input():
     with pytest.raises(ValueError):
         flow_breakdown(LAMS[::-1], 1.0 / LAMS[::-1])
     with pytest.raises(ValueError):
-        flow_breakdown(LAMS[:3], LAMS[:3])
+        flow_breakdown(LAMS[:2], LAMS[:2])
