@@ -49,7 +49,25 @@ def _args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-flow", action="store_true", help="skip the full adaptive Lambda flow")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched coupling sweep")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=["square_j1j2_L7", "square_j1_L3", "pyrochlore_L6", "honeycomb_hk_L5"],
+                    help="configuration to measure (the default is the headline workload)")
     return ap.parse_args()
+
+
+def _describe(cfg):
+    """Lattice, couplings and spin core of a configuration, for the JSON line."""
+    m = cfg.model
+    js = sorted({round(float(c.M[2, 2]), 6) for c in m.couplings})
+    return {"lattice": f"{m.cell.name}, couplings zz in {js}", "core": m.backend}
+
+
+def _oracle_fits(cfg, limit_bytes: float = 1e9) -> bool:
+    """Whether the oracle's translation-only vertex of the configuration stays below limit_bytes."""
+    from oracle import oracle as O
+    of = O.OracleFlow(cfg.model, cfg.L, O.mesh_exponential(2, cfg.w_min, cfg.w_max))
+    n = cfg.n_freq
+    return 8.0 * sum(of.nsite) * 4 * n * n * (n + 1) / 2 <= limit_bytes
 
 
 class ClockSampler:
@@ -233,16 +251,19 @@ def _cpu_baseline(cfg, target_s: float = 12.0):
     # translation-only vertex is one equation, as for the GPU's reduced vertex
     return {"value": m / dt, "unit": UNIT, "cores": O.OracleFlow.threads(), "kind": "oracle",
             "sample": f"{m} random stored vertex entries (RHS of each, incl. self-energy flow) of the "
-                      f"{WORKLOAD} workload at Lambda=0.9 on a synthetic symmetric state; {dt:.1f} s"}
+                      f"{cfg.name} workload at Lambda=0.9 on a synthetic symmetric state; {dt:.1f} s"}
 
 
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    cfg = W.config(WORKLOAD)
+    cfg = W.config(args.workload)
     from oracle import oracle as O
     from tests.helpers import synthetic_state
+    if args.workload != WORKLOAD and not _oracle_fits(cfg):
+        print(json.dumps({"impl": "reference", "unavailable": f"the oracle's unreduced vertex of {cfg.name} exceeds 1 GB"}))
+        return
     mesh = O.mesh_exponential(cfg.n_freq, cfg.w_min, cfg.w_max)
     of = O.OracleFlow(cfg.model, cfg.L, mesh)
     gam, G = synthetic_state(of, cfg.model, seed=3)
@@ -270,9 +291,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_entries_per_step": m, "lambda": 0.9},
+            "data": "synthetic", "config": {"workload": cfg.name, "sample_entries_per_step": m, "lambda": 0.9},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": O.OracleFlow.threads(), "kind": "oracle",
-                             "sample": f"{m} random stored entries per step of {WORKLOAD} at Lambda=0.9"},
+                             "sample": f"{m} random stored entries per step of {cfg.name} at Lambda=0.9"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -347,11 +368,18 @@ def _full_flow(sr, torch, cfg, lat, mesh, prec, kgrid, method="euler", n_steps=2
     complete = True
     for k, lam in enumerate(out_grid[1:]):
         if method == "euler":
-            for j in range(k * per_out, (k + 1) * per_out):
-                fl.step(float(lams[j + 1]), sr.SR_EULER)
-            reached = float(lams[(k + 1) * per_out])
+            try:
+                for j in range(k * per_out, (k + 1) * per_out):
+                    fl.step(float(lams[j + 1]), sr.SR_EULER)
+                reached = float(lams[(k + 1) * per_out])
+            except sr.SrError as e:   # the vertex overflowed (a flow breakdown): stop, no output
+                if e.status != 5:
+                    raise
+                reached = fl.lam
+                complete = False
+                break
         else:
-            fl.set_step_limit(50)
+            fl.set_step_limit(500)
             try:
                 reached = fl.step(float(lam), sr.SR_RK_ADAPTIVE, cfg.rtol, cfg.atol)
             except sr.SrError as e:
@@ -374,7 +402,7 @@ def _full_flow(sr, torch, cfg, lat, mesh, prec, kgrid, method="euler", n_steps=2
            "adaptive Dormand-Prince 5(4), rtol %g, atol %g, normwise error" % (cfg.rtol, cfg.atol),
            "seconds": a.elapsed_time(b) * 1e-3, "wall_seconds": wall, "rhs_evaluations": st["n_rhs"],
            "accepted": st["n_accept"], "rejected": st["n_reject"], "lambda_reached": reached,
-           "complete": bool(complete), "chi_max_final": chimax[-1]}
+           "complete": bool(complete), "chi_max_final": chimax[-1] if chimax else None}
     return res, np.array(chimax), ck
 
 
@@ -456,6 +484,49 @@ def _tensor_core_variant(sr, torch, fl):
     return out
 
 
+def _gradient_timing(sr, torch, cfg, mesh):
+    """d chi(k_max, Lambda_min) / d(J, K) of the Heisenberg-Kitaev flow (200 Euler steps): the
+    reverse-mode adjoint with a checkpoint every 20 steps, the tangent-linear flow, and central
+    finite differences (h = 1e-5) of the FP64 flow; wall times and the agreement."""
+    import math
+    from paper_2109_13317_gb300.autograd import susceptibility, susceptibility_adjoint
+    cell, sites, B = W.honeycomb_kitaev_linear()
+    theta0 = np.array([0.2, -1.0])
+    lams = W.lambda_list(cfg.lam_max, cfg.lam_min, cfg.n_steps)
+    kmax = np.array([[0.0, 4.0 * math.pi / 3.0, 0.0]])
+
+    def grad(fn):
+        th = torch.tensor(theta0, dtype=torch.float64, requires_grad=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        chi = fn(th)
+        (g,) = torch.autograd.grad(chi[0], th)
+        torch.cuda.synchronize()
+        return g.numpy(), time.perf_counter() - t0
+
+    ga, ta = grad(lambda th: susceptibility_adjoint(th, cell, sites, B, cfg.L, mesh, lams, kmax, sr.SR_XYZ, every=20))
+    gt, tt = grad(lambda th: susceptibility(th, cell, sites, B, cfg.L, mesh, lams, kmax, sr.SR_XYZ))
+
+    def chi_at(theta):
+        lat = sr.Lattice.from_model(W.linear_model(cell, sites, B, theta), cfg.L)
+        fl = sr.Flow(lat, mesh, lams[0], sr.SR_FP64)
+        for lam in lams[1:]:
+            fl.step(float(lam), sr.SR_EULER)
+        c, _ = fl.measure(kmax, want_ij=False)
+        fl.close()
+        return float(c[0])
+    t0 = time.perf_counter()
+    h = 1e-5
+    gf = np.array([(chi_at(theta0 + h * e) - chi_at(theta0 - h * e)) / (2 * h) for e in np.eye(2)])
+    tf = time.perf_counter() - t0
+    return {"quantity": "d chi(k) / d(J, K) at k = (0, 4pi/3, 0), Lambda = 0.05, theta = (0.2, -1)",
+            "adjoint": {"grad": ga.tolist(), "seconds": ta, "checkpoint_every": 20},
+            "tangent": {"grad": gt.tolist(), "seconds": tt},
+            "central_fd": {"grad": gf.tolist(), "seconds": tf, "h": h},
+            "adjoint_vs_tangent_rel": float(np.abs(ga - gt).max() / np.abs(gt).max()),
+            "adjoint_vs_fd_rel": float(np.abs(ga - gf).max() / np.abs(gf).max())}
+
+
 def run_ours(args):
     import torch
     import paper_2109_13317_gb300 as sr
@@ -464,7 +535,8 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    cfg = W.config(WORKLOAD)
+    cfg = W.config(args.workload)
+    headline = args.workload == WORKLOAD
     mesh = sr.sr_frequency_mesh_exponential(cfg.n_freq, cfg.w_min, cfg.w_max)
     lat = sr.Lattice.from_model(cfg.model, cfg.L)
     lams = W.lambda_list(cfg.lam_max, cfg.lam_min, cfg.n_steps)
@@ -543,23 +615,32 @@ def run_ours(args):
 
     if not args.no_flow and prec == sr.SR_FP64:
         ff = {"lambda": [cfg.lam_max, cfg.lam_min], "outputs": 50}
-        e64, cm64, ck64 = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP64, kgrid, "euler")
-        e32, cm32, ck32 = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP32_MIXED, kgrid, "euler")
-        e32["chi_rel_err_vs_fp64_final"] = float(np.abs(ck32 - ck64).max() / np.abs(ck64).max())
-        e32["chi_max_rel_err_vs_fp64_all_outputs"] = float(np.abs(cm32 - cm64).max() / np.abs(cm64).max())
+        n_eu = 200 if cfg.method == "rk" else cfg.n_steps   # the configuration's Euler steps
+        # Euler flows run to the end (their cost is fixed by the configuration's steps)
+        e64, cm64, ck64 = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP64, kgrid, "euler", n_steps=n_eu, budget_s=1e9)
+        e32, cm32, ck32 = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP32_MIXED, kgrid, "euler", n_steps=n_eu,
+                                     budget_s=1e9)
+        if e32["complete"] and e64["complete"]:
+            e32["chi_rel_err_vs_fp64_final"] = float(np.abs(ck32 - ck64).max() / np.abs(ck64).max())
+        n_cmp = min(len(cm32), len(cm64))   # outputs both flows reached
+        e32["chi_max_rel_err_vs_fp64_all_outputs"] = float(np.abs(cm32[:n_cmp] - cm64[:n_cmp]).max() /
+                                                           np.abs(cm64[:n_cmp]).max())
         e32["speedup_vs_fp64"] = e64["seconds"] / e32["seconds"]
         ff["euler"] = {"fp64": e64, "fp32_mixed": e32}
-        a64, _, _ = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP64, kgrid, "rk", budget_s=110.0)
-        a32, _, _ = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP32_MIXED, kgrid, "rk", budget_s=30.0)
-        ff["adaptive"] = {"fp64": a64, "fp32_mixed": a32}
+        if cfg.method == "rk":
+            a64, _, _ = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP64, kgrid, "rk", budget_s=110.0)
+            a32, _, _ = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP32_MIXED, kgrid, "rk", budget_s=30.0)
+            ff["adaptive"] = {"fp64": a64, "fp32_mixed": a32}
         extra["full_flow"] = ff
+        if cfg.name == "honeycomb_hk_L5":
+            extra["gradient"] = _gradient_timing(sr, torch, cfg, mesh)
 
-    if not args.no_batch and rank == 0:
+    if not args.no_batch and rank == 0 and headline:
         extra["batched_sweep"] = _batched_sweep(sr, torch)
 
     clocks = sampler.summary() if sampler else None
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and not args.no_cpu and (headline or _oracle_fits(cfg)):
         try:
             cpu = _cpu_baseline(cfg)
         except Exception as e:  # the oracle is a baseline, never the product path
@@ -571,10 +652,10 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == sr.SR_FP64 else "f32-mixed", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "lattice": "square J1=1 J2=0.5", "range_L": cfg.L,
+            "config": {"workload": cfg.name, **_describe(cfg), "range_L": cfg.L,
                        "N_s": lat.N_s, "N_tot": lat.N_tot, "P": lat.P, "lattice_sum_products": fl.lattice_sum_products(),
                        "n_freq": cfg.n_freq,
-                       "freq_range": [cfg.w_min, cfg.w_max], "entries": n_ent, "core": "SU2",
+                       "freq_range": [cfg.w_min, cfg.w_max], "entries": n_ent,
                        "step": "Euler step (self-energy + vertex flow + update) + chi(k) on 64x64 k-grid",
                        "lambda_range_timed": [float(lam_rng[0]), float(lam_rng[1])],
                        "l2": "flushed between timed steps (256 MB write)",
