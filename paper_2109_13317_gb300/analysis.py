@@ -10,6 +10,12 @@ small cutoff, the first local maximum of chi_max after which chi_max falls by mo
 the steep growth of chi_max ending without a decrease -- is not a peak; `log_slope` gives
 d ln chi_max / d ln(1/Lambda) along the flow to look at it.
 
+A second diagnostic for subtle breakdowns is the scaling of the on-site correlation chi_ii with
+the truncation range L (Sec. 6.2): with short-ranged correlations chi_ii(Lambda) converges
+quickly in L; once correlations become long-ranged (Lambda < Lambda_c in an ordered system)
+the curves for different L separate.  `onsite_flow` records chi_ii along a flow and
+`range_spread` compares such records across ranges.
+
 Everything here is host-side bookkeeping over values the library measured.
 """
 from __future__ import annotations
@@ -77,3 +83,43 @@ def log_slope(lambdas: Sequence[float], chi_max: Sequence[float]) -> np.ndarray:
     lam = np.asarray(lambdas, dtype=np.float64)
     y = np.asarray(chi_max, dtype=np.float64)
     return -np.diff(np.log(y)) / np.diff(np.log(lam))
+
+
+def onsite_correlation(flow: Flow) -> float:
+    """The on-site spin correlation chi^{zz}_{ii} of the current state, averaged over the basis
+    sites (the first site of every basis site's list is the site itself)."""
+    _, chi_ij = flow.measure(None, want_ij=True)
+    c = chi_ij.cpu().numpy()
+    if c.shape[2] == 2:
+        return float(c[:, 0, 1].mean())            # SU2: component 1 is the spin part
+    return float(c[:, 0, 3].mean())                # XYZ: zz
+
+
+def onsite_flow(flow: Flow, lambdas: Sequence[float], method: int = SR_EULER, stop_on_nonfinite: bool = True):
+    """chi_ii after every step through `lambdas` (the first is the current cutoff): (cutoffs,
+    values).  A non-finite step ends the record (see run_susceptibility_flow)."""
+    lams: List[float] = []
+    vals: List[float] = []
+    for lam in list(lambdas)[1:]:
+        try:
+            flow.step(float(lam), method)
+        except SrError as e:
+            if stop_on_nonfinite and e.status == SR_ENONFINITE:
+                break
+            raise
+        lams.append(float(lam))
+        vals.append(onsite_correlation(flow))
+    return np.array(lams), np.array(vals)
+
+
+def range_spread(records) -> tuple:
+    """Relative spread (max - min) / mean of chi_ii across truncation ranges at the cutoffs all
+    records share; `records` is a sequence of (cutoffs, values) on one cutoff grid.  Returns
+    (cutoffs, spread)."""
+    n = min(len(r[0]) for r in records)
+    lam = np.asarray(records[0][0][:n])
+    for r in records:
+        if not np.allclose(r[0][:n], lam, rtol=0, atol=0):
+            raise ValueError("records must share their cutoff grid")
+    v = np.stack([np.asarray(r[1][:n]) for r in records])
+    return lam, (v.max(axis=0) - v.min(axis=0)) / np.abs(v.mean(axis=0))

@@ -49,3 +49,15 @@ def test_bad_input():
         flow_breakdown(LAMS[::-1], 1.0 / LAMS[::-1])
     with pytest.raises(ValueError):
         flow_breakdown(LAMS[:2], LAMS[:2])
+
+
+def test_range_spread():
+    from paper_2109_13317_gb300.analysis import range_spread
+    lam = LAMS[:5]
+    recs = [(lam, np.array([1.0, 2.0, 3.0, 4.0, 5.0])), (lam, np.array([1.0, 2.0, 3.3, 4.0, 5.0])),
+            (lam[:4], np.array([1.0, 2.0, 2.7, 4.4]))]
+    l2, sp = range_spread(recs)
+    assert l2.shape == (4,)
+    np.testing.assert_allclose(sp, [0.0, 0.0, 0.6 / 3.0, 0.4 / (12.4 / 3)])
+    with pytest.raises(ValueError):
+        range_spread([(lam, lam), (lam * 1.01, lam)])
