@@ -429,6 +429,7 @@ def _batched_sweep(sr, torch, steps=20):
     b.run(window, use_graph=True, autotune=True)
     info = b.info()
     classes = b.classes()
+    parallel = b.parallel_classes
     batched_ms = info["run_ms"]
     after_b = [f.get_state()[1] for f in flows]
     for f, (g, G) in zip(flows, saved):
@@ -451,7 +452,7 @@ def _batched_sweep(sr, torch, steps=20):
             "entries": n_ent, "steps_timed": steps, "lambda_window": [float(window[0]), float(window[-1])],
             "batched_ms_per_step": batched_ms / steps, "batched_entries_per_s": n_ent * steps / (batched_ms * 1e-3),
             "sequential_ms_per_step": seq_ms / steps, "sequential_entries_per_s": n_ent * steps / (seq_ms * 1e-3),
-            "speedup": seq_ms / batched_ms, "size_classes": classes,
+            "speedup": seq_ms / batched_ms, "size_classes": classes, "parallel_classes": parallel,
             "max_rel_diff_batched_vs_sequential": diff}
 
 

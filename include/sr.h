@@ -268,6 +268,10 @@ sr_status sr_batch_classes(const sr_batch* batch, int* n_classes);
 sr_status sr_batch_class(const sr_batch* batch, int k, int* n_instances, long* units, int* smem_bytes, int* qc,
                          int* ctas_per_sm, double* tune_ms);
 
+/* Whether the classes' launches run as parallel graph branches (1) or one after another (0);
+ * the autotuner times both and keeps the faster (parallel without autotuning). */
+sr_status sr_batch_parallel_classes(const sr_batch* batch, int* parallel);
+
 sr_status sr_batch_destroy(sr_batch* batch);
 
 /* ---- measurement helpers (not part of the method) ---- */

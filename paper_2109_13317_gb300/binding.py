@@ -105,6 +105,7 @@ def load_library():
             "sr_batch_destroy": [vp],
             "sr_batch_classes": [vp, ip],
             "sr_batch_class": [vp, i, ip, lp, ip, ip, ip, dp],
+            "sr_batch_parallel_classes": [vp, ip],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -453,6 +454,12 @@ class Batch:
             out.append({"instances": ni.value, "units": u.value, "smem_bytes": sm.value, "node_block": qc.value,
                         "ctas_per_sm": ct.value, "tuned_ms": ms.value})
         return out
+
+    @property
+    def parallel_classes(self) -> bool:
+        v = C.c_int()
+        _check(self._lib.sr_batch_parallel_classes(self.h, C.byref(v)))
+        return bool(v.value)
 
     def close(self):
         if getattr(self, "h", None):

@@ -2300,7 +2300,7 @@ __global__ void k_nodes_b(const BInst* __restrict__ I, const double* __restrict_
 
 // One size class of instances: units [u_begin, u_end) (instances [i_begin, i_end)).
 template <int NC, bool DENSE>
-__global__ void __launch_bounds__(kThreads, 6) k_gamma_persistent(const BInst* __restrict__ I, int i_begin, int i_end,
+__global__ void __launch_bounds__(kThreads, 7) k_gamma_persistent(const BInst* __restrict__ I, int i_begin, int i_end,
                                                                long u_begin, long u_end,
                                                                unsigned long long* __restrict__ counter) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -2418,6 +2418,7 @@ struct sr_batch {
     std::vector<cudaStream_t> side;   // one per size class beyond the first
     std::vector<cudaEvent_t> join;
     cudaEvent_t fork = nullptr;
+    bool parallel = true;             // size classes as parallel branches (else one after another)
     ~sr_batch() {
         for (cudaStream_t s : side) cudaStreamDestroy(s);
         for (cudaEvent_t e : join) cudaEventDestroy(e);
@@ -2438,6 +2439,25 @@ static void launch_class(sr_batch* b, int k, cudaStream_t st) {
         k_gamma_persistent<4, false><<<grid, kThreads, c.smem, st>>>(b->dinst.p, c.i_begin, c.i_end, c.u_begin, c.u_end, ctr);
 }
 
+// The vertex flow of every size class: as parallel branches (fork / join, so a class's tail
+// overlaps the others) or one after another on the batch stream, as the autotuner chose.
+static sr_status launch_classes(sr_batch* b) {
+    const int nk = (int)b->cls.size();
+    if (b->parallel && nk > 1) {
+        CK(cudaEventRecord(b->fork, b->stream));
+        for (int k = 1; k < nk; ++k) {
+            CK(cudaStreamWaitEvent(b->side[k - 1], b->fork, 0));
+            launch_class(b, k, b->side[k - 1]);
+            CK(cudaEventRecord(b->join[k - 1], b->side[k - 1]));
+        }
+        launch_class(b, 0, b->stream);
+        for (int k = 1; k < nk; ++k) CK(cudaStreamWaitEvent(b->stream, b->join[k - 1], 0));
+    } else {
+        for (int k = 0; k < nk; ++k) launch_class(b, k, b->stream);
+    }
+    return SR_OK;
+}
+
 static sr_status batch_launch_step(sr_batch* b) {
     const int ni = (int)b->inst.size();
     int maxN = 0;
@@ -2445,18 +2465,7 @@ static sr_status batch_launch_step(sr_batch* b) {
     for (const BInst& B : b->inst) { maxN = std::max(maxN, B.g.N); maxent = std::max(maxent, B.g.nentp); }
     k_sigma_b<<<dim3(maxN, ni), 64, 0, b->stream>>>(b->dinst.p, b->lams.p, b->step.p);
     k_nodes_b<<<dim3(3 * maxN, ni), 128, 0, b->stream>>>(b->dinst.p, b->lams.p, b->step.p);
-    // size classes as parallel branches (fork / join), so a class's tail overlaps the others
-    const int nk = (int)b->cls.size();
-    if (nk > 1) {
-        CK(cudaEventRecord(b->fork, b->stream));
-        for (int k = 1; k < nk; ++k) {
-            CK(cudaStreamWaitEvent(b->side[k - 1], b->fork, 0));
-            launch_class(b, k, b->side[k - 1]);
-            CK(cudaEventRecord(b->join[k - 1], b->side[k - 1]));
-        }
-    }
-    launch_class(b, 0, b->stream);
-    for (int k = 1; k < nk; ++k) CK(cudaStreamWaitEvent(b->stream, b->join[k - 1], 0));
+    if (sr_status s = launch_classes(b)) return s;
     const int ub = (int)std::min<long>((maxent + 255) / 256, 4 * b->nsm);
     k_update_b<<<dim3(ub, ni), 256, 0, b->stream>>>(b->dinst.p, b->lams.p, b->step.p, b->flag.p);
     k_shadow_b<<<dim3(ub, ni), 256, 0, b->stream>>>(b->dinst.p);
@@ -2522,7 +2531,37 @@ static sr_status batch_tune(sr_batch* b) {
     b->tune_ms = total;
     b->qc = b->cls.empty() ? kQF : b->cls[0].qc;
     b->ctas = b->cls.empty() ? 1 : b->cls[0].ctas;
-    return batch_upload(b);
+    if (sr_status s = batch_upload(b)) return s;
+    // then the classes together: parallel branches or one after another, whichever is faster
+    if (b->cls.size() > 1) {
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        double best[2] = {1e300, 1e300};
+        for (int rep = 0; rep < 2; ++rep)
+            for (int mode = 0; mode < 2; ++mode) {
+                b->parallel = mode == 1;
+                CK(cudaMemsetAsync(b->counter.p, 0, sizeof(unsigned long long) * b->cls.size(), b->stream));
+                CK(cudaEventRecord(e0, b->stream));
+                if (sr_status s = launch_classes(b)) return s;
+                CK(cudaEventRecord(e1, b->stream));
+                CK(cudaEventSynchronize(e1));
+                float t = 0.f;
+                CK(cudaEventElapsedTime(&t, e0, e1));
+                best[mode] = std::min(best[mode], (double)t);
+            }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        b->parallel = best[1] < best[0];
+        b->tune_ms = std::min(best[0], best[1]);
+    }
+    return SR_OK;
+}
+
+extern "C" sr_status sr_batch_parallel_classes(const sr_batch* b, int* parallel) {
+    if (!b || !parallel) return fail(SR_EINVAL, "null argument");
+    *parallel = b->parallel ? 1 : 0;
+    return SR_OK;
 }
 
 extern "C" sr_status sr_batch_create(int n, sr_flow* const* flows, sr_batch** out) {
