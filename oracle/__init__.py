@@ -3,4 +3,4 @@
 Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
 may import this package.  The product library never loads it.
 """
-from .oracle import OracleFlow, build, load, mesh_exponential, cutoff_exponential, spin_tables  # noqa: F401
+from .oracle import OracleFlow, OracleFlowTRI, tri_spin_tables, build, load, mesh_exponential, cutoff_exponential, spin_tables  # noqa: F401

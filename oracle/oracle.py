@@ -87,6 +87,24 @@ def load():
         lib.or_spin_tables.argtypes = [_dp, _dp, _dp, _dp, _dp]
         lib.or_num_threads.restype = C.c_int
         lib.or_set_num_threads.argtypes = [C.c_int]
+        lib.or_tri_spin_tables.argtypes = [_dp, _dp, _dp, _dp, _dp]
+        lib.or_tri_state_new.restype = vp
+        lib.or_tri_state_new.argtypes = [vp, C.c_int, _dp]
+        lib.or_tri_state_free.argtypes = [vp]
+        lib.or_tri_state_size.restype = C.c_size_t
+        lib.or_tri_state_size.argtypes = [vp]
+        lib.or_tri_state_offset.restype = C.c_size_t
+        lib.or_tri_state_offset.argtypes = [vp, C.c_int]
+        lib.or_tri_state_get.argtypes = [vp, _dp, _dp]
+        lib.or_tri_state_set.argtypes = [vp, _dp, _dp]
+        lib.or_tri_state_init.argtypes = [vp]
+        lib.or_tri_lookup.argtypes = [vp, C.c_int, _ip, C.c_int, C.c_double, C.c_double, C.c_double, _dp]
+        lib.or_tri_sigma_imag.restype = C.c_double
+        lib.or_tri_rhs.argtypes = [vp, C.c_double, _dp, _dp]
+        lib.or_tri_rhs_prepare.argtypes = [vp, C.c_double, _dp]
+        lib.or_tri_rhs_point.argtypes = [vp, C.c_int, _ip, C.c_int, C.c_double, C.c_double, C.c_double, _dp]
+        lib.or_tri_euler_step.argtypes = [vp, C.c_double, C.c_double]
+        lib.or_tri_chi.argtypes = [vp, C.c_double, _dp]
         _lib = lib
         return lib
 
@@ -115,6 +133,18 @@ def spin_tables():
     cx = np.zeros(16)
     closed = load().or_spin_tables(coef, h, f, cd, cx)
     return coef.reshape(5, 4, 4, 4), h, f, cd.reshape(4, 4), cx.reshape(4, 4), bool(closed)
+
+
+def tri_spin_tables():
+    """Complex coefficient tables of the TRI core from the oracle's literal Pauli contraction:
+    (coef[5,16,16,16], hartree[16], fock[16], chi_dir[16,16], chi_exc[16,16]); component
+    index mu * 4 + nu."""
+    coef = np.zeros(5 * 4096 * 2)
+    h, f = np.zeros(32), np.zeros(32)
+    cd, cx = np.zeros(512), np.zeros(512)
+    load().or_tri_spin_tables(coef, h, f, cd, cx)
+    z = lambda a: a[0::2] + 1j * a[1::2]  # noqa: E731
+    return (z(coef).reshape(5, 16, 16, 16), z(h), z(f), z(cd).reshape(16, 16), z(cx).reshape(16, 16))
 
 
 def dp54_tableau():
@@ -283,3 +313,128 @@ class OracleFlow:
     @staticmethod
     def threads() -> int:
         return load().or_num_threads()
+
+
+class OracleFlowTRI(OracleFlow):
+    """The oracle's general time-reversal-invariant core: all 16 basis functions
+    Gamma^{mu nu} (component mu * 4 + nu) stored as complex numbers, layout
+    [b][k][mu nu][pair(s,u)][t].  Accepts couplings with off-diagonal entries."""
+
+    def __init__(self, model, L: int, mesh: np.ndarray):
+        from workloads import flatten_model
+        lib = load()
+        self.lib = lib
+        prim, basis, bonds, frm, to, M = flatten_model(model)
+        self.nb = basis.shape[0]
+        self.la = lib.or_lattice_new(self.nb, np.ascontiguousarray(prim.reshape(-1)),
+                                     np.ascontiguousarray(basis.reshape(-1)), bonds.shape[0],
+                                     np.ascontiguousarray(bonds.reshape(-1)), frm.shape[0],
+                                     np.ascontiguousarray(frm.reshape(-1)), np.ascontiguousarray(to.reshape(-1)),
+                                     np.ascontiguousarray(M.reshape(-1)), L)
+        if not self.la:
+            raise ValueError("oracle lattice construction failed")
+        self.mesh = np.ascontiguousarray(mesh, dtype=np.float64)
+        self.N = len(self.mesh)
+        self.st = lib.or_tri_state_new(self.la, self.N, self.mesh)
+        if not self.st:
+            raise ValueError("oracle state construction failed")
+        self.size = int(lib.or_tri_state_size(self.st))
+        self.nsite = [lib.or_lattice_nsites(self.la, b) for b in range(self.nb)]
+        self.prim = prim
+        self.basis = basis
+        self.npair = self.N * (self.N + 1) // 2
+        lib.or_tri_state_init(self.st)
+
+    def __del__(self):
+        try:
+            self.lib.or_tri_state_free(self.st)
+            self.lib.or_lattice_free(self.la)
+        except Exception:
+            pass
+
+    def init(self):
+        self.lib.or_tri_state_init(self.st)
+
+    def get_state(self):
+        gam = np.zeros(self.N)
+        G = np.zeros(2 * self.size)
+        self.lib.or_tri_state_get(self.st, gam, G)
+        return gam, G[0::2] + 1j * G[1::2]
+
+    def set_state(self, gam, G):
+        G = np.asarray(G, dtype=np.complex128)
+        buf = np.empty(2 * self.size)
+        buf[0::2] = G.real
+        buf[1::2] = G.imag
+        self.lib.or_tri_state_set(self.st, np.ascontiguousarray(gam, dtype=np.float64), buf)
+
+    def block(self, G: np.ndarray, b: int) -> np.ndarray:
+        """View of basis b's block as [k][mu nu][pair][t]."""
+        off = int(self.lib.or_tri_state_offset(self.st, b))
+        n = self.nsite[b] * 16 * self.npair * self.N
+        return G[off:off + n].reshape(self.nsite[b], 16, self.npair, self.N)
+
+    def lookup(self, b1, d, b2, s, t, u) -> np.ndarray:
+        out = np.zeros(32)
+        self.lib.or_tri_lookup(self.st, b1, np.asarray(d, dtype=np.int32), b2, s, t, u, out)
+        return out[0::2] + 1j * out[1::2]
+
+    def rhs(self, lam: float):
+        dg = np.zeros(self.N)
+        dG = np.zeros(2 * self.size)
+        self.lib.or_tri_rhs(self.st, lam, dg, dG)
+        return dg, dG[0::2] + 1j * dG[1::2]
+
+    def rhs_entries(self, lam, ent):  # pragma: no cover - not provided by the TRI core
+        raise NotImplementedError
+
+    def prepare(self, lam: float) -> np.ndarray:
+        dg = np.zeros(self.N)
+        self.lib.or_tri_rhs_prepare(self.st, lam, dg)
+        return dg
+
+    def rhs_point(self, b1, d, b2, s, t, u) -> np.ndarray:
+        out = np.zeros(32)
+        self.lib.or_tri_rhs_point(self.st, b1, np.asarray(d, dtype=np.int32), b2, s, t, u, out)
+        return out[0::2] + 1j * out[1::2]
+
+    @staticmethod
+    def sigma_imag() -> float:
+        """Largest |Im H| of the self-energy flow seen so far (zero for states of the right
+        real / imaginary classes)."""
+        return load().or_tri_sigma_imag()
+
+    def sigma_rhs_point(self, w, lam, b=0):  # pragma: no cover - not provided by the TRI core
+        raise NotImplementedError
+
+    def euler(self, lam: float, lam_next: float):
+        self.lib.or_tri_euler_step(self.st, lam, lam_next)
+
+    def dp54(self, lam, lam_next, rtol, atol):  # pragma: no cover - not provided by the TRI core
+        raise NotImplementedError
+
+    def chi(self, lam: float):
+        """Per basis b: complex array (nsite_b, 16) of chi^{mu nu}_{b k}."""
+        tot = sum(self.nsite)
+        out = np.zeros(tot * 32)
+        self.lib.or_tri_chi(self.st, lam, out)
+        out = (out[0::2] + 1j * out[1::2]).reshape(tot, 16)
+        res, o = [], 0
+        for b in range(self.nb):
+            res.append(out[o:o + self.nsite[b]])
+            o += self.nsite[b]
+        return res
+
+    def chi_k(self, lam: float, kpts: np.ndarray, chi=None) -> np.ndarray:
+        """chi(k) with the spin-diagonal components xx, yy, zz (indices 5, 10, 15)."""
+        if chi is None:
+            chi = self.chi(lam)
+        kpts = np.asarray(kpts, dtype=np.float64).reshape(-1, 3)
+        acc = np.zeros(kpts.shape[0])
+        for b in range(self.nb):
+            sites = self.sites(b)
+            rb = self.basis[b]
+            for k, s in enumerate(sites):
+                dr = rb - self.position(s)
+                acc += np.cos(kpts @ dr) * chi[b][k, [5, 10, 15]].real.sum()
+        return acc / self.nb

@@ -912,3 +912,424 @@ void or_set_num_threads(int n) {
     (void)n;
 #endif
 }
+
+/* ========================================================================= */
+/* General time-reversal-invariant core: all 16 basis functions Gamma^{mu nu} */
+/* ========================================================================= */
+/*
+ * The TRI core of Sec. 3 keeps every basis function Gamma^{mu nu}, mu, nu = 0..3, of the
+ * parametrization Eq. (frg:parametrization), so that couplings with off-diagonal entries
+ * (Dzyaloshinskii-Moriya, symmetric off-diagonal exchange) can be represented.  Here the
+ * vertex is stored as complex numbers: the real / imaginary classes of Eq.
+ * (frg:parametrizationBasis2p) are then a property the flow has to preserve, not an
+ * assumption of the storage.  The spin sums alpha3, alpha4 are again done literally on
+ * Pauli matrices and projected back (generalising build_tables to unit basis functions
+ * Gamma^{kl} with k != l).  Same lattice (translation-only storage), meshes, propagators,
+ * node sets and readings C1-C9 as the spin-diagonal oracle above; additional reading:
+ *   C15 the self-energy flow takes the spin trace of Eq. (frg:flowexplicit:1particle)
+ *       (the average over alpha1): by time-reversal invariance Sigma is spin-diagonal and
+ *       alpha-independent, so the alpha1-odd part vanishes for a state of the right classes.
+ * Layout: [b][k][mu * 4 + nu][pair(s,u)][t], complex.
+ */
+
+static cx cscale(cx a, double s) { cx r = {a.re * s, a.im * s}; return r; }
+
+/* Spin tensor of a unit basis function Gamma^{kl} = 1: V^{a b; c d} = sigma^k_{a c} sigma^l_{b d}. */
+static cx unitV2(int k, int l, int a, int b, int c, int d) { return cmul(pauli(k, a, c), pauli(l, b, d)); }
+
+/* Non-zero projected coefficients of one term, out^{o} += coef A^{x} B^{y}. */
+typedef struct { int o, x, y; cx coef; } TriCoef;
+static TriCoef* g_tlist[5];
+static int g_tcount[5];
+static cx g_thart[16], g_tfock[16];              /* Sigma flow, averaged over alpha1 (C15) */
+static cx g_tchi_dir[16][16], g_tchi_exc[16][16]; /* chi^{mu nu} vertex term */
+static int g_ttables_ready = 0;
+
+static void build_tri_tables(void) {
+    if (g_ttables_ready) return;
+    for (int term = 0; term < 5; ++term) {
+        g_tlist[term] = (TriCoef*)malloc(sizeof(TriCoef) * 16 * 16 * 16);
+        g_tcount[term] = 0;
+        for (int x = 0; x < 16; ++x) for (int y = 0; y < 16; ++y) {
+            const int k1 = x / 4, k2 = x % 4, l1 = y / 4, l2 = y % 4;
+            cx T[2][2][2][2];
+            for (int a1p = 0; a1p < 2; ++a1p) for (int a2p = 0; a2p < 2; ++a2p)
+            for (int a1 = 0; a1 < 2; ++a1) for (int a2 = 0; a2 < 2; ++a2) {
+                cx acc = {0.0, 0.0};
+                for (int a3 = 0; a3 < 2; ++a3) for (int a4 = 0; a4 < 2; ++a4) {
+                    cx p;
+                    switch (term) {
+                    case 0: /* Gamma^{1'2';34} Gamma^{34;12} */
+                        p = cmul(unitV2(k1, k2, a1p, a2p, a3, a4), unitV2(l1, l2, a3, a4, a1, a2)); break;
+                    case 1: /* Gamma^{1'4;13}_{i1 j} Gamma^{32';42}_{j i2} */
+                        p = cmul(unitV2(k1, k2, a1p, a4, a1, a3), unitV2(l1, l2, a3, a2p, a4, a2)); break;
+                    case 2: /* Gamma^{1'4;13}_{i1 i2} Gamma^{2'3;42}_{i2 i2} */
+                        p = cmul(unitV2(k1, k2, a1p, a4, a1, a3), unitV2(l1, l2, a2p, a3, a4, a2)); break;
+                    case 3: /* Gamma^{41';13}_{i1 i1} Gamma^{32';42}_{i1 i2} */
+                        p = cmul(unitV2(k1, k2, a4, a1p, a1, a3), unitV2(l1, l2, a3, a2p, a4, a2)); break;
+                    default: /* Gamma^{42';13} Gamma^{1'3;42} */
+                        p = cmul(unitV2(k1, k2, a4, a2p, a1, a3), unitV2(l1, l2, a1p, a3, a4, a2)); break;
+                    }
+                    acc = cadd(acc, p);
+                }
+                T[a1p][a2p][a1][a2] = acc;
+            }
+            for (int o = 0; o < 16; ++o) {
+                cx pr = project(o / 4, o % 4, T);
+                if (fabs(pr.re) > 1e-12 || fabs(pr.im) > 1e-12) {
+                    TriCoef c = {o, x, y, pr};
+                    g_tlist[term][g_tcount[term]++] = c;
+                }
+            }
+        }
+    }
+    for (int x = 0; x < 16; ++x) {
+        const int k = x / 4, l = x % 4;
+        cx h = {0, 0}, f = {0, 0};
+        for (int a1 = 0; a1 < 2; ++a1) for (int a2 = 0; a2 < 2; ++a2) {
+            h = cadd(h, unitV2(k, l, a1, a2, a1, a2));
+            f = cadd(f, unitV2(k, l, a2, a1, a1, a2));
+        }
+        g_thart[x] = cscale(h, 0.5);
+        g_tfock[x] = cscale(f, 0.5);
+    }
+    for (int o = 0; o < 16; ++o) for (int x = 0; x < 16; ++x) {
+        const int mu = o / 4, nu = o % 4, k = x / 4, l = x % 4;
+        cx d = {0, 0}, e = {0, 0};
+        for (int a1p = 0; a1p < 2; ++a1p) for (int a2p = 0; a2p < 2; ++a2p)
+        for (int a1 = 0; a1 < 2; ++a1) for (int a2 = 0; a2 < 2; ++a2) {
+            cx pre = cmul(pauli(mu, a1, a1p), pauli(nu, a2, a2p));
+            d = cadd(d, cmul(pre, unitV2(k, l, a1p, a2p, a1, a2)));
+            e = cadd(e, cmul(pre, unitV2(k, l, a2p, a1p, a1, a2)));
+        }
+        g_tchi_dir[o][x] = d;
+        g_tchi_exc[o][x] = e;
+    }
+    g_ttables_ready = 1;
+}
+
+/* Export of the generated TRI tables (dense, complex as re/im pairs): coef[5][16][16][16][2],
+ * hartree[16][2], fock[16][2], chi_dir[16][16][2], chi_exc[16][16][2]. */
+void or_tri_spin_tables(double* coef, double* hartree, double* fock, double* chi_dir, double* chi_exc) {
+    build_tri_tables();
+    memset(coef, 0, sizeof(double) * 5 * 4096 * 2);
+    for (int term = 0; term < 5; ++term)
+        for (int i = 0; i < g_tcount[term]; ++i) {
+            const TriCoef* c = &g_tlist[term][i];
+            size_t at = (((size_t)term * 16 + c->o) * 16 + c->x) * 16 + c->y;
+            coef[2 * at] = c->coef.re; coef[2 * at + 1] = c->coef.im;
+        }
+    for (int x = 0; x < 16; ++x) {
+        hartree[2 * x] = g_thart[x].re; hartree[2 * x + 1] = g_thart[x].im;
+        fock[2 * x] = g_tfock[x].re; fock[2 * x + 1] = g_tfock[x].im;
+    }
+    for (int o = 0; o < 16; ++o) for (int x = 0; x < 16; ++x) {
+        chi_dir[2 * (o * 16 + x)] = g_tchi_dir[o][x].re; chi_dir[2 * (o * 16 + x) + 1] = g_tchi_dir[o][x].im;
+        chi_exc[2 * (o * 16 + x)] = g_tchi_exc[o][x].re; chi_exc[2 * (o * 16 + x) + 1] = g_tchi_exc[o][x].im;
+    }
+}
+
+typedef struct {
+    OrState f;     /* mesh, gamma, dgamma, cutoff of the self-energy flow (f.G unused) */
+    size_t* off;   /* per basis b: offset of its block */
+    size_t ntot;   /* complex entries */
+    cx* G;
+} OrStateT;
+
+static size_t gT_index(const OrStateT* st, int b, int k, int c, int si, int ti, int ui) {
+    return st->off[b] + ((((size_t)k * 16 + c) * st->f.npair + pair_index(si, ui)) * st->f.N + ti);
+}
+
+OrStateT* or_tri_state_new(const OrLattice* la, int N, const double* mesh) {
+    if (N < 2) return NULL;
+    build_tri_tables();
+    OrStateT* st = (OrStateT*)calloc(1, sizeof(OrStateT));
+    st->f.la = la; st->f.N = N;
+    st->f.w = (double*)malloc(sizeof(double) * N);
+    memcpy(st->f.w, mesh, sizeof(double) * N);
+    st->f.npair = N * (N + 1) / 2;
+    st->f.gam = (double*)calloc(N, sizeof(double));
+    st->f.dgam = (double*)calloc(N, sizeof(double));
+    st->off = (size_t*)malloc(sizeof(size_t) * la->nb);
+    size_t acc = 0;
+    for (int b = 0; b < la->nb; ++b) { st->off[b] = acc; acc += (size_t)la->nsite[b] * 16 * st->f.npair * N; }
+    st->ntot = acc;
+    st->G = (cx*)calloc(acc, sizeof(cx));
+    return st;
+}
+
+void or_tri_state_free(OrStateT* st) {
+    if (!st) return;
+    free(st->f.w); free(st->f.gam); free(st->f.dgam); free(st->off); free(st->G); free(st);
+}
+
+size_t or_tri_state_size(const OrStateT* st) { return st->ntot; }
+size_t or_tri_state_offset(const OrStateT* st, int b) { return st->off[b]; }
+/* G as interleaved (re, im) pairs. */
+void or_tri_state_get(const OrStateT* st, double* gam, double* G) {
+    if (gam) memcpy(gam, st->f.gam, sizeof(double) * st->f.N);
+    if (G) memcpy(G, st->G, sizeof(cx) * st->ntot);
+}
+void or_tri_state_set(OrStateT* st, const double* gam, const double* G) {
+    if (gam) memcpy(st->f.gam, gam, sizeof(double) * st->f.N);
+    if (G) memcpy(st->G, G, sizeof(cx) * st->ntot);
+}
+
+/* Eq. (frg:parametrizationInitial): gamma = 0, Gamma^{mu nu} = J^{mu nu}/4 for mu, nu = x, y, z,
+ * every basis function with mu = 0 or nu = 0 zero.  Frequency independent, real. */
+void or_tri_state_init(OrStateT* st) {
+    const OrLattice* la = st->f.la;
+    memset(st->f.gam, 0, sizeof(double) * st->f.N);
+    for (int b = 0; b < la->nb; ++b)
+    for (int k = 0; k < la->nsite[b]; ++k)
+    for (int c = 0; c < 16; ++c) {
+        const int mu = c / 4, nu = c % 4;
+        cx v = {0.0, 0.0};
+        if (mu > 0 && nu > 0) v.re = la->J[b][9 * k + 3 * (mu - 1) + (nu - 1)] / 4.0;
+        for (int p = 0; p < st->f.npair; ++p) for (int t = 0; t < st->f.N; ++t)
+            st->G[st->off[b] + (((size_t)k * 16 + c) * st->f.npair + p) * st->f.N + t] = v;
+    }
+}
+
+/* Stored value of component (mu, nu) with the s <-> u exchange for corners below the
+ * diagonal (C5): factor -xi(nu). */
+static cx storedT(const OrStateT* st, int b, int k, int mu, int nu, int si, int ti, int ui) {
+    if (si >= ui) return st->G[gT_index(st, b, k, 4 * mu + nu, si, ti, ui)];
+    return cscale(st->G[gT_index(st, b, k, 4 * mu + nu, ui, ti, si)], -xi(nu));
+}
+
+/* Gamma^{mu nu}_{i1 i2}(s, t, u), all 16 components, for i1 = (0, b1), i2 = (d, b2): the
+ * relations of Eq. (frg:parametrizationBasis2p) applied in the paper's order --
+ *   t -> -t: factor xi(mu) xi(nu);
+ *   s -> -s: exchange the sites and mu <-> nu;
+ *   u -> -u: factor xi(mu) xi(nu), exchange the sites and mu <-> nu;
+ *   s < u:   factor -xi(nu) with (s, u) exchanged --
+ * then trilinear interpolation (Sec. 4.2).  Zero beyond the truncation range. */
+static void lookupT(const OrStateT* st, int b1, const int d[3], int b2, double s, double t, double u, cx out[16]) {
+    const double s0 = s, t0 = t, u0 = u;
+    for (int c = 0; c < 16; ++c) {
+        int m = c / 4, n = c % 4, swap = 0, tmp;
+        double fac = 1.0;
+        s = s0; t = t0; u = u0;
+        if (t < 0) { t = -t; fac *= xi(m) * xi(n); }
+        if (s < 0) { s = -s; swap ^= 1; tmp = m; m = n; n = tmp; }
+        if (u < 0) { u = -u; fac *= xi(m) * xi(n); swap ^= 1; tmp = m; m = n; n = tmp; }
+        int ib = b1, jb = b2, dd[3] = {d[0], d[1], d[2]};
+        if (swap) { ib = b2; jb = b1; dd[0] = -d[0]; dd[1] = -d[1]; dd[2] = -d[2]; }
+        int k = site_of(st->f.la, ib, dd, jb);
+        if (k < 0) { out[c].re = out[c].im = 0.0; continue; }
+        if (s < u) { double q = s; s = u; u = q; fac *= -xi(n); }
+        int sl, tl, ul; double sw0, sw1, tw0, tw1, uw0, uw1;
+        bracket(st->f.w, st->f.N, s, &sl, &sw0, &sw1);
+        bracket(st->f.w, st->f.N, t, &tl, &tw0, &tw1);
+        bracket(st->f.w, st->f.N, u, &ul, &uw0, &uw1);
+        cx v = {0.0, 0.0};
+        const double ws[2] = {sw0, sw1}, wt[2] = {tw0, tw1}, wu[2] = {uw0, uw1};
+        for (int a = 0; a < 2; ++a) for (int bb = 0; bb < 2; ++bb) for (int e = 0; e < 2; ++e) {
+            double wgt = ws[a] * wt[bb] * wu[e];
+            if (wgt == 0.0) continue;
+            v = cadd(v, cscale(storedT(st, ib, k, m, n, sl + a, tl + bb, ul + e), wgt));
+        }
+        out[c] = cscale(v, fac);
+    }
+}
+
+void or_tri_lookup(const OrStateT* st, int b1, const int* d, int b2, double s, double t, double u, double* out32) {
+    lookupT(st, b1, d, b2, s, t, u, (cx*)out32);
+}
+
+/* Self-energy flow with the spin trace (C15):
+ * dgamma(w1) = -(1/2pi) sum_{w2 = +-Lambda} Re H(w1, w2) / (w2 + gamma(w2)),
+ * H = sum_j h_x Gamma^x_{i1 j}(w1+w2, 0, w1-w2) - f_x Gamma^x_{i1 i1}(w1+w2, w2-w1, 0). */
+static double g_tri_sigma_imag = 0.0;   /* largest |Im H| seen (zero for a state of the right classes) */
+static double sigma_rhs_atT(const OrStateT* st, int b, double w1, double lam) {
+    const OrLattice* la = st->f.la;
+    double acc = 0.0;
+    cx v[16];
+    for (int sg = 0; sg < 2; ++sg) {
+        double w2 = sg == 0 ? lam : -lam;
+        cx H = {0.0, 0.0};
+        for (int k = 0; k < la->nsite[b]; ++k) {
+            Site j = la->sites[b][k];
+            lookupT(st, b, j.n, j.b, w1 + w2, 0.0, w1 - w2, v);
+            for (int x = 0; x < 16; ++x) H = cadd(H, cmul(g_thart[x], v[x]));
+        }
+        int z[3] = {0, 0, 0};
+        lookupT(st, b, z, b, w1 + w2, w2 - w1, 0.0, v);
+        for (int x = 0; x < 16; ++x) H = cadd(H, cscale(cmul(g_tfock[x], v[x]), -1.0));
+        if (fabs(H.im) > g_tri_sigma_imag) g_tri_sigma_imag = fabs(H.im);
+        acc += H.re / (w2 + interp_odd(st->f.w, st->f.N, st->f.gam, w2));
+    }
+    return -acc / (2.0 * OR_PI);
+}
+
+double or_tri_sigma_imag(void) { return g_tri_sigma_imag; }
+
+static void accumT(cx out[16], double W, int term, const cx A[16], const cx B[16], double sign) {
+    for (int i = 0; i < g_tcount[term]; ++i) {
+        const TriCoef* c = &g_tlist[term][i];
+        out[c->o] = cadd(out[c->o], cscale(cmul(c->coef, cmul(A[c->x], B[c->y])), sign * W));
+    }
+}
+
+/* dGamma^{mu nu}_{i1 i2}(s, t, u)/dLambda, Eq. (frg:flowexplicit:2particle), as gamma_rhs_at
+ * with all 16 components. */
+static void gamma_rhs_atT(const OrStateT* st, int b1, const int d2[3], int b2, double s, double t, double u,
+                          double* xs, double* Ws, cx out[16]) {
+    const OrLattice* la = st->f.la;
+    double w1p = (s + t + u) / 2, w2p = (s - t - u) / 2, w1 = (s - t + u) / 2, w2 = (s + t - u) / 2;
+    cx A[16], B[16], C[16];
+    int z[3] = {0, 0, 0};
+    for (int c = 0; c < 16; ++c) out[c].re = out[c].im = 0.0;
+    int n = channel_nodes(&st->f, CH_S, s, xs, Ws);
+    for (int q = 0; q < n; ++q) {
+        double x = xs[q];
+        lookupT(st, b1, d2, b2, s, w1p - x, x - w2p, A);
+        lookupT(st, b1, d2, b2, s, x - w1, x - w2, B);
+        accumT(out, Ws[q], 0, A, B, 1.0);
+    }
+    n = channel_nodes(&st->f, CH_T, t, xs, Ws);
+    for (int q = 0; q < n; ++q) {
+        double x = xs[q];
+        for (int k = 0; k < la->nsite[b1]; ++k) {
+            Site j = la->sites[b1][k];
+            int dj2[3] = {d2[0] - j.n[0], d2[1] - j.n[1], d2[2] - j.n[2]};
+            if (site_of(la, j.b, dj2, b2) < 0) continue;
+            lookupT(st, b1, j.n, j.b, w1 + x, t, w1p - x, A);
+            lookupT(st, j.b, dj2, b2, x + w2p, t, x - w2, B);
+            accumT(out, Ws[q], 1, A, B, -1.0);
+        }
+        lookupT(st, b1, d2, b2, w1 + x, t, w1p - x, A);
+        lookupT(st, b2, z, b2, w2p + x, w2 - x, -t, C);
+        accumT(out, Ws[q], 2, A, C, 1.0);
+        lookupT(st, b1, z, b1, w1 + x, x - w1p, -t, C);
+        lookupT(st, b1, d2, b2, x + w2p, t, x - w2, B);
+        accumT(out, Ws[q], 3, C, B, 1.0);
+    }
+    n = channel_nodes(&st->f, CH_U, u, xs, Ws);
+    for (int q = 0; q < n; ++q) {
+        double x = xs[q];
+        lookupT(st, b1, d2, b2, w1 + x, x - w2p, u, A);
+        lookupT(st, b1, d2, b2, w1p + x, w2 - x, u, B);
+        accumT(out, Ws[q], 4, A, B, 1.0);
+    }
+}
+
+static void compute_dgamT(OrStateT* st, double lam) {
+    st->f.lam = lam;
+    for (int i = 0; i < st->f.N; ++i) st->f.dgam[i] = sigma_rhs_atT(st, 0, st->f.w[i], lam);
+}
+
+/* Full right-hand side: dgamma (N) and dGamma (state layout, interleaved re / im). */
+void or_tri_rhs(OrStateT* st, double lam, double* dgam, double* dG) {
+    compute_dgamT(st, lam);
+    if (dgam) memcpy(dgam, st->f.dgam, sizeof(double) * st->f.N);
+    const OrLattice* la = st->f.la;
+    const int N = st->f.N, npair = st->f.npair;
+    cx* out = (cx*)dG;
+    for (int b = 0; b < la->nb; ++b) {
+        long total = (long)la->nsite[b] * npair * N;
+        #pragma omp parallel
+        {
+            double* xs = (double*)malloc(sizeof(double) * (2 * N + 16));
+            double* Ws = (double*)malloc(sizeof(double) * (2 * N + 16));
+            #pragma omp for schedule(dynamic, 4)
+            for (long e = 0; e < total; ++e) {
+                int k = (int)(e / ((long)npair * N));
+                long rem = e % ((long)npair * N);
+                int p = (int)(rem / N), ti = (int)(rem % N);
+                int si = 0; while ((si + 1) * (si + 2) / 2 <= p) ++si;
+                int ui = p - si * (si + 1) / 2;
+                Site j = la->sites[b][k];
+                cx o[16];
+                gamma_rhs_atT(st, b, j.n, j.b, st->f.w[si], st->f.w[ti], st->f.w[ui], xs, Ws, o);
+                for (int c = 0; c < 16; ++c) out[gT_index(st, b, k, c, si, ti, ui)] = o[c];
+            }
+            free(xs); free(Ws);
+        }
+    }
+}
+
+void or_tri_rhs_prepare(OrStateT* st, double lam, double* dgam) {
+    compute_dgamT(st, lam);
+    if (dgam) memcpy(dgam, st->f.dgam, sizeof(double) * st->f.N);
+}
+/* Right-hand side at an arbitrary (s, t, u) and site pair after or_tri_rhs_prepare:
+ * out32 = 16 complex values. */
+void or_tri_rhs_point(const OrStateT* st, int b1, const int* d, int b2, double s, double t, double u, double* out32) {
+    double xs[512], Ws[512];
+    if (2 * st->f.N + 16 > 512) { for (int i = 0; i < 32; ++i) out32[i] = NAN; return; }
+    gamma_rhs_atT(st, b1, d, b2, s, t, u, xs, Ws, (cx*)out32);
+}
+
+/* Euler step (Sec. 4.3). */
+void or_tri_euler_step(OrStateT* st, double lam, double lam_next) {
+    double dl = lam - lam_next;
+    double* dg = (double*)malloc(sizeof(double) * st->f.N);
+    double* dG = (double*)malloc(sizeof(cx) * st->ntot);
+    or_tri_rhs(st, lam, dg, dG);
+    for (int i = 0; i < st->f.N; ++i) st->f.gam[i] -= dl * dg[i];
+    double* G = (double*)st->G;
+    for (size_t i = 0; i < 2 * st->ntot; ++i) G[i] -= dl * dG[i];
+    free(dg); free(dG);
+}
+
+/* chi^{mu nu}_{b k}, all 16 components (complex, interleaved): out[((off_b + k) * 16 + o) * 2].
+ * Same quadrature as or_chi (C9); the bubble term carries tr(sigma^mu sigma^nu) / 2 =
+ * delta_{mu nu} and is local (C8). */
+void or_tri_chi(const OrStateT* st, double lam, double* outd) {
+    const OrLattice* la = st->f.la;
+    const int N = st->f.N;
+    cx* out = (cx*)outd;
+    double* y = (double*)malloc(sizeof(double) * (N + 1));
+    double* Wn = (double*)calloc(N + 1, sizeof(double));
+    int K = 0;
+    y[K++] = lam;
+    for (int i = 0; i < N; ++i) if (st->f.w[i] > lam) y[K++] = st->f.w[i];
+    for (int k = 0; k + 1 < K; ++k) {
+        double ya = y[k] + interp_odd(st->f.w, N, st->f.gam, y[k]);
+        double yb = y[k + 1] + interp_odd(st->f.w, N, st->f.gam, y[k + 1]);
+        double seg = (y[k + 1] - y[k]) / (ya * yb);
+        Wn[k] += 0.5 * seg; Wn[k + 1] += 0.5 * seg;
+    }
+    Wn[K - 1] += 1.0 / (y[K - 1] + interp_odd(st->f.w, N, st->f.gam, y[K - 1]));
+    double bubble = 0.0;
+    for (int k = 0; k < K; ++k) bubble += Wn[k];
+    bubble /= (2.0 * OR_PI);
+    int M = 2 * K;
+    double* xs = (double*)malloc(sizeof(double) * M);
+    double* ws = (double*)malloc(sizeof(double) * M);
+    for (int k = 0; k < K; ++k) { xs[k] = y[k]; ws[k] = Wn[k]; xs[K + k] = -y[k]; ws[K + k] = Wn[k]; }
+    size_t base = 0;
+    for (int b = 0; b < la->nb; ++b) {
+        int ns = la->nsite[b];
+        #pragma omp parallel for schedule(dynamic, 1)
+        for (int k = 0; k < ns; ++k) {
+            Site j = la->sites[b][k];
+            int onsite = (j.b == b && j.n[0] == 0 && j.n[1] == 0 && j.n[2] == 0);
+            int z[3] = {0, 0, 0};
+            cx acc[16];
+            for (int o = 0; o < 16; ++o) acc[o].re = acc[o].im = 0.0;
+            for (int p = 0; p < M; ++p) for (int q = 0; q < M; ++q) {
+                cx v[16], e[16];
+                lookupT(st, b, j.n, j.b, xs[p] + xs[q], 0.0, xs[p] - xs[q], v);
+                if (onsite) lookupT(st, b, z, b, xs[p] + xs[q], xs[q] - xs[p], 0.0, e);
+                for (int o = 0; o < 16; ++o) {
+                    cx F = {0.0, 0.0};
+                    for (int x = 0; x < 16; ++x) {
+                        F = cadd(F, cmul(g_tchi_dir[o][x], v[x]));
+                        if (onsite) F = cadd(F, cscale(cmul(g_tchi_exc[o][x], e[x]), -1.0));
+                    }
+                    acc[o] = cadd(acc[o], cscale(F, ws[p] * ws[q]));
+                }
+            }
+            for (int o = 0; o < 16; ++o) {
+                cx r = cscale(acc[o], -1.0 / (16.0 * OR_PI * OR_PI));
+                if (onsite && o / 4 == o % 4) r.re += bubble;
+                out[(base + k) * 16 + o] = r;
+            }
+        }
+        base += ns;
+    }
+    free(y); free(Wn); free(xs); free(ws);
+}

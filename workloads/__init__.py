@@ -45,7 +45,7 @@ class Coupling:
 class Model:
     cell: UnitCell
     couplings: List[Coupling]
-    backend: str = "SU2"             # "SU2" or "XYZ"
+    backend: str = "SU2"             # "SU2", "XYZ" or "TRI"
 
 
 def _cell(name, prim, basis, bonds) -> UnitCell:
@@ -137,6 +137,31 @@ def honeycomb_kitaev(J: float = 0.2, K: float = -1.0) -> Model:
     to = [(0, 0, 0, 1), (0, -1, 0, 1), (-1, 0, 0, 1)]
     cps = [Coupling((0, 0, 0, 0), t, J * I3 + K * _diag(i)) for i, t in enumerate(to)]
     return Model(c, cps, "XYZ")
+
+
+def dm_matrix(D) -> np.ndarray:
+    """Coupling matrix of D . (S_from x S_to): M[a][b] = sum_c eps_{c a b} D_c."""
+    D = np.asarray(D, dtype=np.float64)
+    return np.array([[0.0, D[2], -D[1]], [-D[2], 0.0, D[0]], [D[1], -D[0], 0.0]])
+
+
+def kagome_dm(J: float = 1.0, D: float = 0.5) -> Model:
+    """Kagome Heisenberg antiferromagnet with out-of-plane Dzyaloshinskii-Moriya vectors of the
+    paper's second worked example (Sec. 6.2 model listing): on each of the six directed
+    nearest-neighbour bonds per cell, J S_from . S_to + D (S_from x S_to)_z, i.e. the terms xy
+    and -yx with weight D.  Needs the TRI core."""
+    c = kagome()
+    directed = [((0, 0, 0, 1), (0, 0, 0, 0)), ((0, 0, 0, 0), (0, 0, 0, 2)),
+                ((-1, 0, 0, 1), (0, 0, 0, 0)), ((0, 0, 0, 0), (0, -1, 0, 2)),
+                ((0, 0, 0, 2), (0, 0, 0, 1)), ((0, -1, 0, 2), (-1, 0, 0, 1))]
+    M = J * I3 + dm_matrix((0.0, 0.0, D))
+    return Model(c, [Coupling(f, t, M.copy()) for f, t in directed], "TRI")
+
+
+def rotated(model: Model, R: np.ndarray, backend: str = "TRI") -> Model:
+    """The same model with every coupling matrix rotated in spin space, M -> R M R^T."""
+    R = np.asarray(R, dtype=np.float64)
+    return Model(model.cell, [Coupling(c.frm, c.to, R @ c.M @ R.T) for c in model.couplings], backend)
 
 
 def honeycomb_kitaev_linear():
