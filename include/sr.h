@@ -30,7 +30,11 @@
  *   gamma: index ((pair(s_i, u_i) * N + t_i) * n_c + c) * N_s + r
  *          with pair(s, u) = s (s + 1) / 2 + u for s >= u (the stored octant),
  *          c = spin component (SU2: 0 = density Gamma^00, 1 = spin Gamma^zz;
- *          XYZ: 0 = Gamma^00, 1..3 = Gamma^xx, Gamma^yy, Gamma^zz),
+ *          XYZ: 0 = Gamma^00, 1..3 = Gamma^xx, Gamma^yy, Gamma^zz;
+ *          TRI: c = mu * 4 + nu for all 16 basis functions, stored as real g^{mu nu} with
+ *          Gamma^{mu nu} = i g^{mu nu} for the six functions with exactly one of mu, nu = 0
+ *          (the imaginary class of Eq. frg:parametrizationBasis2p), Gamma^{mu nu} = g^{mu nu}
+ *          otherwise),
  *          r = symmetry-irreducible site (r = 0 is the reference site itself).
  *   N_entries = N (N + 1) / 2 * N * n_c * N_s.
  */
@@ -51,7 +55,7 @@ typedef enum {
     SR_ESYMMETRY = 4,     /* not all lattice sites are equivalent under the model's symmetries */
     SR_ENONFINITE = 5,    /* the flow produced NaN / Inf */
     SR_ETIMEOUT = 6,      /* a bounded device-side wait gave up */
-    SR_EUNSUPPORTED = 7   /* valid request that this build does not implement (e.g. TRI core) */
+    SR_EUNSUPPORTED = 7   /* valid request that this build does not implement (e.g. a TRI flow in FP32) */
 } sr_status;
 
 typedef enum { SR_SU2 = 0, SR_XYZ = 1, SR_TRI = 2 } sr_backend;
@@ -79,7 +83,7 @@ typedef struct {
     int n_couplings;
     const sr_coupling* couplings;  /* host */
     int range_L;                   /* truncation range in bonds (Sec. 4.1) */
-    sr_backend backend;            /* SR_SU2 or SR_XYZ (SR_TRI -> SR_EUNSUPPORTED) */
+    sr_backend backend;            /* SR_SU2 (Heisenberg), SR_XYZ (diagonal J) or SR_TRI (any J) */
     double eps;                    /* real-space precision of the symmetry search; <= 0 means 1e-5 */
 } sr_lattice_desc;
 
@@ -89,9 +93,12 @@ typedef struct sr_flow sr_flow;
 /* Build the truncated lattice and its symmetry tables on the host (Sec. 4.1): the sites
  * within bond distance L of the reference site (basis site 0 of cell 0), the lattice and
  * spin-permutation symmetries of the model, the irreducible site set, the site-exchange
- * map, and the lattice-sum table of sum_j Gamma_{i1 j} Gamma_{j i2}.  No GPU is touched.
+ * map, and the lattice-sum table of sum_j Gamma_{i1 j} Gamma_{j i2}.  The TRI core (Sec. 3,
+ * the general time-reversal-invariant case) combines lattice symmetries with the 24 proper
+ * rotations among the signed permutations of x, y, z.  No GPU is touched.
  * Errors: SR_EINVAL (bad desc), SR_ESYMMETRY (sites not all equivalent),
- * SR_EUNSUPPORTED (SR_TRI, or a coupling the chosen core cannot represent). */
+ * SR_EUNSUPPORTED (a coupling the chosen core cannot represent: off-diagonal J outside
+ * TRI, anisotropic J in SU2). */
 sr_status sr_lattice_create(const sr_lattice_desc* desc, sr_lattice** out);
 
 /* N_s irreducible sites, N_tot sites within range, basis size, P lattice-sum table length. */
@@ -104,6 +111,13 @@ sr_status sr_lattice_representatives(const sr_lattice* lat, int* rep);
  * *r = irreducible site or -1 if beyond range, perm[c] = stored component holding
  * component c of the pair (perm has 4 entries; for SU2 only c = 0, 1 are meaningful). */
 sr_status sr_lattice_map_pair(const sr_lattice* lat, const int* i1, const int* i2, int* r, int* perm);
+
+/* As sr_lattice_map_pair for every core, with signs: component c (c < n_c) of the pair
+ * (i1, i2) equals sign[c] * stored component comp[c] of irreducible site *r (comp, sign:
+ * host out, n_c entries each; n_c = 2, 4 or 16).  For SU2 / XYZ the signs are +1; for TRI
+ * the map is a signed permutation of the 16 basis functions (Sec. 4.1 symmetries with a
+ * spin rotation).  *r = -1 beyond range.  Errors: SR_EINVAL. */
+sr_status sr_lattice_map_pair_components(const sr_lattice* lat, const int* i1, const int* i2, int* r, int* comp, int* sign);
 
 sr_status sr_lattice_destroy(sr_lattice* lat);
 

@@ -70,6 +70,7 @@ def load_library():
             "sr_lattice_info": [vp, ip, ip, ip, lp],
             "sr_lattice_representatives": [vp, ip],
             "sr_lattice_map_pair": [vp, ip, ip, ip, ip],
+            "sr_lattice_map_pair_components": [vp, ip, ip, ip, ip, ip],
             "sr_lattice_destroy": [vp],
             "sr_frequency_mesh_exponential": [i, d, d, dp],
             "sr_flow_init": [vp, i, dp, d, i, vp, C.POINTER(vp)],
@@ -185,7 +186,7 @@ class Lattice:
     def from_model(cls, model, L: int, backend=None, eps: float = 1e-5) -> "Lattice":
         cell = model.cell
         coups = [(c.frm, c.to, c.M) for c in model.couplings]
-        be = backend if backend is not None else (SR_XYZ if getattr(model, "backend", "SU2") == "XYZ" else SR_SU2)
+        be = backend if backend is not None else {"XYZ": SR_XYZ, "TRI": SR_TRI}.get(getattr(model, "backend", "SU2"), SR_SU2)
         return cls(cell.prim, cell.basis, cell.bonds, coups, L, be, eps)
 
     def representatives(self) -> np.ndarray:
@@ -200,6 +201,21 @@ class Lattice:
         perm = np.zeros(4, dtype=np.int32)
         _check(self._lib.sr_lattice_map_pair(self.h, _iptr(a), _iptr(b), C.byref(r), _iptr(perm)))
         return r.value, perm
+
+    @property
+    def n_comp(self) -> int:
+        return {SR_SU2: 2, SR_XYZ: 4, SR_TRI: 16}[int(self.backend)]
+
+    def map_pair_components(self, i1, i2):
+        """(r, comp, sign): component c of the pair (i1, i2) is sign[c] * stored component
+        comp[c] of irreducible site r (r = -1 beyond range)."""
+        a = np.ascontiguousarray(i1, dtype=np.int32)
+        b = np.ascontiguousarray(i2, dtype=np.int32)
+        r = C.c_int()
+        comp = np.zeros(self.n_comp, dtype=np.int32)
+        sign = np.zeros(self.n_comp, dtype=np.int32)
+        _check(self._lib.sr_lattice_map_pair_components(self.h, _iptr(a), _iptr(b), C.byref(r), _iptr(comp), _iptr(sign)))
+        return r.value, comp, sign
 
     def __del__(self):
         try:

@@ -1360,6 +1360,7 @@ __global__ void k_chi_k(int nk, const double* __restrict__ kp, const T* __restri
 }  // namespace
 
 #include "adjoint.cuh"
+#include "tri.cuh"
 
 // ----------------------------------------------------------------------------- objects
 
@@ -1435,12 +1436,20 @@ struct sr_flow {
     size_t smem_adj = 0;
     DevBuf<int> pinv_off, pinv_out, ainv_off, ainv_idx, binv_off, binv_idx;
     DevBuf<double> ntw, Wbar, dgbar, tg, tG, chibar, kbar;
+    // TRI core tables (nc = 16)
+    DevBuf<int> swap_map16, onsite_map16, tlat_off, chi_r16, chi_m16;
+    DevBuf<int2> tlat_ent;
 
     Tabs tabs() const {
         Tabs t;
         t.swap_r = swap_r.p; t.swap_perm = swap_perm.p; t.onsite_perm = onsite_perm.p; t.mult = mult.p;
         t.prod = prod.p; t.gath_off = gath_off.p; t.gath_idx = gath_idx.p; t.nprod = nprod; t.invh = invh.p;
         t.w = w.p; t.wf = wf.p; t.invhf = invhf.p; t.prodp = prodp.p; t.dgath_idx = dgath_idx.p;
+        return t;
+    }
+    TabsT tabs_tri() const {
+        TabsT t;
+        t.swap_map = swap_map16.p; t.onsite_map = onsite_map16.p; t.lat_off = tlat_off.p; t.lat_ent = tlat_ent.p;
         return t;
     }
 };
@@ -1518,6 +1527,23 @@ static sr_status run_rhs(sr_flow* f, double lam, const double* gam_s, const doub
         f->n_rhs++;
         return SR_OK;
     }
+    if (g.nc == 16) {
+        // TRI core (FP64)
+        const TabsT tt = f->tabs_tri();
+        if (sr_status s = prof_begin(f, 0, &e0)) return s;
+        k_sigma_rhs_tri<<<g.N, 64, 0, f->stream>>>(g, tb, tt, f->w.p, gam_s, G_s, lam, dgam_o);
+        if (sr_status s = prof_end(f, 0, e0)) return s;
+        if (sr_status s = prof_begin(f, 1, &e0)) return s;
+        k_channel_nodes<double><<<3 * g.N, 128, 0, f->stream>>>(g, f->w.p, f->invh.p, gam_s, dgam_o, lam, f->nx.p, f->nW.p, f->nWf.p,
+                                                               f->ncount.p, nullptr);
+        if (sr_status s = prof_end(f, 1, e0)) return s;
+        if (sr_status s = prof_begin(f, 2, &e0)) return s;
+        k_gamma_rhs_tri<<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, tt, f->w.p, G_s, f->nx.p, f->nW.p, f->ncount.p, dG_o);
+        if (sr_status s = prof_end(f, 2, e0)) return s;
+        CK(cudaGetLastError());
+        f->n_rhs++;
+        return SR_OK;
+    }
     if (sr_status s = prof_begin(f, 0, &e0)) return s;
     k_sigma_rhs<double><<<g.N, 64, 0, f->stream>>>(g, tb, f->w.p, gam_s, G_s, lam, dgam_o);
     if (sr_status s = prof_end(f, 0, e0)) return s;
@@ -1566,8 +1592,7 @@ extern "C" sr_status sr_lattice_create(const sr_lattice_desc* desc, sr_lattice**
     if (desc->n_bonds <= 0 || !desc->bonds) return fail(SR_EINVAL, "at least one bond is required");
     if (desc->n_couplings < 0 || (desc->n_couplings > 0 && !desc->couplings)) return fail(SR_EINVAL, "bad couplings");
     if (desc->range_L < 0 || desc->range_L > 64) return fail(SR_EINVAL, "range_L must be in [0, 64]");
-    if (desc->backend == SR_TRI) return fail(SR_EUNSUPPORTED, "the TRI core is not provided by this build");
-    if (desc->backend != SR_SU2 && desc->backend != SR_XYZ) return fail(SR_EINVAL, "unknown backend");
+    if (desc->backend != SR_SU2 && desc->backend != SR_XYZ && desc->backend != SR_TRI) return fail(SR_EINVAL, "unknown backend");
     std::unique_ptr<sr_lattice> lat(new (std::nothrow) sr_lattice());
     if (!lat) return fail(SR_ENOMEM, "out of host memory");
     std::string msg;
@@ -1612,6 +1637,23 @@ extern "C" sr_status sr_lattice_map_pair(const sr_lattice* lat, const int* i1, c
     return SR_OK;
 }
 
+extern "C" sr_status sr_lattice_map_pair_components(const sr_lattice* lat, const int* i1, const int* i2, int* r, int* comp,
+                                                    int* sign) {
+    if (!lat || !i1 || !i2 || !r || !comp || !sign) return fail(SR_EINVAL, "null argument");
+    if (i1[3] < 0 || i1[3] >= lat->nb || i2[3] < 0 || i2[3] >= lat->nb) return fail(SR_EINVAL, "basis index out of range");
+    sr::SiteKey a{{i1[0], i1[1], i1[2]}, i1[3]}, b{{i2[0], i2[1], i2[2]}, i2[3]};
+    if (lat->nc == 16) {
+        const sr::PairMap16 pm = lat->map_pair16(a, b);
+        *r = pm.r;
+        for (int c = 0; c < 16; ++c) { comp[c] = pm.m[c] & 15; sign[c] = (pm.m[c] & 16) ? -1 : 1; }
+        return SR_OK;
+    }
+    const sr::PairMap pm = lat->map_pair(a, b);
+    *r = pm.r;
+    for (int c = 0; c < lat->nc; ++c) { comp[c] = lat->backend == SR_SU2 ? c : pm.perm[c]; sign[c] = 1; }
+    return SR_OK;
+}
+
 extern "C" sr_status sr_lattice_destroy(sr_lattice* lat) {
     delete lat;
     return SR_OK;
@@ -1636,6 +1678,7 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
     }
     if (!(lambda_init > 0.0) || !std::isfinite(lambda_init)) return fail(SR_EINVAL, "lambda_init must be positive");
     if (precision != SR_FP64 && precision != SR_FP32_MIXED) return fail(SR_EINVAL, "unknown precision");
+    if (lat->nc == 16 && precision != SR_FP64) return fail(SR_EUNSUPPORTED, "the TRI core runs in FP64");
     std::unique_ptr<sr_flow> f(new (std::nothrow) sr_flow());
     if (!f) return fail(SR_ENOMEM, "out of host memory");
     f->lat = lat;
@@ -1679,7 +1722,7 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
     // components, and for every output (site, component) the list of its products
     std::vector<int2> prods;
     std::vector<int> goff(lat->Ns * lat->nc + 1, 0), gidx;
-    {
+    if (lat->nc != 16) {
         std::map<std::pair<int, int>, int> pid;
         for (int r = 0; r < lat->Ns; ++r)
             for (int c = 0; c < lat->nc; ++c) {
@@ -1702,7 +1745,7 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
     f->h_goff = goff;
     f->h_gidx = gidx;
     // padded-layout products, site-exchange map, dense (SU2) gather indices
-    {
+    if (lat->nc != 16) {
         const int nsp = g.nsp;
         std::vector<int2> pp(prods.size());
         for (size_t k = 0; k < prods.size(); ++k) {
@@ -1755,6 +1798,46 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
         CK(f->chi_dr.upload(lat->chi_dr.data(), lat->chi_dr.size(), st));
         CK(f->chi.alloc(lat->chi_map.size() * g.nc * ts));
     }
+    if (lat->nc == 16) {
+        // TRI core: component maps, lattice-sum entries per output (site, mu nu): for every
+        // table entry (rA, mA, rB, mB) of the site and every l, the product of row A component
+        // (mu, l) and row B component (l, nu) with the sign of both maps and of i^{iota}
+        const int Ns = lat->Ns;
+        std::vector<int> sm((size_t)Ns * 16), om((size_t)Ns * 16);
+        for (int r = 0; r < Ns; ++r)
+            for (int c = 0; c < 16; ++c) { sm[r * 16 + c] = lat->swap_map16[r][c]; om[r * 16 + c] = lat->onsite_map16[r][c]; }
+        std::vector<int> loff((size_t)Ns * 16 + 1, 0);
+        std::vector<int2> lent;
+        for (int r = 0; r < Ns; ++r)
+            for (int c = 0; c < 16; ++c) {
+                loff[r * 16 + c] = (int)lent.size();
+                const int mu = c / 4, nu = c % 4;
+                for (int e = lat->rpa_off[r]; e < lat->rpa_off[r + 1]; ++e) {
+                    const sr::RpaEntry16& en = lat->rpa16[e];
+                    for (int l = 0; l < 4; ++l) {
+                        const int ma = en.mA[mu * 4 + l], mb = en.mB[l * 4 + nu];
+                        int sg = sr::tri::coef_t(mu, nu, l);
+                        if (ma & 16) sg = -sg;
+                        if (mb & 16) sg = -sg;
+                        const int ia = en.rA * 16 + (ma & 15), ib = en.rB * 16 + (mb & 15);
+                        lent.push_back(make_int2(ia, sg > 0 ? ib : ~ib));
+                    }
+                }
+            }
+        loff[(size_t)Ns * 16] = (int)lent.size();
+        std::vector<int> cr(lat->chi_map16.size()), cm(lat->chi_map16.size() * 16);
+        for (size_t i = 0; i < cr.size(); ++i) {
+            cr[i] = lat->chi_map16[i].r;
+            for (int c = 0; c < 16; ++c) cm[i * 16 + c] = lat->chi_map16[i].m[c];
+        }
+        CK(f->swap_map16.upload(sm.data(), sm.size(), st));
+        CK(f->onsite_map16.upload(om.data(), om.size(), st));
+        CK(f->tlat_off.upload(loff.data(), loff.size(), st));
+        CK(f->tlat_ent.upload(lent.data(), lent.size(), st));
+        CK(f->chi_r16.upload(cr.data(), cr.size(), st));
+        CK(f->chi_m16.upload(cm.data(), cm.size(), st));
+        f->nprod = (int)lent.size();
+    }
     // state
     CK(f->gam.alloc((size_t)g.N * ts));
     CK(f->G.alloc((size_t)g.nent * ts));
@@ -1777,15 +1860,18 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
     CK(cudaGetLastError());
     if (sr_status s2 = refresh_shadow(f.get(), f->G.p, f->Gf.p)) return s2;
     const bool tc_ok = precision == SR_FP32_MIXED && tc_supported(g.nc, g.nsp, f->dense);
-    f->smem_rhs = precision == SR_FP32_MIXED ? f32_smem_bytes(g.Ns, g.nsp, g.nc, f->nprod, f->dense)
-                                             : rhs_smem_bytes(g, f->nprod, f->ntan ? sizeof(DualT) : sizeof(double));
+    f->smem_rhs = g.nc == 16 ? tri_smem_bytes(g.Ns, tri_groups(g.Ns, kThreads))
+                  : precision == SR_FP32_MIXED ? f32_smem_bytes(g.Ns, g.nsp, g.nc, f->nprod, f->dense)
+                                               : rhs_smem_bytes(g, f->nprod, f->ntan ? sizeof(DualT) : sizeof(double));
     if (tc_ok) f->smem_tc = f32_smem_bytes(g.Ns, g.nsp, g.nc, f->nprod, f->dense, true);
     f->use_tc = false;   // off by default: slower than the CUDA-core contraction on the square
                          // J1-J2 and pyrochlore workloads (operand staging outweighs the contraction)
     CK(f->tcfail.alloc(1));
     CK(cudaMemsetAsync(f->tcfail.p, 0, sizeof(int), st));
     if (f->smem_rhs > 227 * 1024) return fail(SR_EUNSUPPORTED, "lattice too large for one CTA's shared memory (%zu bytes)", f->smem_rhs);
-    if (f->ntan) {
+    if (g.nc == 16) {
+        CK(ensure_smem((const void*)k_gamma_rhs_tri, f->smem_rhs));
+    } else if (f->ntan) {
         CK(ensure_smem((const void*)k_gamma_rhs<DualT, 2>, f->smem_rhs));
         CK(ensure_smem((const void*)k_gamma_rhs<DualT, 4>, f->smem_rhs));
     } else if (precision == SR_FP64) {
@@ -2097,7 +2183,10 @@ extern "C" sr_status sr_measure_susceptibility(sr_flow* f, int n_k, const double
     const Geo& g = f->g;
     const int npairs = (int)lat->chi_map.size();
     Tabs tb = f->tabs();
-    if (g.nc == 2)
+    if (g.nc == 16)
+        k_chi_tri<<<npairs, 128, 0, f->stream>>>(g, tb, f->tabs_tri(), f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_r16.p, f->chi_m16.p,
+                                                 f->chi_onsite.p, lat->Ntot, f->chi.p);
+    else if (g.nc == 2)
         k_chi<double, 2><<<npairs, 128, 0, f->stream>>>(g, tb, f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_map.p, f->chi_onsite.p, lat->Ntot, f->chi.p);
     else
         k_chi<double, 4><<<npairs, 128, 0, f->stream>>>(g, tb, f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_map.p, f->chi_onsite.p, lat->Ntot, f->chi.p);
@@ -2107,7 +2196,10 @@ extern "C" sr_status sr_measure_susceptibility(sr_flow* f, int n_k, const double
         if (f->kbuf.n < (size_t)3 * n_k) CK(f->kbuf.alloc((size_t)3 * n_k));
         if (f->chik.n < (size_t)n_k) CK(f->chik.alloc(n_k));
         CK(cudaMemcpyAsync(f->kbuf.p, k_xyz, sizeof(double) * 3 * n_k, cudaMemcpyHostToDevice, f->stream));
-        k_chi_k<double><<<(n_k + 127) / 128, 128, 0, f->stream>>>(n_k, f->kbuf.p, f->chi.p, f->chi_dr.p, npairs, lat->nb, g.nc, f->chik.p);
+        if (g.nc == 16)
+            k_chi_k_tri<<<(n_k + 127) / 128, 128, 0, f->stream>>>(n_k, f->kbuf.p, f->chi.p, f->chi_dr.p, npairs, lat->nb, f->chik.p);
+        else
+            k_chi_k<double><<<(n_k + 127) / 128, 128, 0, f->stream>>>(n_k, f->kbuf.p, f->chi.p, f->chi_dr.p, npairs, lat->nb, g.nc, f->chik.p);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(chi_k, f->chik.p, sizeof(double) * n_k, cudaMemcpyDeviceToHost, f->stream));
         CK(cudaStreamSynchronize(f->stream));
@@ -2167,6 +2259,7 @@ static sr_status adj_check(const sr_flow* f) {
     if (!f) return fail(SR_EINVAL, "null flow");
     if (f->ntan) return fail(SR_EUNSUPPORTED, "the adjoint is defined for plain flows, not tangent flows");
     if (f->prec != SR_FP64) return fail(SR_EUNSUPPORTED, "the adjoint is defined for FP64 flows");
+    if (f->g.nc == 16) return fail(SR_EUNSUPPORTED, "the adjoint is provided for the SU2 and XYZ cores");
     return SR_OK;
 }
 
@@ -2785,13 +2878,19 @@ extern "C" sr_status sr_measure_susceptibility_static(sr_flow* f, int n_k, const
         scratch = g_chi_static_ptr[dev];
     }
     Tabs tb = f->tabs();
-    if (g.nc == 2)
+    if (g.nc == 16)
+        k_chi_tri<<<npairs, 128, 0, f->stream>>>(g, tb, f->tabs_tri(), f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_r16.p, f->chi_m16.p,
+                                                 f->chi_onsite.p, lat->Ntot, scratch);
+    else if (g.nc == 2)
         k_chi<double, 2><<<npairs, 128, 0, f->stream>>>(g, tb, f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_map.p, f->chi_onsite.p, lat->Ntot, scratch);
     else
         k_chi<double, 4><<<npairs, 128, 0, f->stream>>>(g, tb, f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_map.p, f->chi_onsite.p, lat->Ntot, scratch);
     CK(cudaGetLastError());
     if (n_k > 0) {
-        k_chi_k<double><<<(n_k + 127) / 128, 128, 0, f->stream>>>(n_k, d_k_xyz, scratch, f->chi_dr.p, npairs, lat->nb, g.nc, d_chi_k);
+        if (g.nc == 16)
+            k_chi_k_tri<<<(n_k + 127) / 128, 128, 0, f->stream>>>(n_k, d_k_xyz, scratch, f->chi_dr.p, npairs, lat->nb, d_chi_k);
+        else
+            k_chi_k<double><<<(n_k + 127) / 128, 128, 0, f->stream>>>(n_k, d_k_xyz, scratch, f->chi_dr.p, npairs, lat->nb, g.nc, d_chi_k);
         CK(cudaGetLastError());
     }
     return SR_OK;

@@ -80,6 +80,31 @@ sr::PairMap sr_lattice::map_pair(const sr::SiteKey& i1, const sr::SiteKey& i2) c
     return pm;
 }
 
+sr::PairMap16 sr_lattice::map_pair16(const sr::SiteKey& i1, const sr::SiteKey& i2) const {
+    sr::SiteKey d;
+    for (int k = 0; k < 3; ++k) d.n[k] = i2.n[k] - i1.n[k];
+    d.b = i2.b;
+    const sr::Sym& g = T[i1.b];
+    sr::SiteKey j = g.apply(d);
+    sr::PairMap16 pm;
+    auto it = site_index.find(j);
+    if (it == site_index.end()) {
+        pm.r = -1;
+        for (int c = 0; c < 16; ++c) pm.m[c] = c;
+        return pm;
+    }
+    const int idx = it->second;
+    pm.r = site_r[idx];
+    // Gamma^{mu nu}_{i1 i2} = sg(mu) sg(nu) Gamma^{sp(mu) sp(nu)}_{ref, j}, then the site map of j
+    for (int c = 0; c < 16; ++c) {
+        const int mu = c / 4, nu = c % 4;
+        const int cj = g.sp[mu] * 4 + g.sp[nu];
+        const int neg = (g.sg[mu] * g.sg[nu] < 0) ? 16 : 0;
+        pm.m[c] = site_map16[idx][cj] ^ neg;
+    }
+    return pm;
+}
+
 namespace sr {
 
 sr_status build_lattice(const sr_lattice_desc* d, sr_lattice* lat, std::string* msg) {
@@ -88,7 +113,7 @@ sr_status build_lattice(const sr_lattice_desc* d, sr_lattice* lat, std::string* 
     lat->nb = d->n_basis;
     lat->L = d->range_L;
     lat->backend = d->backend;
-    lat->nc = d->backend == SR_SU2 ? 2 : 4;
+    lat->nc = d->backend == SR_SU2 ? 2 : (d->backend == SR_XYZ ? 4 : 16);
     std::memcpy(lat->prim, d->prim, sizeof(lat->prim));
     lat->basis.assign(d->basis_xyz, d->basis_xyz + 3 * d->n_basis);
     lat->bonds.assign(d->bonds, d->bonds + d->n_bonds);
@@ -135,9 +160,10 @@ sr_status build_lattice(const sr_lattice_desc* d, sr_lattice* lat, std::string* 
     // the chosen core must be able to represent the couplings
     for (auto& kv : cmap) {
         const auto& J = kv.second;
+        if (lat->backend == SR_TRI) continue;
         for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j)
             if (i != j && std::fabs(J[3 * i + j]) > eps) {
-                *msg = "off-diagonal couplings need the TRI core, which this build does not provide";
+                *msg = "off-diagonal couplings need the TRI core";
                 return SR_EUNSUPPORTED;
             }
         if (lat->backend == SR_SU2 && (std::fabs(J[0] - J[4]) > eps || std::fabs(J[0] - J[8]) > eps)) {
@@ -166,7 +192,25 @@ sr_status build_lattice(const sr_lattice_desc* d, sr_lattice* lat, std::string* 
     std::vector<bool> haveT(nb, false);
     lat->G0.clear();
     std::vector<int> perm_order;
-    int nperm = lat->backend == SR_SU2 ? 1 : 6;
+    // candidate spin maps: SU2 the identity, XYZ the permutations of x, y, z, TRI the 24
+    // proper rotations among the signed permutations
+    struct SpinMap { int sp[3]; int sg[3]; };
+    std::vector<SpinMap> spin_maps;
+    if (lat->backend == SR_SU2) spin_maps.push_back({{1, 2, 3}, {1, 1, 1}});
+    else if (lat->backend == SR_XYZ) {
+        for (int p = 0; p < 6; ++p) spin_maps.push_back({{kPerms[p][0], kPerms[p][1], kPerms[p][2]}, {1, 1, 1}});
+    } else {
+        for (int p = 0; p < 6; ++p)
+            for (int sm = 0; sm < 8; ++sm) {
+                SpinMap q{{kPerms[p][0], kPerms[p][1], kPerms[p][2]}, {(sm & 1) ? -1 : 1, (sm & 2) ? -1 : 1, (sm & 4) ? -1 : 1}};
+                // determinant of the signed permutation matrix: parity of the permutation times the signs
+                int inv = 0;
+                for (int a = 0; a < 3; ++a) for (int b = a + 1; b < 3; ++b) inv += q.sp[a] > q.sp[b];
+                const int det = ((inv & 1) ? -1 : 1) * q.sg[0] * q.sg[1] * q.sg[2];
+                if (det == 1) spin_maps.push_back(q);
+            }
+    }
+    const int nperm = (int)spin_maps.size();
 
     for (const Cand& c0 : cands) {
         if (std::fabs(dot(c0.v, c0.v) - G[0][0]) > geps) continue;
@@ -218,7 +262,8 @@ sr_status build_lattice(const sr_lattice_desc* d, sr_lattice* lat, std::string* 
                     // couplings onto couplings up to one spin permutation
                     int chosen = -1;
                     for (int p = 0; p < nperm && chosen < 0; ++p) {
-                        const int* sp = kPerms[p];  // spin x,y,z -> sp[0], sp[1], sp[2] (1-based)
+                        const int* sp = spin_maps[p].sp;  // spin x,y,z -> sp[0], sp[1], sp[2] (1-based)
+                        const int* sgn = spin_maps[p].sg;
                         bool good = true;
                         for (auto& kv : cmap) {
                             SiteKey s1{{0, 0, 0}, kv.first.bi}, s2{{kv.first.d0, kv.first.d1, kv.first.d2}, kv.first.bj};
@@ -227,14 +272,15 @@ sr_status build_lattice(const sr_lattice_desc* d, sr_lattice* lat, std::string* 
                             auto it = cmap.find(k);
                             for (int a = 0; a < 3 && good; ++a) for (int bb = 0; bb < 3 && good; ++bb) {
                                 double Jimg = it == cmap.end() ? 0.0 : it->second[3 * (sp[a] - 1) + (sp[bb] - 1)];
-                                if (std::fabs(Jimg - kv.second[3 * a + bb]) > eps) good = false;
+                                if (std::fabs(Jimg - sgn[a] * sgn[bb] * kv.second[3 * a + bb]) > eps) good = false;
                             }
                             if (!good) break;
                         }
                         if (good) chosen = p;
                     }
                     if (chosen < 0) continue;
-                    g.sp = {0, kPerms[chosen][0], kPerms[chosen][1], kPerms[chosen][2]};
+                    g.sp = {0, spin_maps[chosen].sp[0], spin_maps[chosen].sp[1], spin_maps[chosen].sp[2]};
+                    g.sg = {1, spin_maps[chosen].sg[0], spin_maps[chosen].sg[1], spin_maps[chosen].sg[2]};
                     if (src == 0) lat->G0.push_back(g);
                     if (!haveT[src]) { lat->T[src] = g; haveT[src] = true; }
                 }
@@ -300,6 +346,11 @@ sr_status build_lattice(const sr_lattice_desc* d, sr_lattice* lat, std::string* 
     // orbits of the point group: representative = first site of the orbit in BFS order
     lat->site_r.assign(ntot, -1);
     lat->site_perm.assign(ntot, Perm{0, 1, 2, 3});
+    {
+        Map16 id;
+        for (int c = 0; c < 16; ++c) id[c] = c;
+        lat->site_map16.assign(ntot, id);
+    }
     lat->rep.clear();
     for (int i = 0; i < ntot; ++i) {
         if (lat->site_r[i] >= 0) continue;
@@ -317,6 +368,11 @@ sr_status build_lattice(const sr_lattice_desc* d, sr_lattice* lat, std::string* 
             Perm inv{0, 0, 0, 0};
             for (int c = 0; c < 4; ++c) inv[g.sp[c]] = c;
             lat->site_perm[jj] = inv;
+            // TRI: Gamma^{sp(mu) sp(nu)}_{ref, j} = sg(mu) sg(nu) Gamma^{mu nu}_{ref, rep}
+            for (int c = 0; c < 16; ++c) {
+                const int mu = inv[c / 4], nu = inv[c % 4];
+                lat->site_map16[jj][c] = (mu * 4 + nu) | ((g.sg[mu] * g.sg[nu] < 0) ? 16 : 0);
+            }
         }
     }
     lat->Ns = (int)lat->rep.size();
@@ -332,6 +388,8 @@ sr_status build_lattice(const sr_lattice_desc* d, sr_lattice* lat, std::string* 
     lat->swap_perm.assign(Ns, Perm{0, 1, 2, 3});
     lat->onsite_perm.assign(Ns, Perm{0, 1, 2, 3});
     lat->init_gamma.assign((size_t)Ns * lat->nc, 0.0);
+    lat->swap_map16.clear();
+    lat->onsite_map16.clear();
     for (int r = 0; r < Ns; ++r) {
         const SiteKey& s = lat->sites[lat->rep[r]];
         PairMap pm = lat->map_pair(s, ref);
@@ -341,9 +399,20 @@ sr_status build_lattice(const sr_lattice_desc* d, sr_lattice* lat, std::string* 
         PairMap po = lat->map_pair(s, s);
         if (po.r != 0) { *msg = "on-site pair does not map to the reference site"; return SR_ESYMMETRY; }
         lat->onsite_perm[r] = po.perm;
+        if (lat->nc == 16) {
+            const PairMap16 ps = lat->map_pair16(s, ref);
+            const PairMap16 pq = lat->map_pair16(s, s);
+            Map16 sw;
+            for (int c = 0; c < 16; ++c) sw[c] = ps.m[(c % 4) * 4 + c / 4];   // exchanged pair: mu <-> nu
+            lat->swap_map16.push_back(sw);
+            lat->onsite_map16.push_back(pq.m);
+        }
         auto it = cmap.find(PairKey{0, s.b, s.n[0], s.n[1], s.n[2]});
         if (it != cmap.end()) {
-            if (lat->nc == 2) {
+            if (lat->nc == 16) {
+                for (int a = 1; a < 4; ++a)
+                    for (int b = 1; b < 4; ++b) lat->init_gamma[(size_t)r * 16 + a * 4 + b] = it->second[3 * (a - 1) + (b - 1)] / 4.0;
+            } else if (lat->nc == 2) {
                 lat->init_gamma[(size_t)r * 2 + 1] = it->second[8] / 4.0;
             } else {
                 for (int c = 1; c < 4; ++c) lat->init_gamma[(size_t)r * 4 + c] = it->second[4 * (c - 1)] / 4.0;
@@ -359,6 +428,7 @@ sr_status build_lattice(const sr_lattice_desc* d, sr_lattice* lat, std::string* 
     // both the reference site and rep_r2, with the stored sites of (ref, j) and (j, rep_r2)
     lat->rpa_off.assign(Ns + 1, 0);
     lat->rpa.clear();
+    lat->rpa16.clear();
     for (int r2 = 0; r2 < Ns; ++r2) {
         const SiteKey& i2 = lat->sites[lat->rep[r2]];
         for (int j = 0; j < ntot; ++j) {
@@ -371,6 +441,15 @@ sr_status build_lattice(const sr_lattice_desc* d, sr_lattice* lat, std::string* 
             e.pB = pb.perm;
             if (lat->backend == SR_SU2) { e.pA = Perm{0, 1, 2, 3}; e.pB = Perm{0, 1, 2, 3}; }
             lat->rpa.push_back(e);
+            if (lat->nc == 16) {
+                RpaEntry16 e16;
+                e16.rA = e.rA;
+                e16.mA = lat->site_map16[j];
+                PairMap16 pb16 = lat->map_pair16(lat->sites[j], i2);
+                e16.rB = pb16.r;
+                e16.mB = pb16.m;
+                lat->rpa16.push_back(e16);
+            }
         }
         lat->rpa_off[r2 + 1] = (int)lat->rpa.size();
     }
@@ -378,6 +457,7 @@ sr_status build_lattice(const sr_lattice_desc* d, sr_lattice* lat, std::string* 
     // correlation sites: for each basis b the sites within range of (0, b)
     lat->chi_sites.clear();
     lat->chi_map.clear();
+    lat->chi_map16.clear();
     lat->chi_dr.clear();
     lat->chi_onsite.clear();
     for (int b = 0; b < nb; ++b) {
@@ -393,6 +473,7 @@ sr_status build_lattice(const sr_lattice_desc* d, sr_lattice* lat, std::string* 
             if (pm.r < 0) { *msg = "correlation pair out of range"; return SR_ESYMMETRY; }
             if (lat->backend == SR_SU2) pm.perm = Perm{0, 1, 2, 3};
             lat->chi_map.push_back(pm);
+            if (lat->nc == 16) lat->chi_map16.push_back(lat->map_pair16(sb, j));
             double pj[3];
             lat->position(j, pj);
             for (int k = 0; k < 3; ++k) lat->chi_dr.push_back(pb[k] - pj[k]);
@@ -427,6 +508,7 @@ std::array<double, 9> pair_coupling(const sr_lattice* lat, int b1, const SiteKey
 
 sr_status tangent_init(const sr_lattice* lat, int npar, const double* dM, std::vector<double>* out, std::string* msg) {
     const int nc = lat->nc, Ns = lat->Ns;
+    if (nc == 16) { *msg = "tangent flows are provided for the SU2 and XYZ cores"; return SR_EUNSUPPORTED; }
     const size_t ncoup = lat->couplings.size();
     out->assign((size_t)Ns * nc * npar, 0.0);
     for (int p = 0; p < npar; ++p) {

@@ -29,16 +29,34 @@ struct SiteKeyHash {
 };
 
 // A symmetry acting on sites by integer arithmetic: (n, b) -> (M n + m[b], pb[b]), with the
-// spin components permuted by sp (sp[0] = 0): J^{sp(mu) sp(nu)}_{g(i) g(j)} = J^{mu nu}_{i j}.
+// spin components mapped by the signed permutation (sp, sg) (sp[0] = 0, sg[0] = 1):
+// J^{sp(mu) sp(nu)}_{g(i) g(j)} = sg(mu) sg(nu) J^{mu nu}_{i j}.  The SU2 and XYZ cores use
+// unsigned permutations (sg = 1); the TRI core uses the proper rotations among the signed
+// permutations, under which the flow of all 16 basis functions is covariant.
 struct Sym {
     int M[3][3];
     std::vector<std::array<int, 3>> m;
     std::vector<int> pb;
     std::array<int, 4> sp;
+    std::array<int, 4> sg{{1, 1, 1, 1}};
     SiteKey apply(const SiteKey& s) const;
 };
 
 using Perm = std::array<int, 4>;
+
+// TRI core: component c = mu * 4 + nu of a pair read as stored component (m[c] & 15) of the
+// pair's irreducible site, negated when bit 4 of m[c] is set.
+using Map16 = std::array<int, 16>;
+
+struct RpaEntry16 {
+    int rA, rB;
+    Map16 mA, mB;
+};
+
+struct PairMap16 {
+    int r;      // irreducible site, -1 beyond range
+    Map16 m;
+};
 
 struct RpaEntry {
     int rA, rB;
@@ -77,7 +95,16 @@ struct sr_lattice {
     std::vector<int> swap_r;          // irreducible site of the exchanged pair (rep, ref)
     std::vector<sr::Perm> swap_perm;
     std::vector<sr::Perm> onsite_perm;  // component map of the pair (rep, rep) onto site 0
-    std::vector<double> init_gamma;     // Ns x nc, J^{cc}/4 of the pair (ref, rep)
+    std::vector<double> init_gamma;     // Ns x nc, J^{cc}/4 (TRI: J^{mu nu}/4) of the pair (ref, rep)
+
+    // TRI core (nc = 16): signed component maps with the mu <-> nu transposition of the site
+    // exchange folded into swap_map16
+    std::vector<sr::Map16> site_map16;   // per site: (ref, site) onto its irreducible site
+    std::vector<sr::Map16> swap_map16;   // per irreducible site r: component c of (ref, rep_r) at
+                                         // exchanged frequencies reads transposed (rep_r, ref)
+    std::vector<sr::Map16> onsite_map16; // per irreducible site: (rep, rep) onto site 0
+    std::vector<sr::RpaEntry16> rpa16;   // lattice-sum entries, as rpa
+    std::vector<sr::PairMap16> chi_map16;
 
     std::vector<int> rpa_off;          // Ns + 1
     std::vector<sr::RpaEntry> rpa;     // P entries, grouped by output site
@@ -90,6 +117,7 @@ struct sr_lattice {
     std::vector<int> chi_onsite;         // nb x Ntot
 
     sr::PairMap map_pair(const sr::SiteKey& i1, const sr::SiteKey& i2) const;
+    sr::PairMap16 map_pair16(const sr::SiteKey& i1, const sr::SiteKey& i2) const;
     void position(const sr::SiteKey& s, double out[3]) const;
 };
 

@@ -1,0 +1,370 @@
+// Kernels of the TRI core: the flow of all 16 basis functions Gamma^{mu nu} (FP64).
+//
+// Included by flow.cu after the forward kernels, whose propagators, node arguments and lookup
+// descriptors it shares.  Equations: arXiv:2109.13317, Sec. 3 (Eqs. frg:flowexplicit:1particle
+// and frg:flowexplicit:2particle with the parametrization Eq. frg:parametrization and the
+// relations Eq. frg:parametrizationBasis2p), discretised as in Sec. 4.2.  Storage: real
+// g^{mu nu} with Gamma^{mu nu} = i^{iota} g^{mu nu} (tri_coef.h), layout
+// [pair(s,u)][t][mu * 4 + nu][site] like the SU2 and XYZ cores.
+//
+// Lookup: the descriptor of make_desc folds the frequencies (t -> -t, s -> -s and u -> -u
+// with site exchange, s <-> u) and keeps two corner-weight sets, for functions whose second
+// spin index is 0 (factor -1 under s <-> u) and for the others; the TRI core adds the sign
+// xi(mu) xi(nu) of t -> -t and u -> -u for the six imaginary-class functions (`mneg`), and
+// the site exchange reads component nu mu of the exchanged pair (folded into swap_map).
+#pragma once
+
+#include "tri_coef.h"
+
+namespace {
+
+constexpr int kQTri = 8;   // integration nodes per shared-memory block of the TRI kernel
+
+struct TabsT {
+    const int* swap_map;    // Ns * 16: component map of the exchanged pair (transposed)
+    const int* onsite_map;  // Ns * 16: component map of (rep, rep) onto site 0
+    const int* lat_off;     // Ns * 16 + 1: lattice-sum entries of each output (site, component)
+    const int2* lat_ent;    // (row-A index, row-B index or its complement for a negative sign)
+};
+
+__device__ __forceinline__ bool tri_mixed(int c) { return ((c >> 2) == 0) != ((c & 3) == 0); }
+
+// Component c of the pair (ref, rep_r) at the descriptor's frequencies.
+__device__ __forceinline__ double tri_value(const double* __restrict__ G, const Desc<double>& d, bool mneg,
+                                            const Tabs& tb, const TabsT& tt, const Geo& g, int r, int c) {
+    int rs = r, m = c;
+    if (d.swap) { rs = tb.swap_r[r]; m = tt.swap_map[r * 16 + c]; }
+    const int cs = m & 15;
+    const double* base = G + cs * g.Ns + rs;
+    const double* wgt = (cs & 3) == 0 ? d.wd : d.ws;
+    double acc = 0.0;
+    for (int k = 0; k < d.n; ++k) acc = fma(wgt[k], base[d.off[k]], acc);
+    const bool neg = ((m & 16) != 0) != (mneg && tri_mixed(c));
+    return neg ? -acc : acc;
+}
+
+// Component map entry applied to a 16-vector v: sign * v[stored component].
+__device__ __forceinline__ double tri_mapped(const double* v, int m) { return (m & 16) ? -v[m & 15] : v[m & 15]; }
+
+// Self-energy flow (spin trace): dgamma(w) = -(1/2pi) sum_{w2 = +-Lambda} H / (w2 + gamma(w2)),
+// H = 2 sum_j Gamma^00_{ref j}(w+w2, 0, w-w2) - sum_k Gamma^kk_{ref ref}(w+w2, w2-w, 0).
+__global__ void k_sigma_rhs_tri(Geo g, Tabs tb, TabsT tt, const double* __restrict__ w, const double* __restrict__ gam,
+                                const double* __restrict__ G, double lam, double* __restrict__ dgam) {
+    __shared__ double red[2 * 32];
+    const int n = blockIdx.x;
+    const double w1 = w[n];
+    double H[2] = {0.0, 0.0};
+    for (int sg = 0; sg < 2; ++sg) {
+        const double w2 = sg == 0 ? lam : -lam;
+        Desc<double> d;
+        make_desc(w1 + w2, 0.0, w1 - w2, 1, 0, tb, g, d);
+        const bool mn = (w1 - w2) < 0.0;
+        double h = 0.0;
+        for (int r = threadIdx.x; r < g.Ns; r += blockDim.x) h += (double)tb.mult[r] * tri_value(G, d, mn, tb, tt, g, r, 0);
+        h = 2.0 * h;
+        if (threadIdx.x == 0) {
+            Desc<double> e;
+            make_desc(w1 + w2, w2 - w1, 0.0, 2, 0, tb, g, e);
+            const bool me = (w2 - w1) < 0.0;
+            double f = 0.0;
+            for (int k = 0; k < 4; ++k) f += tri_value(G, e, me, tb, tt, g, 0, 5 * k);
+            h -= f;
+        }
+        H[sg] = h;
+    }
+    block_sum<double, 2>(H, red);
+    if (threadIdx.x == 0) {
+        double acc = H[0] / (lam + interp_odd(w, tb.invh, g.N, gam, lam));
+        acc += H[1] / (-lam + interp_odd(w, tb.invh, g.N, gam, -lam));
+        dgam[n] = -acc / (2.0 * kPi);
+    }
+}
+
+// Site-local products of the s (CH = 0) or u (CH = 2) channel at one node, accumulated into
+// o[16] (A, B: the site's two rows).
+template <int CH>
+__device__ __forceinline__ void tri_su_acc(const double* __restrict__ A, const double* __restrict__ B, double* o) {
+    double a[16], b[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) { a[k] = A[k]; b[k] = B[k]; }
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+        for (int nu = 0; nu < 4; ++nu)
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) {
+                    const int cf = CH == 0 ? sr::tri::coef_s(mu, nu, x, y) : sr::tri::coef_u(mu, nu, x, y);
+                    const double p = b[(x ^ mu) * 4 + (y ^ nu)];
+                    o[mu * 4 + nu] = fma(cf > 0 ? a[x * 4 + y] : -a[x * 4 + y], p, o[mu * 4 + nu]);
+                }
+}
+
+// t-channel on-site terms: A C (C the on-site row of the pair (i2, i2)) and D B (D of (i1, i1)).
+__device__ __forceinline__ void tri_onsite_acc(const double* __restrict__ A, const double* __restrict__ B,
+                                               const double* __restrict__ C, const double* __restrict__ D, double* o) {
+    double a[16], b[16], c[16], d[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) { a[k] = A[k]; b[k] = B[k]; c[k] = C[k]; d[k] = D[k]; }
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+        for (int nu = 0; nu < 4; ++nu)
+#pragma unroll
+            for (int l = 0; l < 4; ++l)
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const int c2 = sr::tri::coef_o2(mu, nu, l, m);
+                    const int c3 = sr::tri::coef_o3(mu, nu, l, m);
+                    const double x2 = c[m * 4 + (m ^ l ^ nu)];
+                    o[mu * 4 + nu] = fma(c2 > 0 ? a[mu * 4 + l] : -a[mu * 4 + l], x2, o[mu * 4 + nu]);
+                    const double x3 = d[(mu ^ l ^ m) * 4 + l];
+                    o[mu * 4 + nu] = fma(c3 > 0 ? x3 : -x3, b[m * 4 + nu], o[mu * 4 + nu]);
+                }
+}
+
+struct ShT {
+    Desc<double>* desc;   // kQTri * 4
+    int* mneg;            // kQTri * 4
+    double* rows;         // kQTri * 2 * 16 Ns (site-major: r * 16 + c)
+    double* onrow;        // kQTri * 2 * 16
+    double* part;         // NG * Ns * 16: per node-group partial sums of the site-local products
+    double* lat;          // Ns * 16: lattice-sum integrals
+};
+
+__host__ __device__ inline size_t tri_smem_bytes(int Ns, int NG) {
+    auto rnd = [](size_t b) { return (b + 15) & ~size_t(15); };
+    return rnd(sizeof(Desc<double>) * kQTri * 4) + rnd(sizeof(int) * kQTri * 4) + rnd(sizeof(double) * kQTri * 2 * 16 * Ns) +
+           rnd(sizeof(double) * kQTri * 2 * 16) + rnd(sizeof(double) * (size_t)NG * Ns * 16) + rnd(sizeof(double) * Ns * 16);
+}
+
+__host__ __device__ inline int tri_groups(int Ns, int threads) {
+    const int ng = threads / Ns;
+    return ng < 1 ? 1 : (ng > kQTri ? kQTri : ng);
+}
+
+// dGamma/dLambda of every stored entry of one frequency triple (one CTA per triple).
+__global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, TabsT tt, const double* __restrict__ w,
+                                                            const double* __restrict__ G, const double* __restrict__ nx,
+                                                            const double* __restrict__ nW, const int* __restrict__ ncount,
+                                                            double* __restrict__ dG) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int NG = tri_groups(g.Ns, blockDim.x);
+    ShT sh;
+    {
+        size_t off = 0;
+        auto take = [&](size_t bytes) { unsigned char* q = smem + off; off += (bytes + 15) & ~size_t(15); return q; };
+        sh.desc = (Desc<double>*)take(sizeof(Desc<double>) * kQTri * 4);
+        sh.mneg = (int*)take(sizeof(int) * kQTri * 4);
+        sh.rows = (double*)take(sizeof(double) * kQTri * 2 * 16 * g.Ns);
+        sh.onrow = (double*)take(sizeof(double) * kQTri * 2 * 16);
+        sh.part = (double*)take(sizeof(double) * (size_t)NG * g.Ns * 16);
+        sh.lat = (double*)take(sizeof(double) * g.Ns * 16);
+    }
+    const int tid = threadIdx.x;
+    const int ti = blockIdx.x % g.N;
+    const int p = blockIdx.x / g.N;
+    int si = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
+    while ((si + 1) * (si + 2) / 2 <= p) ++si;
+    while (si * (si + 1) / 2 > p) --si;
+    const int ui = p - si * (si + 1) / 2;
+    const double s = w[si], t = w[ti], u = w[ui];
+    const double w1p = (s + t + u) / 2, w2p = (s - t - u) / 2, w1 = (s - t + u) / 2, w2 = (s + t - u) / 2;
+    const int row = g.Ns * 16;
+    const int nwork = g.Ns * NG;
+
+    for (int o = tid; o < NG * row; o += blockDim.x) sh.part[o] = 0.0;
+    for (int o = tid; o < row; o += blockDim.x) sh.lat[o] = 0.0;
+
+    for (int ch = 0; ch < 3; ++ch) {
+        const int vi = ch == 0 ? si : (ch == 1 ? ti : ui);
+        const int cidx = ch * g.N + vi;
+        const int nq = ncount[cidx];
+        const double* X = nx + (size_t)cidx * g.nmax;
+        const double* Wp = nW + (size_t)cidx * g.nmax;
+        const int nrow = ch == 1 ? 4 : 2;
+        for (int q0 = 0; q0 < nq; q0 += kQTri) {
+            const int qn = min(kQTri, nq - q0);
+            __syncthreads();
+            // descriptors of every row at every node of this block; the node weight goes into
+            // the corner weights of the first row (and of the second on-site row)
+            for (int idx = tid; idx < qn * nrow; idx += blockDim.x) {
+                const int q = idx / nrow, rw = idx % nrow;
+                const double x = X[q0 + q];
+                double a, b, c;
+                node_args(ch, rw, x, s, t, u, w1p, w2p, w1, w2, a, b, c);
+                const int exs = ch == 0 ? 0 : (ch == 2 ? 2 : (rw < 2 ? 1 : 2));
+                Desc<double>& d = sh.desc[q * 4 + rw];
+                make_desc(a, b, c, exs, vi, tb, g, d);
+                sh.mneg[q * 4 + rw] = (b < 0.0) != (c < 0.0);
+                if (rw == 0 || rw == 3) {
+                    const double wn = Wp[q0 + q];
+                    for (int k = 0; k < d.n; ++k) { d.wd[k] *= wn; d.ws[k] *= wn; }
+                }
+            }
+            __syncthreads();
+            for (int idx = tid; idx < qn * 2 * row; idx += blockDim.x) {
+                const int q = idx / (2 * row), rem = idx % (2 * row);
+                const int rw = rem / row, e = rem % row;
+                const int r = e >> 4, c = e & 15;
+                sh.rows[(q * 2 + rw) * row + e] = tri_value(G, sh.desc[q * 4 + rw], sh.mneg[q * 4 + rw] != 0, tb, tt, g, r, c);
+            }
+            if (ch == 1)
+                for (int j = tid; j < qn * 2 * 16; j += blockDim.x) {
+                    const int q = j / 32, rr = (j / 16) % 2, c = j % 16;
+                    sh.onrow[(q * 2 + rr) * 16 + c] =
+                        tri_value(G, sh.desc[q * 4 + 2 + rr], sh.mneg[q * 4 + 2 + rr] != 0, tb, tt, g, 0, c);
+                }
+            __syncthreads();
+            // site-local products: work item (site r, node group gq) owns part[gq][r]
+            for (int wk = tid; wk < nwork; wk += blockDim.x) {
+                const int r = wk % g.Ns, gq = wk / g.Ns;
+                double o[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) o[k] = 0.0;
+                for (int q = gq; q < qn; q += NG) {
+                    const double* A = sh.rows + (q * 2) * row + r * 16;
+                    const double* B = A + row;
+                    if (ch == 0) tri_su_acc<0>(A, B, o);
+                    else if (ch == 2) tri_su_acc<2>(A, B, o);
+                    else {
+                        double Cp[16];
+                        const double* C0 = sh.onrow + (q * 2) * 16;
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) Cp[k] = tri_mapped(C0, tt.onsite_map[r * 16 + k]);
+                        tri_onsite_acc(A, B, Cp, sh.onrow + (q * 2 + 1) * 16, o);
+                    }
+                }
+                double* P = sh.part + (size_t)gq * row + r * 16;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) P[k] += o[k];
+            }
+            // lattice sum: every output (site, component) integrates its signed products
+            if (ch == 1)
+                for (int o = tid; o < row; o += blockDim.x) {
+                    double acc = 0.0;
+                    for (int k = tt.lat_off[o]; k < tt.lat_off[o + 1]; ++k) {
+                        const int2 en = tt.lat_ent[k];
+                        const int ib = en.y < 0 ? ~en.y : en.y;
+                        double a = 0.0;
+                        for (int q = 0; q < qn; ++q) a = fma(sh.rows[(q * 2) * row + en.x], sh.rows[(q * 2 + 1) * row + ib], a);
+                        acc += en.y < 0 ? -a : a;
+                    }
+                    sh.lat[o] += acc;
+                }
+        }
+    }
+    __syncthreads();
+    for (int o = tid; o < row; o += blockDim.x) {
+        double a = 0.0;
+        for (int k = 0; k < NG; ++k) a += sh.part[(size_t)k * row + o];
+        const int r = o >> 4, c = o & 15;
+        dG[((size_t)(p * g.N + ti) * 16 + c) * g.Ns + r] = a - 2.0 * sh.lat[o];
+    }
+}
+
+// Correlations chi^{mu nu}_{b j}, all 16 components (Eq. frg:correlation), one block per
+// (b, j): bubble delta_{mu nu} (local) and the product-trapezoid vertex term.
+__global__ void k_chi_tri(Geo g, Tabs tb, TabsT tt, const double* __restrict__ w, const double* __restrict__ gam,
+                          const double* __restrict__ G, double lam, const int* __restrict__ cr,
+                          const int* __restrict__ cm, const int* __restrict__ onsite, int ntot, double* __restrict__ chi) {
+    __shared__ double y[kMaxFreq + 1];
+    __shared__ double Wn[kMaxFreq + 1];
+    __shared__ double red[16 * 32];
+    __shared__ int Ksh;
+    const int pidx = blockIdx.x;      // b * ntot + j
+    const int b = pidx / ntot;
+    const int on = onsite[pidx];
+    const int r = cr[pidx];
+    const int r0 = cr[b * ntot];      // the first site of each list is (0, b) itself
+    const int* m = cm + (size_t)pidx * 16;
+    const int* m0 = cm + (size_t)b * ntot * 16;
+    const int N = g.N;
+    if (threadIdx.x == 0) {
+        int K = 0;
+        y[K++] = lam;
+        for (int i = 0; i < N; ++i) if (w[i] > lam) y[K++] = w[i];
+        for (int k = 0; k < K; ++k) Wn[k] = 0.0;
+        for (int k = 0; k + 1 < K; ++k) {
+            const double ya = y[k] + interp_odd(w, tb.invh, N, gam, y[k]);
+            const double yb = y[k + 1] + interp_odd(w, tb.invh, N, gam, y[k + 1]);
+            const double seg = (y[k + 1] - y[k]) / (ya * yb);
+            Wn[k] += 0.5 * seg;
+            Wn[k + 1] += 0.5 * seg;
+        }
+        Wn[K - 1] += 1.0 / (y[K - 1] + interp_odd(w, tb.invh, N, gam, y[K - 1]));
+        Ksh = K;
+    }
+    __syncthreads();
+    const int K = Ksh, M = 2 * K;
+    double acc[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+    for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+        const int pi = idx / M, qi = idx % M;
+        const double xp = pi < K ? y[pi] : -y[pi - K];
+        const double xq = qi < K ? y[qi] : -y[qi - K];
+        const double wpq = Wn[pi % K] * Wn[qi % K];
+        Desc<double> d;
+        make_desc(xp + xq, 0.0, xp - xq, 1, 0, tb, g, d);
+        const bool mn = (xp - xq) < 0.0;
+        double v[16], e[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const int mc = m[c];
+            const double x = tri_value(G, d, mn, tb, tt, g, r, mc & 15);
+            v[c] = (mc & 16) ? -x : x;
+        }
+        if (on) {
+            make_desc(xp + xq, xq - xp, 0.0, 2, 0, tb, g, d);
+            const bool me = (xq - xp) < 0.0;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const int mc = m0[c];
+                const double x = tri_value(G, d, me, tb, tt, g, r0, mc & 15);
+                e[c] = (mc & 16) ? -x : x;
+            }
+        }
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+            for (int nu = 0; nu < 4; ++nu) {
+                double F = 4.0 * v[mu * 4 + nu];
+                if (on) {
+                    double x = 0.0;
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) {
+                        const double ev = e[(mu ^ nu ^ l) * 4 + l];
+                        x += sr::tri::coef_x(mu, nu, l) > 0 ? 2.0 * ev : -2.0 * ev;
+                    }
+                    F -= x;
+                }
+                acc[mu * 4 + nu] += wpq * F;
+            }
+    }
+    block_sum<double, 16>(acc, red);
+    if (threadIdx.x == 0) {
+        double bub = 0.0;
+        for (int k = 0; k < K; ++k) bub += Wn[k];
+        bub = bub / (2.0 * kPi);
+        for (int c = 0; c < 16; ++c)
+            chi[(size_t)pidx * 16 + c] = ((on && (c >> 2) == (c & 3)) ? bub : 0.0) - acc[c] / (16.0 * kPi * kPi);
+    }
+}
+
+// chi(k) = (1/N_b) sum_{b, j} cos(k (r_b - r_j)) (chi^xx + chi^yy + chi^zz)_{b j}.
+__global__ void k_chi_k_tri(int nk, const double* __restrict__ kp, const double* __restrict__ chi,
+                            const double* __restrict__ dr, int npairs, int nb, double* __restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nk) return;
+    const double kx = kp[3 * i], ky = kp[3 * i + 1], kz = kp[3 * i + 2];
+    double acc = 0.0;
+    for (int p = 0; p < npairs; ++p) {
+        const double sp = chi[(size_t)p * 16 + 5] + chi[(size_t)p * 16 + 10] + chi[(size_t)p * 16 + 15];
+        acc += cos(kx * dr[3 * p] + ky * dr[3 * p + 1] + kz * dr[3 * p + 2]) * sp;
+    }
+    out[i] = acc / (double)nb;
+}
+
+}  // namespace

@@ -67,3 +67,28 @@ def synthetic_state(of: "O.OracleFlow", model, seed: int = 0, amp: float = 0.3):
                 blk[k, c] = J[c - 1, c - 1] / 4.0 + amp * damp * (a1 / (1.0 + 0.5 * (S + U) + T) + a2 * np.exp(-(S + U) / (1.0 + T)) * 0.2)
     gam = 0.2 * np.tanh(w) + 0.05 * w / (1 + w)
     return gam, G
+
+
+IMAG_CLASS = np.array([(c // 4 == 0) != (c % 4 == 0) for c in range(16)])
+
+
+def tri_real(arr: np.ndarray, axis: int) -> np.ndarray:
+    """Library storage of complex TRI values along the component axis: the real part of the
+    real-class functions, the imaginary part of the six imaginary-class ones."""
+    sh = [1] * arr.ndim
+    sh[axis] = 16
+    m = IMAG_CLASS.reshape(sh)
+    return np.where(m, arr.imag, arr.real)
+
+
+def tri_oracle_to_gpu(of: "O.OracleFlowTRI", lat, arr_oracle: np.ndarray) -> np.ndarray:
+    """Map an oracle TRI Gamma array (complex, layout [b][k][mu nu][pair][t]) onto the library
+    layout [pair][t][mu nu][r] (real storage) through the representative sites."""
+    reps = lat.representatives()
+    blk = of.block(arr_oracle, 0)
+    out = np.zeros((of.npair, of.N, 16, lat.N_s))
+    for r, rep in enumerate(reps):
+        k = of.find(0, rep[:3], int(rep[3]))
+        assert k >= 0, "representative outside the oracle's range"
+        out[:, :, :, r] = np.transpose(tri_real(blk[k], 0), (1, 2, 0))
+    return out

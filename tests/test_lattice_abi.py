@@ -128,12 +128,40 @@ def test_symmetry_tables_against_unreduced_oracle(model, L):
     assert np.abs(G).max() > 0
 
 
+@pytest.mark.parametrize("model,L", [(W.kagome_dm(1.0, 0.5), 2), (W.rotated(W.kagome_dm(1.0, 0.3), np.eye(3)[[1, 2, 0]]), 2),
+                                     (W.nn_heisenberg(W.honeycomb()), 2)])
+def test_tri_symmetry_tables_against_unreduced_oracle(model, L):
+    """TRI core: every pair (b, j) of the oracle's translation-only storage maps to an
+    irreducible site and a signed permutation of the 16 basis functions; after a few flow
+    steps the oracle's value of every component equals the signed value stored for its image
+    (lattice symmetries combined with proper spin rotations are exact symmetries of the flow)."""
+    mesh = O.mesh_exponential(5, 0.05, 10.0)
+    of = O.OracleFlowTRI(model, L, mesh)
+    for a, b in zip([6.0, 3.0], [3.0, 1.5]):
+        of.euler(a, b)
+    lat = sr.Lattice.from_model(model, L, backend=sr.SR_TRI)
+    assert lat.n_comp == 16
+    _, G = of.get_state()
+    reps = lat.representatives()
+    ref_blk = of.block(G, 0)
+    rep_k = [of.find(0, r[:3], int(r[3])) for r in reps]
+    nonid = 0
+    for b in range(of.nb):
+        blk = of.block(G, b)
+        for k, s in enumerate(of.sites(b)):
+            r, comp, sign = lat.map_pair_components([0, 0, 0, b], s)
+            assert r >= 0
+            nonid += int(np.any(comp != np.arange(16)) or np.any(sign < 0))
+            np.testing.assert_allclose(blk[k], sign[:, None, None] * ref_blk[rep_k[r], comp], rtol=1e-11, atol=1e-14)
+    assert np.abs(G).max() > 0
+    assert lat.N_s < sum(of.nsite)        # the point group reduced the storage
+    if model.cell.name == "kagome":
+        assert nonid > 0                 # and some images carry a non-trivial spin map
+
+
 def test_errors_are_reported():
-    # TRI core and off-diagonal couplings are not provided
-    m = W.nn_heisenberg(W.square())
-    with pytest.raises(sr.SrError) as e:
-        sr.Lattice.from_model(m, 2, backend=2)
-    assert e.value.status == 7
+    # the TRI core accepts any coupling; TRI flows run in FP64 only (checked on the GPU)
+    assert sr.Lattice.from_model(W.nn_heisenberg(W.square()), 2, backend=2).n_comp == 16
     m2 = W.nn_heisenberg(W.square())
     m2.couplings[0].M = np.array([[0, 1.0, 0], [0, 0, 0], [0, 0, 0]])
     with pytest.raises(sr.SrError) as e:
