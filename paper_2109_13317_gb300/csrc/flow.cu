@@ -1528,7 +1528,7 @@ static sr_status run_rhs(sr_flow* f, double lam, const double* gam_s, const doub
         return SR_OK;
     }
     if (g.nc == 16) {
-        // TRI core (FP64)
+        // TRI core: FP64 state and lookups; rows and products in FP64 or FP32
         const TabsT tt = f->tabs_tri();
         if (sr_status s = prof_begin(f, 0, &e0)) return s;
         k_sigma_rhs_tri<<<g.N, 64, 0, f->stream>>>(g, tb, tt, f->w.p, gam_s, G_s, lam, dgam_o);
@@ -1538,7 +1538,10 @@ static sr_status run_rhs(sr_flow* f, double lam, const double* gam_s, const doub
                                                                f->ncount.p, nullptr);
         if (sr_status s = prof_end(f, 1, e0)) return s;
         if (sr_status s = prof_begin(f, 2, &e0)) return s;
-        k_gamma_rhs_tri<<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, tt, f->w.p, G_s, f->nx.p, f->nW.p, f->ncount.p, dG_o);
+        if (f->prec == SR_FP64)
+            k_gamma_rhs_tri<double><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, tt, f->w.p, G_s, f->nx.p, f->nW.p, f->ncount.p, dG_o);
+        else
+            k_gamma_rhs_tri<float><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, tt, f->w.p, G_s, f->nx.p, f->nW.p, f->ncount.p, dG_o);
         if (sr_status s = prof_end(f, 2, e0)) return s;
         CK(cudaGetLastError());
         f->n_rhs++;
@@ -1576,7 +1579,7 @@ static sr_status run_rhs(sr_flow* f, double lam, const double* gam_s, const doub
 }
 
 static sr_status refresh_shadow(sr_flow* f, const double* G_s, float* Gf_s) {
-    if (f->prec != SR_FP32_MIXED) return SR_OK;
+    if (f->prec != SR_FP32_MIXED || f->g.nc == 16) return SR_OK;   // the TRI kernel reads the FP64 state
     long n = f->g.nentp;
     k_shadow<<<(unsigned)((n + 255) / 256), 256, 0, f->stream>>>(f->g, f->tabs(), G_s, Gf_s, f->has_swap ? 1 : 0);
     CK(cudaGetLastError());
@@ -1678,7 +1681,6 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
     }
     if (!(lambda_init > 0.0) || !std::isfinite(lambda_init)) return fail(SR_EINVAL, "lambda_init must be positive");
     if (precision != SR_FP64 && precision != SR_FP32_MIXED) return fail(SR_EINVAL, "unknown precision");
-    if (lat->nc == 16 && precision != SR_FP64) return fail(SR_EUNSUPPORTED, "the TRI core runs in FP64");
     std::unique_ptr<sr_flow> f(new (std::nothrow) sr_flow());
     if (!f) return fail(SR_ENOMEM, "out of host memory");
     f->lat = lat;
@@ -1843,7 +1845,7 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
     CK(f->G.alloc((size_t)g.nent * ts));
     CK(f->dgam.alloc((size_t)g.N * ts));
     CK(f->dG.alloc((size_t)g.nent * ts));
-    if (precision == SR_FP32_MIXED) CK(f->Gf.alloc((size_t)g.nentp * (f->has_swap ? 2 : 1)));
+    if (precision == SR_FP32_MIXED && g.nc != 16) CK(f->Gf.alloc((size_t)g.nentp * (f->has_swap ? 2 : 1)));
     CK(f->nx.alloc((size_t)3 * g.N * g.nmax));
     CK(f->nW.alloc((size_t)3 * g.N * g.nmax * ts));
     CK(f->nWf.alloc((size_t)3 * g.N * g.nmax));
@@ -1860,7 +1862,7 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
     CK(cudaGetLastError());
     if (sr_status s2 = refresh_shadow(f.get(), f->G.p, f->Gf.p)) return s2;
     const bool tc_ok = precision == SR_FP32_MIXED && tc_supported(g.nc, g.nsp, f->dense);
-    f->smem_rhs = g.nc == 16 ? tri_smem_bytes(g.Ns, tri_groups(g.Ns, kThreads))
+    f->smem_rhs = g.nc == 16 ? tri_smem_bytes(g.Ns, tri_groups(g.Ns, kThreads), precision == SR_FP64 ? sizeof(double) : sizeof(float))
                   : precision == SR_FP32_MIXED ? f32_smem_bytes(g.Ns, g.nsp, g.nc, f->nprod, f->dense)
                                                : rhs_smem_bytes(g, f->nprod, f->ntan ? sizeof(DualT) : sizeof(double));
     if (tc_ok) f->smem_tc = f32_smem_bytes(g.Ns, g.nsp, g.nc, f->nprod, f->dense, true);
@@ -1870,7 +1872,8 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
     CK(cudaMemsetAsync(f->tcfail.p, 0, sizeof(int), st));
     if (f->smem_rhs > 227 * 1024) return fail(SR_EUNSUPPORTED, "lattice too large for one CTA's shared memory (%zu bytes)", f->smem_rhs);
     if (g.nc == 16) {
-        CK(ensure_smem((const void*)k_gamma_rhs_tri, f->smem_rhs));
+        if (precision == SR_FP64) CK(ensure_smem((const void*)k_gamma_rhs_tri<double>, f->smem_rhs));
+        else CK(ensure_smem((const void*)k_gamma_rhs_tri<float>, f->smem_rhs));
     } else if (f->ntan) {
         CK(ensure_smem((const void*)k_gamma_rhs<DualT, 2>, f->smem_rhs));
         CK(ensure_smem((const void*)k_gamma_rhs<DualT, 4>, f->smem_rhs));
@@ -2666,6 +2669,7 @@ extern "C" sr_status sr_batch_create(int n, sr_flow* const* flows, sr_batch** ou
         sr_flow* f = flows[i];
         if (!f) return fail(SR_EINVAL, "null flow %d", i);
         if (f->prec != SR_FP32_MIXED) return fail(SR_EUNSUPPORTED, "batched flows use the FP32-mixed kernels (flow %d is FP64)", i);
+        if (f->g.nc == 16) return fail(SR_EUNSUPPORTED, "batched flows are provided for the SU2 and XYZ cores (flow %d is TRI)", i);
         b->flows.push_back(f);
     }
     // instances grouped by kind and by the shared memory their vertex flow needs (each class

@@ -1,4 +1,5 @@
-// Kernels of the TRI core: the flow of all 16 basis functions Gamma^{mu nu} (FP64).
+// Kernels of the TRI core: the flow of all 16 basis functions Gamma^{mu nu} (FP64 state; the
+// vertex products in FP64, or in FP32 for the mixed-precision flow).
 //
 // Included by flow.cu after the forward kernels, whose propagators, node arguments and lookup
 // descriptors it shares.  Equations: arXiv:2109.13317, Sec. 3 (Eqs. frg:flowexplicit:1particle
@@ -43,9 +44,6 @@ __device__ __forceinline__ double tri_value(const double* __restrict__ G, const 
     return neg ? -acc : acc;
 }
 
-// Component map entry applied to a 16-vector v: sign * v[stored component].
-__device__ __forceinline__ double tri_mapped(const double* v, int m) { return (m & 16) ? -v[m & 15] : v[m & 15]; }
-
 // Self-energy flow (spin trace): dgamma(w) = -(1/2pi) sum_{w2 = +-Lambda} H / (w2 + gamma(w2)),
 // H = 2 sum_j Gamma^00_{ref j}(w+w2, 0, w-w2) - sum_k Gamma^kk_{ref ref}(w+w2, w2-w, 0).
 __global__ void k_sigma_rhs_tri(Geo g, Tabs tb, TabsT tt, const double* __restrict__ w, const double* __restrict__ gam,
@@ -82,9 +80,9 @@ __global__ void k_sigma_rhs_tri(Geo g, Tabs tb, TabsT tt, const double* __restri
 
 // Site-local products of the s (CH = 0) or u (CH = 2) channel at one node, accumulated into
 // o[16] (A, B: the site's two rows).
-template <int CH>
-__device__ __forceinline__ void tri_su_acc(const double* __restrict__ A, const double* __restrict__ B, double* o) {
-    double a[16], b[16];
+template <int CH, typename R>
+__device__ __forceinline__ void tri_su_acc(const R* __restrict__ A, const R* __restrict__ B, R* o) {
+    R a[16], b[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) { a[k] = A[k]; b[k] = B[k]; }
 #pragma unroll
@@ -96,15 +94,16 @@ __device__ __forceinline__ void tri_su_acc(const double* __restrict__ A, const d
 #pragma unroll
                 for (int y = 0; y < 4; ++y) {
                     const int cf = CH == 0 ? sr::tri::coef_s(mu, nu, x, y) : sr::tri::coef_u(mu, nu, x, y);
-                    const double p = b[(x ^ mu) * 4 + (y ^ nu)];
-                    o[mu * 4 + nu] = fma(cf > 0 ? a[x * 4 + y] : -a[x * 4 + y], p, o[mu * 4 + nu]);
+                    const R p = b[(x ^ mu) * 4 + (y ^ nu)];
+                    o[mu * 4 + nu] = fmadd(cf > 0 ? a[x * 4 + y] : -a[x * 4 + y], p, o[mu * 4 + nu]);
                 }
 }
 
 // t-channel on-site terms: A C (C the on-site row of the pair (i2, i2)) and D B (D of (i1, i1)).
-__device__ __forceinline__ void tri_onsite_acc(const double* __restrict__ A, const double* __restrict__ B,
-                                               const double* __restrict__ C, const double* __restrict__ D, double* o) {
-    double a[16], b[16], c[16], d[16];
+template <typename R>
+__device__ __forceinline__ void tri_onsite_acc(const R* __restrict__ A, const R* __restrict__ B, const R* __restrict__ C,
+                                               const R* __restrict__ D, R* o) {
+    R a[16], b[16], c[16], d[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) { a[k] = A[k]; b[k] = B[k]; c[k] = C[k]; d[k] = D[k]; }
 #pragma unroll
@@ -117,26 +116,28 @@ __device__ __forceinline__ void tri_onsite_acc(const double* __restrict__ A, con
                 for (int m = 0; m < 4; ++m) {
                     const int c2 = sr::tri::coef_o2(mu, nu, l, m);
                     const int c3 = sr::tri::coef_o3(mu, nu, l, m);
-                    const double x2 = c[m * 4 + (m ^ l ^ nu)];
-                    o[mu * 4 + nu] = fma(c2 > 0 ? a[mu * 4 + l] : -a[mu * 4 + l], x2, o[mu * 4 + nu]);
-                    const double x3 = d[(mu ^ l ^ m) * 4 + l];
-                    o[mu * 4 + nu] = fma(c3 > 0 ? x3 : -x3, b[m * 4 + nu], o[mu * 4 + nu]);
+                    const R x2 = c[m * 4 + (m ^ l ^ nu)];
+                    o[mu * 4 + nu] = fmadd(c2 > 0 ? a[mu * 4 + l] : -a[mu * 4 + l], x2, o[mu * 4 + nu]);
+                    const R x3 = d[(mu ^ l ^ m) * 4 + l];
+                    o[mu * 4 + nu] = fmadd(c3 > 0 ? x3 : -x3, b[m * 4 + nu], o[mu * 4 + nu]);
                 }
 }
 
+template <typename R>
 struct ShT {
     Desc<double>* desc;   // kQTri * 4
     int* mneg;            // kQTri * 4
-    double* rows;         // kQTri * 2 * 16 Ns (site-major: r * 16 + c)
-    double* onrow;        // kQTri * 2 * 16
-    double* part;         // NG * Ns * 16: per node-group partial sums of the site-local products
-    double* lat;          // Ns * 16: lattice-sum integrals
+    R* rows;              // kQTri * 2 * 16 Ns (site-major: r * 16 + c)
+    R* onrow;             // kQTri * 2 * 16
+    R* part;              // NG * Ns * 16: per node-group partial sums of the site-local products
+    R* lat;               // Ns * 16: lattice-sum integrals
 };
 
-__host__ __device__ inline size_t tri_smem_bytes(int Ns, int NG) {
+// Dynamic shared memory of k_gamma_rhs_tri<R> (rsz = sizeof(R)).
+__host__ __device__ inline size_t tri_smem_bytes(int Ns, int NG, size_t rsz) {
     auto rnd = [](size_t b) { return (b + 15) & ~size_t(15); };
-    return rnd(sizeof(Desc<double>) * kQTri * 4) + rnd(sizeof(int) * kQTri * 4) + rnd(sizeof(double) * kQTri * 2 * 16 * Ns) +
-           rnd(sizeof(double) * kQTri * 2 * 16) + rnd(sizeof(double) * (size_t)NG * Ns * 16) + rnd(sizeof(double) * Ns * 16);
+    return rnd(sizeof(Desc<double>) * kQTri * 4) + rnd(sizeof(int) * kQTri * 4) + rnd(rsz * kQTri * 2 * 16 * Ns) +
+           rnd(rsz * kQTri * 2 * 16) + rnd(rsz * (size_t)NG * Ns * 16) + rnd(rsz * Ns * 16);
 }
 
 __host__ __device__ inline int tri_groups(int Ns, int threads) {
@@ -144,23 +145,26 @@ __host__ __device__ inline int tri_groups(int Ns, int threads) {
     return ng < 1 ? 1 : (ng > kQTri ? kQTri : ng);
 }
 
-// dGamma/dLambda of every stored entry of one frequency triple (one CTA per triple).
+// dGamma/dLambda of every stored entry of one frequency triple (one CTA per triple).  R is
+// the type of the interpolated rows, the products and their node sums (double: FP64 flow;
+// float: FP32-mixed flow, lookups and output in FP64).
+template <typename R>
 __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, TabsT tt, const double* __restrict__ w,
                                                             const double* __restrict__ G, const double* __restrict__ nx,
                                                             const double* __restrict__ nW, const int* __restrict__ ncount,
                                                             double* __restrict__ dG) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int NG = tri_groups(g.Ns, blockDim.x);
-    ShT sh;
+    ShT<R> sh;
     {
         size_t off = 0;
         auto take = [&](size_t bytes) { unsigned char* q = smem + off; off += (bytes + 15) & ~size_t(15); return q; };
         sh.desc = (Desc<double>*)take(sizeof(Desc<double>) * kQTri * 4);
         sh.mneg = (int*)take(sizeof(int) * kQTri * 4);
-        sh.rows = (double*)take(sizeof(double) * kQTri * 2 * 16 * g.Ns);
-        sh.onrow = (double*)take(sizeof(double) * kQTri * 2 * 16);
-        sh.part = (double*)take(sizeof(double) * (size_t)NG * g.Ns * 16);
-        sh.lat = (double*)take(sizeof(double) * g.Ns * 16);
+        sh.rows = (R*)take(sizeof(R) * kQTri * 2 * 16 * g.Ns);
+        sh.onrow = (R*)take(sizeof(R) * kQTri * 2 * 16);
+        sh.part = (R*)take(sizeof(R) * (size_t)NG * g.Ns * 16);
+        sh.lat = (R*)take(sizeof(R) * g.Ns * 16);
     }
     const int tid = threadIdx.x;
     const int ti = blockIdx.x % g.N;
@@ -174,8 +178,8 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
     const int row = g.Ns * 16;
     const int nwork = g.Ns * NG;
 
-    for (int o = tid; o < NG * row; o += blockDim.x) sh.part[o] = 0.0;
-    for (int o = tid; o < row; o += blockDim.x) sh.lat[o] = 0.0;
+    for (int o = tid; o < NG * row; o += blockDim.x) sh.part[o] = R(0);
+    for (int o = tid; o < row; o += blockDim.x) sh.lat[o] = R(0);
 
     for (int ch = 0; ch < 3; ++ch) {
         const int vi = ch == 0 ? si : (ch == 1 ? ti : ui);
@@ -208,47 +212,50 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
                 const int q = idx / (2 * row), rem = idx % (2 * row);
                 const int rw = rem / row, e = rem % row;
                 const int r = e >> 4, c = e & 15;
-                sh.rows[(q * 2 + rw) * row + e] = tri_value(G, sh.desc[q * 4 + rw], sh.mneg[q * 4 + rw] != 0, tb, tt, g, r, c);
+                sh.rows[(q * 2 + rw) * row + e] = (R)tri_value(G, sh.desc[q * 4 + rw], sh.mneg[q * 4 + rw] != 0, tb, tt, g, r, c);
             }
             if (ch == 1)
                 for (int j = tid; j < qn * 2 * 16; j += blockDim.x) {
                     const int q = j / 32, rr = (j / 16) % 2, c = j % 16;
                     sh.onrow[(q * 2 + rr) * 16 + c] =
-                        tri_value(G, sh.desc[q * 4 + 2 + rr], sh.mneg[q * 4 + 2 + rr] != 0, tb, tt, g, 0, c);
+                        (R)tri_value(G, sh.desc[q * 4 + 2 + rr], sh.mneg[q * 4 + 2 + rr] != 0, tb, tt, g, 0, c);
                 }
             __syncthreads();
             // site-local products: work item (site r, node group gq) owns part[gq][r]
             for (int wk = tid; wk < nwork; wk += blockDim.x) {
                 const int r = wk % g.Ns, gq = wk / g.Ns;
-                double o[16];
+                R o[16];
 #pragma unroll
-                for (int k = 0; k < 16; ++k) o[k] = 0.0;
+                for (int k = 0; k < 16; ++k) o[k] = R(0);
                 for (int q = gq; q < qn; q += NG) {
-                    const double* A = sh.rows + (q * 2) * row + r * 16;
-                    const double* B = A + row;
-                    if (ch == 0) tri_su_acc<0>(A, B, o);
-                    else if (ch == 2) tri_su_acc<2>(A, B, o);
+                    const R* A = sh.rows + (q * 2) * row + r * 16;
+                    const R* B = A + row;
+                    if (ch == 0) tri_su_acc<0, R>(A, B, o);
+                    else if (ch == 2) tri_su_acc<2, R>(A, B, o);
                     else {
-                        double Cp[16];
-                        const double* C0 = sh.onrow + (q * 2) * 16;
+                        R Cp[16];
+                        const R* C0 = sh.onrow + (q * 2) * 16;
 #pragma unroll
-                        for (int k = 0; k < 16; ++k) Cp[k] = tri_mapped(C0, tt.onsite_map[r * 16 + k]);
-                        tri_onsite_acc(A, B, Cp, sh.onrow + (q * 2 + 1) * 16, o);
+                        for (int k = 0; k < 16; ++k) {
+                            const int mk = tt.onsite_map[r * 16 + k];
+                            Cp[k] = (mk & 16) ? -C0[mk & 15] : C0[mk & 15];
+                        }
+                        tri_onsite_acc<R>(A, B, Cp, sh.onrow + (q * 2 + 1) * 16, o);
                     }
                 }
-                double* P = sh.part + (size_t)gq * row + r * 16;
+                R* P = sh.part + (size_t)gq * row + r * 16;
 #pragma unroll
                 for (int k = 0; k < 16; ++k) P[k] += o[k];
             }
             // lattice sum: every output (site, component) integrates its signed products
             if (ch == 1)
                 for (int o = tid; o < row; o += blockDim.x) {
-                    double acc = 0.0;
+                    R acc = R(0);
                     for (int k = tt.lat_off[o]; k < tt.lat_off[o + 1]; ++k) {
                         const int2 en = tt.lat_ent[k];
                         const int ib = en.y < 0 ? ~en.y : en.y;
-                        double a = 0.0;
-                        for (int q = 0; q < qn; ++q) a = fma(sh.rows[(q * 2) * row + en.x], sh.rows[(q * 2 + 1) * row + ib], a);
+                        R a = R(0);
+                        for (int q = 0; q < qn; ++q) a = fmadd(sh.rows[(q * 2) * row + en.x], sh.rows[(q * 2 + 1) * row + ib], a);
                         acc += en.y < 0 ? -a : a;
                     }
                     sh.lat[o] += acc;
@@ -257,10 +264,10 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
     }
     __syncthreads();
     for (int o = tid; o < row; o += blockDim.x) {
-        double a = 0.0;
+        R a = R(0);
         for (int k = 0; k < NG; ++k) a += sh.part[(size_t)k * row + o];
         const int r = o >> 4, c = o & 15;
-        dG[((size_t)(p * g.N + ti) * 16 + c) * g.Ns + r] = a - 2.0 * sh.lat[o];
+        dG[((size_t)(p * g.N + ti) * 16 + c) * g.Ns + r] = (double)a - 2.0 * (double)sh.lat[o];
     }
 }
 
