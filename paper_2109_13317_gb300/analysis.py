@@ -92,6 +92,8 @@ def onsite_correlation(flow: Flow) -> float:
     c = chi_ij.cpu().numpy()
     if c.shape[2] == 2:
         return float(c[:, 0, 1].mean())            # SU2: component 1 is the spin part
+    if c.shape[2] == 16:
+        return float(c[:, 0, 15].mean())           # TRI: mu nu = zz
     return float(c[:, 0, 3].mean())                # XYZ: zz
 
 

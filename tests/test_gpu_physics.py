@@ -6,7 +6,9 @@ paper reads its critical cutoffs off plotted flows (cubic J1-J2: 0.72 at J2 = 0,
 J2 = 0.5; kagome ferromagnet about 0.35; kagome antiferromagnet smooth), so these checks are
 loose: the breakdown criterion of `analysis.flow_breakdown` (a significant peak of the
 structure-factor maximum), the ordering momenta, and for J2 = 0.5 (a breakdown the paper calls
-less pronounced, a kink) the end of the steep growth.
+less pronounced, a kink) the end of the steep growth.  The kagome DM example (TRI core) runs
+with 32 frequencies: D = 0.5 breaks down near 0.39, D = 0 flows smoothly, and the on-site
+correlation converges in the range for D = 0.1 but not for D = 0.5.
 """
 import math
 
@@ -107,3 +109,38 @@ def test_onsite_correlation_range_scaling():
     lam, sp = range_spread(_onsite_records(W.cubic_j1j2(1.0, 0.0)))
     assert sp[lam >= 1.0].max() < 0.01
     assert sp[(lam > 0.5) & (lam < 0.7)].max() > 0.1
+
+
+def _dm_flow(D, n_freq=32):
+    lat = sr.Lattice.from_model(W.kagome_dm(1.0, D), 7)
+    mesh = sr.sr_frequency_mesh_exponential(n_freq, 0.005, 50.0)
+    lams = W.lambda_geometric(50.0, 0.01, 0.98)
+    fl = sr.Flow(lat, mesh, lams[0], sr.SR_FP32_MIXED)
+    rec = run_susceptibility_flow(fl, lams, _kgrid_plane())
+    fl.close()
+    return rec
+
+
+def test_kagome_dm_breakdown_and_smooth_heisenberg_limit():
+    """The paper's second worked example (TRI core): the kagome antiferromagnet with out-of-plane
+    DM couplings D = 0.5 breaks down at Lambda_c = 0.39 (range 7, 64 frequencies) with the
+    structure-factor maximum on the boundary of the extended Brillouin zone, while D = 0 flows
+    smoothly.  Here 32 frequencies, so the window is loose."""
+    rec = _dm_flow(0.5)
+    lc = flow_breakdown(rec.lambdas, rec.chi_max)
+    assert lc is not None and 0.3 < lc < 0.45, lc
+    assert abs(np.linalg.norm(rec.k_max[_at(rec, lc)]) - 2 * PI) < 0.05
+    rec0 = _dm_flow(0.0)
+    assert rec0.lambdas[-1] < 0.0102
+    assert flow_breakdown(rec0.lambdas, rec0.chi_max) is None
+
+
+def test_kagome_dm_onsite_range_scaling():
+    """The paper's range-scaling diagnostic for the DM model (Sec. 6.2): chi_ii at L = 3, 5, 7
+    stays converged for D = 0.1, while for D = 0.5 the ranges separate below the breakdown."""
+    from paper_2109_13317_gb300.analysis import range_spread
+    lam, sp = range_spread(_onsite_records(W.kagome_dm(1.0, 0.1)))
+    assert sp[lam >= 0.01].max() < 0.012, sp.max()
+    lam, sp = range_spread(_onsite_records(W.kagome_dm(1.0, 0.5)))
+    assert sp[lam >= 1.0].max() < 1e-4
+    assert sp[(lam > 0.1) & (lam < 0.3)].min() > 0.01
