@@ -50,7 +50,7 @@ def _args():
     ap.add_argument("--no-flow", action="store_true", help="skip the full adaptive Lambda flow")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched coupling sweep")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=["square_j1j2_L7", "square_j1_L3", "pyrochlore_L6", "honeycomb_hk_L5"],
+                    choices=["square_j1j2_L7", "square_j1_L3", "pyrochlore_L6", "honeycomb_hk_L5", "kagome_dm_L7"],
                     help="configuration to measure (the default is the headline workload)")
     return ap.parse_args()
 
@@ -63,11 +63,14 @@ def _describe(cfg):
 
 
 def _oracle_fits(cfg, limit_bytes: float = 1e9) -> bool:
-    """Whether the oracle's translation-only vertex of the configuration stays below limit_bytes."""
+    """Whether the oracle's translation-only vertex of the configuration stays below limit_bytes
+    (the TRI oracle keeps 16 complex functions: 4 GB)."""
     from oracle import oracle as O
-    of = O.OracleFlow(cfg.model, cfg.L, O.mesh_exponential(2, cfg.w_min, cfg.w_max))
+    tri = cfg.model.backend == "TRI"
+    of = (O.OracleFlowTRI if tri else O.OracleFlow)(cfg.model, cfg.L, O.mesh_exponential(2, cfg.w_min, cfg.w_max))
     n = cfg.n_freq
-    return 8.0 * sum(of.nsite) * 4 * n * n * (n + 1) / 2 <= limit_bytes
+    per = 16 * 16 if tri else 8 * 4
+    return per * sum(of.nsite) * n * n * (n + 1) / 2 <= (4 * limit_bytes if tri else limit_bytes)
 
 
 class ClockSampler:
@@ -165,10 +168,13 @@ def _algorithmic_flops(counts: np.ndarray, N: int, Ns: int, nc: int, P: int, npr
     site: A1 B1, its multiples and three FMAs plus two accumulations; XYZ 32).  t channel: two
     rows, two on-site rows (n_c values each), the on-site terms (SU2 6 flop per site and
     component, XYZ 7) and the lattice sum as one FMA (2 flop) per distinct product of table
-    rows.  Per triple, the lattice sum's table gather adds P n_c flop."""
+    rows.  Per triple, the lattice sum's table gather adds P n_c flop.  TRI (n_c = 16): the
+    s / u products are 256 FMA per site (512 flop), the two on-site terms 1024 flop per site
+    (64 per value), and the lattice sum 64 FMA per table entry (nprod = 64 P), summed in
+    place."""
     row = Ns * nc
-    prod = 11 if nc == 2 else 32
-    onsite = 6 if nc == 2 else 7
+    prod = {2: 11, 4: 32, 16: 512}[nc]
+    onsite = {2: 6, 4: 7, 16: 64}[nc]
     per_s = 2 * row * 8 + row + Ns * prod
     per_u = per_s
     per_t = (2 * row + 2 * nc) * 8 + row + nc + 2 * nprod + onsite * row
@@ -177,7 +183,8 @@ def _algorithmic_flops(counts: np.ndarray, N: int, Ns: int, nc: int, P: int, npr
     tot = N * float(np.sum(ns * cs)) * per_s                   # s channel: node count depends on s_i
     tot += (N * (N + 1) / 2) * float(np.sum(nt)) * per_t       # t channel: on t_i
     tot += N * float(np.sum(nu * (N - np.arange(N)))) * per_u  # u channel: on u_i
-    tot += (N * N * (N + 1) / 2) * P * nc                      # lattice-sum gather per triple
+    if nc != 16:                                               # (the TRI kernel sums in place)
+        tot += (N * N * (N + 1) / 2) * P * nc                  # lattice-sum gather per triple
     return tot
 
 
@@ -216,19 +223,38 @@ def _kgrid(n=64):
     return np.stack([kx.ravel(), ky.ravel(), np.zeros(n * n)], axis=1)
 
 
-def _cpu_baseline(cfg, target_s: float = 12.0):
-    """The oracle as it stands, on the host's cores, on a bounded random sample of stored
-    entries of the same workload (synthetic symmetric state at Lambda = 0.9)."""
+def _oracle_sampler(cfg, seed: int):
+    """The oracle on the workload and a function timing its right-hand side on m random stored
+    entries: returns (run(m) -> (entries, seconds), description of the state).  SU2 / XYZ:
+    synthetic symmetric state at Lambda = 0.9, one stored entry per call of the oracle.  TRI:
+    the initial vertex J/4 with a synthetic self-energy (the work per entry does not depend on
+    the values), all 16 functions of a site pair and frequency triple per call."""
     from oracle import oracle as O
-    from tests.helpers import synthetic_state
     mesh = O.mesh_exponential(cfg.n_freq, cfg.w_min, cfg.w_max)
+    rng = np.random.default_rng(seed)
+    N = cfg.n_freq
+    if cfg.model.backend == "TRI":
+        of = O.OracleFlowTRI(cfg.model, cfg.L, mesh)
+        gam = 0.2 * np.tanh(mesh) + 0.05 * mesh / (1 + mesh)
+        _, G = of.get_state()
+        of.set_state(gam, G)
+
+        def run(m):
+            ent = []
+            for _ in range(m):
+                si = int(rng.integers(0, N))
+                ent.append((0, int(rng.integers(0, of.nsite[0])), si, int(rng.integers(0, N)), int(rng.integers(0, si + 1))))
+            ent = np.array(ent, dtype=np.int32)
+            t0 = time.perf_counter()
+            of.rhs_entries(0.9, ent)
+            return 16 * m, time.perf_counter() - t0
+        return run, "initial vertex J/4 with a synthetic self-energy at Lambda=0.9 (16 functions per sampled pair and triple)"
+    from tests.helpers import synthetic_state
     of = O.OracleFlow(cfg.model, cfg.L, mesh)
     gam, G = synthetic_state(of, cfg.model, seed=3)
     of.set_state(gam, G)
-    rng = np.random.default_rng(5)
-    N = cfg.n_freq
 
-    def sample(m):
+    def run(m):
         ent = []
         for _ in range(m):
             si = int(rng.integers(0, N))
@@ -236,22 +262,28 @@ def _cpu_baseline(cfg, target_s: float = 12.0):
             ti = int(rng.integers(0, N))
             k = int(rng.integers(0, of.nsite[0]))
             ent.append((0, k, si, ti, ui))
-        return np.array(ent, dtype=np.int32)
-    of.rhs_entries(0.9, sample(8))
-    t0 = time.perf_counter()
-    n0 = 64
-    of.rhs_entries(0.9, sample(n0))
-    dt = time.perf_counter() - t0
+        ent = np.array(ent, dtype=np.int32)
+        t0 = time.perf_counter()
+        of.rhs_entries(0.9, ent)
+        return m, time.perf_counter() - t0
+    return run, "synthetic symmetric state at Lambda=0.9"
+
+
+def _cpu_baseline(cfg, target_s: float = 12.0):
+    """The oracle as it stands, on the host's cores, on a bounded random sample of stored
+    entries of the same workload."""
+    from oracle import oracle as O
+    run, state = _oracle_sampler(cfg, 5)
+    run(4)
+    n0 = 32
+    e0, dt = run(n0)
     m = max(n0, int(n0 * target_s / max(dt, 1e-3)))
-    ent = sample(m)
-    t0 = time.perf_counter()
-    of.rhs_entries(0.9, ent)
-    dt = time.perf_counter() - t0
+    e, dt = run(m)
     # the oracle evaluates every symmetry-equivalent pair; a stored entry of the oracle's
     # translation-only vertex is one equation, as for the GPU's reduced vertex
-    return {"value": m / dt, "unit": UNIT, "cores": O.OracleFlow.threads(), "kind": "oracle",
-            "sample": f"{m} random stored vertex entries (RHS of each, incl. self-energy flow) of the "
-                      f"{cfg.name} workload at Lambda=0.9 on a synthetic symmetric state; {dt:.1f} s"}
+    return {"value": e / dt, "unit": UNIT, "cores": O.OracleFlow.threads(), "kind": "oracle",
+            "sample": f"{e} random stored vertex entries (RHS of each, incl. self-energy flow) of the "
+                      f"{cfg.name} workload, {state}; {dt:.1f} s"}
 
 
 def run_reference(args):
@@ -260,40 +292,25 @@ def run_reference(args):
         return
     cfg = W.config(args.workload)
     from oracle import oracle as O
-    from tests.helpers import synthetic_state
     if args.workload != WORKLOAD and not _oracle_fits(cfg):
         print(json.dumps({"impl": "reference", "unavailable": f"the oracle's unreduced vertex of {cfg.name} exceeds 1 GB"}))
         return
-    mesh = O.mesh_exponential(cfg.n_freq, cfg.w_min, cfg.w_max)
-    of = O.OracleFlow(cfg.model, cfg.L, mesh)
-    gam, G = synthetic_state(of, cfg.model, seed=3)
-    of.set_state(gam, G)
-    rng = np.random.default_rng(7)
-    N = cfg.n_freq
-    m = 256
-
-    def sample():
-        ent = []
-        for _ in range(m):
-            si = int(rng.integers(0, N))
-            ent.append((0, int(rng.integers(0, of.nsite[0])), si, int(rng.integers(0, N)), int(rng.integers(0, si + 1))))
-        return np.array(ent, dtype=np.int32)
+    run, state = _oracle_sampler(cfg, 7)
+    m = 256 if cfg.model.backend != "TRI" else 64
     for _ in range(args.warmup):
-        of.rhs_entries(0.9, sample())
-    times = []
+        run(m)
+    tot, ent = 0.0, 0
     for _ in range(args.steps):
-        e = sample()
-        t0 = time.perf_counter()
-        of.rhs_entries(0.9, e)
-        times.append(time.perf_counter() - t0)
-    tot = sum(times)
-    val = m * args.steps / tot
+        e, dt = run(m)
+        tot += dt
+        ent += e
+    val = ent / tot
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": cfg.name, "sample_entries_per_step": m, "lambda": 0.9},
+            "data": "synthetic", "config": {"workload": cfg.name, "sample_entries_per_step": ent // args.steps, "lambda": 0.9},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": O.OracleFlow.threads(), "kind": "oracle",
-                             "sample": f"{m} random stored entries per step of {cfg.name} at Lambda=0.9"},
+                             "sample": f"{ent // args.steps} random stored entries per step of {cfg.name}, {state}"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -661,13 +678,14 @@ def run_ours(args):
                        "lambda_range_timed": [float(lam_rng[0]), float(lam_rng[1])],
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-            "roofline": {"bound": "alu", "kernel": "k_gamma_rhs", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "alu", "kernel": "k_gamma_rhs_tri" if fl.n_comp == 16 else "k_gamma_rhs",
+                         "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak,
                          "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe table)" if prec == sr.SR_FP64 else
                          "FP32 from unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz",
                          "peak_measured_fma": measured_peak, "frac_of_measured_fma": achieved / measured_peak,
                          "algorithmic_flop_per_launch": flops, "launch_ms": k_ms,
-                         "traffic": _traffic(args.precision)},
+                         "traffic": _traffic(args.precision) if headline else None},
             "kernels_ms_per_step": {"sigma_rhs": kms[0] / max(kn[0], 1), "channel_nodes": kms[1] / max(kn[1], 1),
                                     "gamma_rhs": k_ms},
             "clocks": clocks,

@@ -104,6 +104,7 @@ def load():
         lib.or_tri_rhs_prepare.argtypes = [vp, C.c_double, _dp]
         lib.or_tri_rhs_point.argtypes = [vp, C.c_int, _ip, C.c_int, C.c_double, C.c_double, C.c_double, _dp]
         lib.or_tri_euler_step.argtypes = [vp, C.c_double, C.c_double]
+        lib.or_tri_rhs_entries.argtypes = [vp, C.c_int, _ip, _dp]
         lib.or_tri_chi.argtypes = [vp, C.c_double, _dp]
         _lib = lib
         return lib
@@ -385,8 +386,14 @@ class OracleFlowTRI(OracleFlow):
         self.lib.or_tri_rhs(self.st, lam, dg, dG)
         return dg, dG[0::2] + 1j * dG[1::2]
 
-    def rhs_entries(self, lam, ent):  # pragma: no cover - not provided by the TRI core
-        raise NotImplementedError
+    def rhs_entries(self, lam: float, ent: np.ndarray) -> np.ndarray:
+        """All 16 functions of selected (b, k, si, ti, ui) entries: complex (n, 16)."""
+        self.prepare(lam)
+        ent = np.ascontiguousarray(ent, dtype=np.int32).reshape(-1, 5)
+        out = np.zeros(ent.shape[0] * 32)
+        self.lib.or_tri_rhs_entries(self.st, ent.shape[0], ent.reshape(-1), out)
+        out = out.reshape(-1, 32)
+        return out[:, 0::2] + 1j * out[:, 1::2]
 
     def prepare(self, lam: float) -> np.ndarray:
         dg = np.zeros(self.N)

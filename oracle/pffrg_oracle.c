@@ -1262,6 +1262,24 @@ void or_tri_rhs_point(const OrStateT* st, int b1, const int* d, int b2, double s
     gamma_rhs_atT(st, b1, d, b2, s, t, u, xs, Ws, (cx*)out32);
 }
 
+/* Right-hand side of selected stored entries only (after or_tri_rhs_prepare):
+ * ent = n x (b, k, si, ti, ui); out = n x 16 complex (interleaved). */
+void or_tri_rhs_entries(const OrStateT* st, int n, const int* ent, double* out) {
+    const int N = st->f.N;
+    #pragma omp parallel
+    {
+        double* xs = (double*)malloc(sizeof(double) * (2 * N + 16));
+        double* Ws = (double*)malloc(sizeof(double) * (2 * N + 16));
+        #pragma omp for schedule(dynamic, 1)
+        for (int e = 0; e < n; ++e) {
+            const int* q = ent + 5 * e;
+            Site j = st->f.la->sites[q[0]][q[1]];
+            gamma_rhs_atT(st, q[0], j.n, j.b, st->f.w[q[2]], st->f.w[q[3]], st->f.w[q[4]], xs, Ws, (cx*)(out + 32 * (size_t)e));
+        }
+        free(xs); free(Ws);
+    }
+}
+
 /* Euler step (Sec. 4.3). */
 void or_tri_euler_step(OrStateT* st, double lam, double lam_next) {
     double dl = lam - lam_next;

@@ -264,3 +264,15 @@ def test_tri_flow_symmetry_relations(dm_flow):
         np.testing.assert_allclose(f.rhs_point(b2, -d, 0, -s, t, u)[tr], ref, **tol)
         np.testing.assert_allclose(f.rhs_point(b2, -d, 0, s, t, -u)[tr] * xx, ref, **tol)
         np.testing.assert_allclose(f.rhs_point(0, d, b2, u, t, s) * -np.tile(xi, 4), ref, **tol)
+
+
+def test_tri_rhs_entries_match_full_rhs(dm_flow):
+    """The sampled-entry evaluation (used for timing samples) equals the full right-hand side."""
+    f = dm_flow
+    dg, dG = f.rhs(1.9)
+    ent = np.array([[0, 1, 3, 2, 1], [1, 4, 5, 0, 5], [2, 0, 2, 4, 0]], dtype=np.int32)
+    got = f.rhs_entries(1.9, ent)
+    pairs = [(s, u) for s in range(f.N) for u in range(s + 1)]
+    for e, g in zip(ent, got):
+        b, k, si, ti, ui = (int(x) for x in e)
+        np.testing.assert_allclose(g, f.block(dG, b)[k, :, pairs.index((si, ui)), ti], rtol=0, atol=1e-15)

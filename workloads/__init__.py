@@ -214,6 +214,10 @@ def config(name: str) -> FlowConfig:
         return FlowConfig(name, cubic_j1j2(1.0, 0.0), 7, 64, 0.005, 50.0, 50.0, 0.01, 422)
     if name == "honeycomb_hk_L5":
         return FlowConfig(name, honeycomb_kitaev(0.2, -1.0), 5, 32, 0.005, 50.0, 50.0, 0.05, 200)
+    if name == "kagome_dm_L7":
+        # the paper's second worked example (TRI core) at D = 0.5, range 7, with 32 of its 64
+        # frequencies; 200 log steps from 50 to 0.01
+        return FlowConfig(name, kagome_dm(1.0, 0.5), 7, 32, 0.005, 50.0, 50.0, 0.01, 200)
     raise KeyError(name)
 
 
