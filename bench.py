@@ -427,9 +427,10 @@ def _batched_sweep(sr, torch, steps=20):
     """The batched coupling sweep: 64 seeded instances (square J1-J2 with J2/J1 ~ U[0,1] and
     range 5..9, kagome J1 with range 4..8, 32..64 frequencies), FP32-mixed, Euler steps on a
     common log cutoff list 50 -> 0.05 (100 steps).  The flows are advanced untimed to mid-flow
-    by the batch itself, then `steps` Euler steps are timed (a) batched: one persistent vertex
-    launch per step for all instances, CUDA-graph-captured loop, autotuned launch shape, and
-    (b) one flow after another with sr_flow_step, from the same saved states."""
+    by the batch itself, then `steps` Euler steps are timed (a) batched: all instances per step
+    in one CUDA graph (replays timed, capture excluded), per size class the autotuner's choice of
+    a persistent vertex kernel or the instances' own kernels, and (b) one flow after another with
+    sr_flow_step, from the same saved states."""
     insts = W.batched_instances(0)
     lams = W.lambda_list(50.0, 0.05, 100)
     flows = []
@@ -446,6 +447,8 @@ def _batched_sweep(sr, torch, steps=20):
     b.run(window, use_graph=True, autotune=True)
     info = b.info()
     classes = b.classes()
+    for c, per in zip(classes, b.class_launches()):
+        c["launch"] = "per-instance kernels" if per else "persistent kernel"
     parallel = b.parallel_classes
     batched_ms = info["run_ms"]
     after_b = [f.get_state()[1] for f in flows]

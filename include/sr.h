@@ -286,6 +286,16 @@ sr_status sr_batch_class(const sr_batch* batch, int k, int* n_instances, long* u
  * the autotuner times both and keeps the faster (parallel without autotuning). */
 sr_status sr_batch_parallel_classes(const sr_batch* batch, int* parallel);
 
+/* Launch form of the classes' vertex flow: mode 0 (default) lets the autotuner compare, per
+ * class, the persistent kernel with the instances' own vertex kernels launched back to back
+ * (as single flows launch them, here inside the batch's graph) and keep the faster; 1 forces
+ * the persistent kernels, 2 the per-instance kernels.  Takes effect at the next sr_batch_run
+ * (with autotune != 0 for mode 0).  Errors: SR_EINVAL (mode outside 0..2). */
+sr_status sr_batch_force_launch(sr_batch* batch, int mode);
+
+/* 1 if class k runs its instances' own kernels, 0 if its persistent kernel (host out). */
+sr_status sr_batch_class_launch(const sr_batch* batch, int k, int* per_instance);
+
 sr_status sr_batch_destroy(sr_batch* batch);
 
 /* ---- measurement helpers (not part of the method) ---- */

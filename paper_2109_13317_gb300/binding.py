@@ -107,6 +107,8 @@ def load_library():
             "sr_batch_classes": [vp, ip],
             "sr_batch_class": [vp, i, ip, lp, ip, ip, ip, dp],
             "sr_batch_parallel_classes": [vp, ip],
+            "sr_batch_force_launch": [vp, i],
+            "sr_batch_class_launch": [vp, i, ip],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -476,6 +478,21 @@ class Batch:
         v = C.c_int()
         _check(self._lib.sr_batch_parallel_classes(self.h, C.byref(v)))
         return bool(v.value)
+
+    def force_launch(self, mode: int):
+        """0: autotuned launch form per class, 1: persistent kernels, 2: per-instance kernels."""
+        _check(self._lib.sr_batch_force_launch(self.h, int(mode)))
+
+    def class_launches(self):
+        """Per class: True if it runs its instances' own kernels, False if its persistent kernel."""
+        n = C.c_int()
+        _check(self._lib.sr_batch_classes(self.h, C.byref(n)))
+        out = []
+        for k in range(n.value):
+            v = C.c_int()
+            _check(self._lib.sr_batch_class_launch(self.h, k, C.byref(v)))
+            out.append(bool(v.value))
+        return out
 
     def close(self):
         if getattr(self, "h", None):

@@ -2493,6 +2493,8 @@ struct BClass {
     size_t smem;
     int occ, ctas, qc;
     double ms;            // autotuned vertex-flow time of the class
+    bool per_inst;        // the instances' own vertex kernels, one launch each, instead of the
+                          // class's persistent kernel
 };
 
 struct sr_batch {
@@ -2515,6 +2517,9 @@ struct sr_batch {
     std::vector<cudaEvent_t> join;
     cudaEvent_t fork = nullptr;
     bool parallel = true;             // size classes as parallel branches (else one after another)
+    int force = 0;                    // 0: the autotuner picks the launch form per class,
+                                      // 1: persistent kernels, 2: per-instance kernels
+    std::vector<size_t> inst_smem;    // per instance: dynamic shared memory of its own kernel
     ~sr_batch() {
         for (cudaStream_t s : side) cudaStreamDestroy(s);
         for (cudaEvent_t e : join) cudaEventDestroy(e);
@@ -2525,6 +2530,21 @@ struct sr_batch {
 
 static void launch_class(sr_batch* b, int k, cudaStream_t st) {
     const BClass& c = b->cls[k];
+    if (c.per_inst) {
+        // the instances' own vertex kernels (as a single flow launches them), back to back
+        for (int i = c.i_begin; i < c.i_end; ++i) {
+            const BInst& B = b->inst[i];
+            const unsigned blocks = (unsigned)(B.g.npair * B.g.N);
+            const size_t sm = b->inst_smem[i];
+            if (c.kind == 0)
+                k_gamma_rhs_f32<2, true><<<blocks, kThreads, sm, st>>>(B.g, B.tb, B.Gf, B.Gs, B.nxf, B.nWf, B.ncount, B.dG);
+            else if (c.kind == 1)
+                k_gamma_rhs_f32<2, false><<<blocks, kThreads, sm, st>>>(B.g, B.tb, B.Gf, B.Gs, B.nxf, B.nWf, B.ncount, B.dG);
+            else
+                k_gamma_rhs_f32<4, false><<<blocks, kThreads, sm, st>>>(B.g, B.tb, B.Gf, B.Gs, B.nxf, B.nWf, B.ncount, B.dG);
+        }
+        return;
+    }
     const dim3 grid(b->nsm * c.ctas);
     unsigned long long* ctr = b->counter.p + k;
     if (c.kind == 0)
@@ -2599,12 +2619,22 @@ static sr_status batch_time_class(sr_batch* b, int k, double* ms) {
 }
 
 // Autotuner: per size class, the node-block size and the CTAs per SM of its persistent
-// kernel, each candidate timed on the current state and node tables; the fastest is kept.
+// kernel, each candidate timed on the current state and node tables, against the instances'
+// own kernels launched one after another; the fastest is kept.
 static sr_status batch_tune(sr_batch* b) {
     const int qcs[3] = {8, 16, 32};
     double total = 0.0;
     for (int k = 0; k < (int)b->cls.size(); ++k) {
         BClass& c = b->cls[k];
+        c.per_inst = false;
+        if (b->force == 2) {
+            c.per_inst = true;
+            double ms = 0;
+            if (sr_status s = batch_time_class(b, k, &ms)) return s;
+            c.ms = ms;
+            total += ms;
+            continue;
+        }
         std::vector<int> ctas_c;
         for (int v = c.occ; v >= 1; v = v / 2) { ctas_c.push_back(v); if (v == 1) break; }
         double best = 1e300;
@@ -2622,7 +2652,14 @@ static sr_status batch_tune(sr_batch* b) {
         c.ctas = bc;
         c.qc = bq;
         c.ms = best;
-        total += best;
+        if (b->force == 0) {
+            c.per_inst = true;
+            double ms = 0;
+            if (sr_status s = batch_time_class(b, k, &ms)) return s;
+            if (ms < best) c.ms = ms;
+            else c.per_inst = false;
+        }
+        total += c.ms;
     }
     b->tune_ms = total;
     b->qc = b->cls.empty() ? kQF : b->cls[0].qc;
@@ -2720,6 +2757,7 @@ extern "C" sr_status sr_batch_create(int n, sr_flow* const* flows, sr_batch** ou
         B.with_swap = f->has_swap ? 1 : 0;
         unit += (long)f->g.npair * f->g.N;
         b->inst.push_back(B);
+        b->inst_smem.push_back(f->smem_rhs);
         b->cls.back().i_end = idx + 1;
         b->cls.back().u_end = unit;
     }
@@ -2777,7 +2815,6 @@ extern "C" sr_status sr_batch_run(sr_batch* b, int n_lambda, const double* lambd
         CK(cudaGetLastError());
         if (sr_status s = batch_tune(b)) return s;
     }
-    CK(cudaEventRecord(e0, b->stream));
     if (use_graph) {
         cudaGraph_t graph;
         cudaGraphExec_t exec;
@@ -2787,11 +2824,14 @@ extern "C" sr_status sr_batch_run(sr_batch* b, int n_lambda, const double* lambd
         if (s != SR_OK) return s;
         if (ce != cudaSuccess) return fail(SR_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
         CK(cudaGraphInstantiate(&exec, graph, 0));
+        CK(cudaGraphUpload(exec, b->stream));
+        CK(cudaEventRecord(e0, b->stream));   // run time: the replays, not the capture
         for (; done < nsteps; ++done) CK(cudaGraphLaunch(exec, b->stream));
         CK(cudaStreamSynchronize(b->stream));
         cudaGraphExecDestroy(exec);
         cudaGraphDestroy(graph);
     } else {
+        CK(cudaEventRecord(e0, b->stream));
         for (; done < nsteps; ++done)
             if (sr_status s = batch_launch_step(b)) return s;
     }
@@ -2821,6 +2861,20 @@ extern "C" sr_status sr_batch_info(const sr_batch* b, int* qc, int* ctas_per_sm,
     if (tune_ms) *tune_ms = b->tune_ms;
     if (run_ms) *run_ms = b->run_ms;
     if (units) *units = b->total;
+    return SR_OK;
+}
+
+extern "C" sr_status sr_batch_force_launch(sr_batch* b, int mode) {
+    if (!b || mode < 0 || mode > 2) return fail(SR_EINVAL, "mode must be 0 (autotune), 1 (persistent) or 2 (per instance)");
+    b->force = mode;
+    if (mode != 0)
+        for (BClass& c : b->cls) c.per_inst = mode == 2;
+    return SR_OK;
+}
+
+extern "C" sr_status sr_batch_class_launch(const sr_batch* b, int k, int* per_instance) {
+    if (!b || !per_instance || k < 0 || k >= (int)b->cls.size()) return fail(SR_EINVAL, "bad class index");
+    *per_instance = b->cls[k].per_inst ? 1 : 0;
     return SR_OK;
 }
 

@@ -21,8 +21,10 @@ MODELS = [(W.square_j1j2(1.0, 0.3), 2, O.mesh_exponential(7, 0.02, 20.0)),
           (W.honeycomb_kitaev(0.2, -1.0), 1, O.mesh_exponential(5, 0.05, 10.0))]
 
 
-@pytest.mark.parametrize("use_graph,autotune", [(True, True), (False, False)])
-def test_batch_matches_individual_flows(use_graph, autotune):
+@pytest.mark.parametrize("use_graph,autotune,mode", [(True, True, 0), (False, False, 0), (True, True, 1), (True, False, 2)])
+def test_batch_matches_individual_flows(use_graph, autotune, mode):
+    """Every launch form (autotuned, persistent kernels, the instances' own kernels) against the
+    same flows stepped one by one."""
     lams = W.lambda_list(8.0, 0.5, 10)
     single, batched = [], []
     for model, L, mesh in MODELS:
@@ -33,7 +35,12 @@ def test_batch_matches_individual_flows(use_graph, autotune):
         for lam in lams[1:]:
             fl.step(lam, sr.SR_EULER)
     b = sr.Batch([fl for _, fl in batched])
+    b.force_launch(mode)
     b.run(lams, use_graph=use_graph, autotune=autotune)
+    if mode == 1:
+        assert not any(b.class_launches())
+    if mode == 2:
+        assert all(b.class_launches())
     info = b.info()
     assert info["units"] == sum(fl.npair * fl.N for _, fl in batched)
     for (lat, f1), (_, f2) in zip(single, batched):
