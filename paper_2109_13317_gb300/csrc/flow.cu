@@ -1437,8 +1437,11 @@ struct sr_flow {
     DevBuf<int> pinv_off, pinv_out, ainv_off, ainv_idx, binv_off, binv_idx;
     DevBuf<double> ntw, Wbar, dgbar, tg, tG, chibar, kbar;
     // TRI core tables (nc = 16)
-    DevBuf<int> swap_map16, onsite_map16, tlat_off, chi_r16, chi_m16;
+    DevBuf<int> swap_map16, onsite_map16, tlat_item_off, tlat_off, chi_r16, chi_m16;
     DevBuf<int2> tlat_ent;
+    DevBuf<uint4> tlat_rec;
+    DevBuf<int4> tlat_items;
+    int tlat_n_items = 0;
 
     Tabs tabs() const {
         Tabs t;
@@ -1449,7 +1452,8 @@ struct sr_flow {
     }
     TabsT tabs_tri() const {
         TabsT t;
-        t.swap_map = swap_map16.p; t.onsite_map = onsite_map16.p; t.lat_off = tlat_off.p; t.lat_ent = tlat_ent.p;
+        t.swap_map = swap_map16.p; t.onsite_map = onsite_map16.p; t.lat_rec = tlat_rec.p; t.lat_items = tlat_items.p;
+        t.lat_item_off = tlat_item_off.p; t.n_items = tlat_n_items; t.lat_off = tlat_off.p; t.lat_ent = tlat_ent.p;
         return t;
     }
 };
@@ -1801,44 +1805,75 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
         CK(f->chi.alloc(lat->chi_map.size() * g.nc * ts));
     }
     if (lat->nc == 16) {
-        // TRI core: component maps, lattice-sum entries per output (site, mu nu): for every
-        // table entry (rA, mA, rB, mB) of the site and every l, the product of row A component
-        // (mu, l) and row B component (l, nu) with the sign of both maps and of i^{iota}
+        // TRI core: component maps and the lattice-sum table: per entry (rA, mA, rB, mB) of an
+        // output site, the row indices and signs of A^{mu l} = (ref, j) and B^{l nu} = (j, i2);
+        // work items split every site's entries into chunks, at most one item per thread of a
+        // CTA when the table allows (items of a site are summed in a fixed order at the end)
         const int Ns = lat->Ns;
         std::vector<int> sm((size_t)Ns * 16), om((size_t)Ns * 16);
         for (int r = 0; r < Ns; ++r)
             for (int c = 0; c < 16; ++c) { sm[r * 16 + c] = lat->swap_map16[r][c]; om[r * 16 + c] = lat->onsite_map16[r][c]; }
-        std::vector<int> loff((size_t)Ns * 16 + 1, 0);
-        std::vector<int2> lent;
-        for (int r = 0; r < Ns; ++r)
-            for (int c = 0; c < 16; ++c) {
-                loff[r * 16 + c] = (int)lent.size();
-                const int mu = c / 4, nu = c % 4;
-                for (int e = lat->rpa_off[r]; e < lat->rpa_off[r + 1]; ++e) {
-                    const sr::RpaEntry16& en = lat->rpa16[e];
-                    for (int l = 0; l < 4; ++l) {
-                        const int ma = en.mA[mu * 4 + l], mb = en.mB[l * 4 + nu];
-                        int sg = sr::tri::coef_t(mu, nu, l);
-                        if (ma & 16) sg = -sg;
-                        if (mb & 16) sg = -sg;
-                        const int ia = en.rA * 16 + (ma & 15), ib = en.rB * 16 + (mb & 15);
-                        lent.push_back(make_int2(ia, sg > 0 ? ib : ~ib));
+        if (Ns * 16 > 0x7fff) return fail(SR_EUNSUPPORTED, "TRI lattice-sum table: too many irreducible sites (%d)", Ns);
+        const long P = (long)lat->rpa16.size();
+        std::vector<uint4> rec((size_t)P * 4);
+        for (long e = 0; e < P; ++e) {
+            const sr::RpaEntry16& en = lat->rpa16[e];
+            unsigned code[32];
+            for (int k = 0; k < 16; ++k) {
+                code[k] = (unsigned)(en.rA * 16 + (en.mA[k] & 15)) | ((en.mA[k] & 16) ? 0x8000u : 0u);
+                code[16 + k] = (unsigned)(en.rB * 16 + (en.mB[k] & 15)) | ((en.mB[k] & 16) ? 0x8000u : 0u);
+            }
+            unsigned wd[16];
+            for (int k = 0; k < 16; ++k) wd[k] = code[2 * k] | (code[2 * k + 1] << 16);
+            for (int v = 0; v < 4; ++v) rec[(size_t)e * 4 + v] = make_uint4(wd[4 * v], wd[4 * v + 1], wd[4 * v + 2], wd[4 * v + 3]);
+        }
+        const long per = std::max<long>(1, (P + (kThreads - Ns) - 1) / std::max(1, kThreads - Ns));
+        std::vector<int4> items;
+        std::vector<int> ioff((size_t)Ns + 1, 0);
+        for (int r = 0; r < Ns; ++r) {
+            ioff[r] = (int)items.size();
+            for (int e = lat->rpa_off[r]; e < lat->rpa_off[r + 1]; e += (int)per)
+                items.push_back(make_int4(r, e, (int)std::min<long>(e + per, lat->rpa_off[r + 1]), 0));
+        }
+        ioff[Ns] = (int)items.size();
+        f->tlat_n_items = (int)items.size();
+        if (precision == SR_FP64) {
+            // FP64 kernel: per output (site, mu nu), every signed product of its entries
+            std::vector<int> loff((size_t)Ns * 16 + 1, 0);
+            std::vector<int2> lent;
+            for (int r = 0; r < Ns; ++r)
+                for (int c = 0; c < 16; ++c) {
+                    loff[r * 16 + c] = (int)lent.size();
+                    const int mu = c / 4, nu = c % 4;
+                    for (int e = lat->rpa_off[r]; e < lat->rpa_off[r + 1]; ++e) {
+                        const sr::RpaEntry16& en = lat->rpa16[e];
+                        for (int l = 0; l < 4; ++l) {
+                            const int ma = en.mA[mu * 4 + l], mb = en.mB[l * 4 + nu];
+                            int sg = sr::tri::coef_t(mu, nu, l);
+                            if (ma & 16) sg = -sg;
+                            if (mb & 16) sg = -sg;
+                            const int ia = en.rA * 16 + (ma & 15), ib = en.rB * 16 + (mb & 15);
+                            lent.push_back(make_int2(ia, sg > 0 ? ib : ~ib));
+                        }
                     }
                 }
-            }
-        loff[(size_t)Ns * 16] = (int)lent.size();
+            loff[(size_t)Ns * 16] = (int)lent.size();
+            CK(f->tlat_off.upload(loff.data(), loff.size(), st));
+            CK(f->tlat_ent.upload(lent.data(), lent.size(), st));
+        }
+        CK(f->swap_map16.upload(sm.data(), sm.size(), st));
+        CK(f->onsite_map16.upload(om.data(), om.size(), st));
+        CK(f->tlat_rec.upload(rec.data(), rec.size(), st));
+        CK(f->tlat_items.upload(items.data(), items.size(), st));
+        CK(f->tlat_item_off.upload(ioff.data(), ioff.size(), st));
         std::vector<int> cr(lat->chi_map16.size()), cm(lat->chi_map16.size() * 16);
         for (size_t i = 0; i < cr.size(); ++i) {
             cr[i] = lat->chi_map16[i].r;
             for (int c = 0; c < 16; ++c) cm[i * 16 + c] = lat->chi_map16[i].m[c];
         }
-        CK(f->swap_map16.upload(sm.data(), sm.size(), st));
-        CK(f->onsite_map16.upload(om.data(), om.size(), st));
-        CK(f->tlat_off.upload(loff.data(), loff.size(), st));
-        CK(f->tlat_ent.upload(lent.data(), lent.size(), st));
         CK(f->chi_r16.upload(cr.data(), cr.size(), st));
         CK(f->chi_m16.upload(cm.data(), cm.size(), st));
-        f->nprod = (int)lent.size();
+        f->nprod = (int)(64 * P);   // products of the lattice sum per node (reported)
     }
     // state
     CK(f->gam.alloc((size_t)g.N * ts));
@@ -1862,7 +1897,8 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
     CK(cudaGetLastError());
     if (sr_status s2 = refresh_shadow(f.get(), f->G.p, f->Gf.p)) return s2;
     const bool tc_ok = precision == SR_FP32_MIXED && tc_supported(g.nc, g.nsp, f->dense);
-    f->smem_rhs = g.nc == 16 ? tri_smem_bytes(g.Ns, tri_groups(g.Ns, kThreads), precision == SR_FP64 ? sizeof(double) : sizeof(float))
+    f->smem_rhs = g.nc == 16 ? tri_smem_bytes(g.Ns, tri_groups(g.Ns, kThreads), f->tlat_n_items,
+                                              precision == SR_FP64 ? sizeof(double) : sizeof(float))
                   : precision == SR_FP32_MIXED ? f32_smem_bytes(g.Ns, g.nsp, g.nc, f->nprod, f->dense)
                                                : rhs_smem_bytes(g, f->nprod, f->ntan ? sizeof(DualT) : sizeof(double));
     if (tc_ok) f->smem_tc = f32_smem_bytes(g.Ns, g.nsp, g.nc, f->nprod, f->dense, true);

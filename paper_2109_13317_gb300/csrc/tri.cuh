@@ -24,7 +24,14 @@ constexpr int kQTri = 8;   // integration nodes per shared-memory block of the T
 struct TabsT {
     const int* swap_map;    // Ns * 16: component map of the exchanged pair (transposed)
     const int* onsite_map;  // Ns * 16: component map of (rep, rep) onto site 0
-    const int* lat_off;     // Ns * 16 + 1: lattice-sum entries of each output (site, component)
+    const uint4* lat_rec;   // P * 4: per lattice-sum table entry, 32 16-bit codes: the row-A index
+                            // (rA * 16 + stored component) of A^{mu l} (codes 0..15, mu * 4 + l)
+                            // and the row-B index of B^{l nu} (codes 16..31), bit 15 = sign
+    const int4* lat_items;  // n_items: (site r, first entry, end entry, 0), the entries of r split
+                            // into chunks; items of a site are consecutive
+    const int* lat_item_off;  // Ns + 1: items of each site
+    int n_items;
+    const int* lat_off;     // Ns * 16 + 1: per output (site, component) its signed products
     const int2* lat_ent;    // (row-A index, row-B index or its complement for a negative sign)
 };
 
@@ -130,14 +137,59 @@ struct ShT {
     R* rows;              // kQTri * 2 * 16 Ns (site-major: r * 16 + c)
     R* onrow;             // kQTri * 2 * 16
     R* part;              // NG * Ns * 16: per node-group partial sums of the site-local products
-    R* lat;               // Ns * 16: lattice-sum integrals
+    R* lat;               // lattice-sum integrals: per work item (FP32, n_items * 16) or per
+                          // output (FP64, Ns * 16)
 };
 
+// Lattice-sum slots of k_gamma_rhs_tri<R>: FP32 work items, FP64 outputs.
+__host__ __device__ inline int tri_lat_slots(int Ns, int n_items, size_t rsz) { return rsz == sizeof(float) ? n_items : Ns; }
+
 // Dynamic shared memory of k_gamma_rhs_tri<R> (rsz = sizeof(R)).
-__host__ __device__ inline size_t tri_smem_bytes(int Ns, int NG, size_t rsz) {
+__host__ __device__ inline size_t tri_smem_bytes(int Ns, int NG, int n_items, size_t rsz) {
     auto rnd = [](size_t b) { return (b + 15) & ~size_t(15); };
     return rnd(sizeof(Desc<double>) * kQTri * 4) + rnd(sizeof(int) * kQTri * 4) + rnd(rsz * kQTri * 2 * 16 * Ns) +
-           rnd(rsz * kQTri * 2 * 16) + rnd(rsz * (size_t)NG * Ns * 16) + rnd(rsz * Ns * 16);
+           rnd(rsz * kQTri * 2 * 16) + rnd(rsz * (size_t)NG * Ns * 16) + rnd(rsz * (size_t)tri_lat_slots(Ns, n_items, rsz) * 16);
+}
+
+// Lattice sum of one work item at the nodes of the current block: for every table entry of the
+// item, the 4 x 4 spin matrices A (rows of (ref, j)) and B (rows of (j, i2)) with their
+// signed component maps, out^{mu nu} += sum_l sign(mu, l, nu) A^{mu l} B^{l nu} (the factor 2
+// and the leading minus are applied at the end).
+template <typename R>
+__device__ __forceinline__ void tri_lattice_item(const R* __restrict__ rows, int row, int qn, const uint4* __restrict__ rec,
+                                                 int e0, int e1, R* acc) {
+    for (int e = e0; e < e1; ++e) {
+        const uint4 w0 = rec[4 * e], w1 = rec[4 * e + 1], w2 = rec[4 * e + 2], w3 = rec[4 * e + 3];
+        const unsigned wd[16] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w,
+                                 w2.x, w2.y, w2.z, w2.w, w3.x, w3.y, w3.z, w3.w};
+        int off[32];
+        unsigned neg = 0;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            const unsigned c = (k & 1) ? (wd[k >> 1] >> 16) : (wd[k >> 1] & 0xffffu);
+            off[k] = (int)(c & 0x7fffu);
+            neg |= ((c >> 15) & 1u) << k;
+        }
+        for (int q = 0; q < qn; ++q) {
+            const R* Ar = rows + (q * 2) * row;
+            const R* Br = Ar + row;
+            R a[16], b[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const R va = Ar[off[k]], vb = Br[off[16 + k]];
+                a[k] = ((neg >> k) & 1u) ? -va : va;
+                b[k] = ((neg >> (16 + k)) & 1u) ? -vb : vb;
+            }
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+                for (int nu = 0; nu < 4; ++nu)
+#pragma unroll
+                    for (int l = 0; l < 4; ++l)
+                        acc[mu * 4 + nu] = fmadd(sr::tri::coef_t(mu, nu, l) > 0 ? a[mu * 4 + l] : -a[mu * 4 + l], b[l * 4 + nu],
+                                                 acc[mu * 4 + nu]);
+        }
+    }
 }
 
 __host__ __device__ inline int tri_groups(int Ns, int threads) {
@@ -164,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
         sh.rows = (R*)take(sizeof(R) * kQTri * 2 * 16 * g.Ns);
         sh.onrow = (R*)take(sizeof(R) * kQTri * 2 * 16);
         sh.part = (R*)take(sizeof(R) * (size_t)NG * g.Ns * 16);
-        sh.lat = (R*)take(sizeof(R) * g.Ns * 16);
+        sh.lat = (R*)take(sizeof(R) * (size_t)tri_lat_slots(g.Ns, tt.n_items, sizeof(R)) * 16);
     }
     const int tid = threadIdx.x;
     const int ti = blockIdx.x % g.N;
@@ -179,7 +231,7 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
     const int nwork = g.Ns * NG;
 
     for (int o = tid; o < NG * row; o += blockDim.x) sh.part[o] = R(0);
-    for (int o = tid; o < row; o += blockDim.x) sh.lat[o] = R(0);
+    for (int o = tid; o < tri_lat_slots(g.Ns, tt.n_items, sizeof(R)) * 16; o += blockDim.x) sh.lat[o] = R(0);
 
     for (int ch = 0; ch < 3; ++ch) {
         const int vi = ch == 0 ? si : (ch == 1 ? ti : ui);
@@ -247,8 +299,11 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
 #pragma unroll
                 for (int k = 0; k < 16; ++k) P[k] += o[k];
             }
-            // lattice sum: every output (site, component) integrates its signed products
-            if (ch == 1)
+            // lattice sum.  FP32: work items (a site and a chunk of its table entries), one per
+            // thread, 4 x 4 spin matrices per entry (half a shared-memory load per FMA); FP64
+            // (bound by the FP64 pipe): every output (site, component) integrates its signed
+            // products
+            if (ch == 1 && sizeof(R) == sizeof(double))
                 for (int o = tid; o < row; o += blockDim.x) {
                     R acc = R(0);
                     for (int k = tt.lat_off[o]; k < tt.lat_off[o + 1]; ++k) {
@@ -260,6 +315,17 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
                     }
                     sh.lat[o] += acc;
                 }
+            if (ch == 1 && sizeof(R) == sizeof(float))
+                for (int it = tid; it < tt.n_items; it += blockDim.x) {
+                    const int4 item = tt.lat_items[it];
+                    R acc[16];
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) acc[k] = R(0);
+                    tri_lattice_item<R>(sh.rows, row, qn, tt.lat_rec, item.y, item.z, acc);
+                    R* L = sh.lat + (size_t)it * 16;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) L[k] += acc[k];
+                }
         }
     }
     __syncthreads();
@@ -267,7 +333,11 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
         R a = R(0);
         for (int k = 0; k < NG; ++k) a += sh.part[(size_t)k * row + o];
         const int r = o >> 4, c = o & 15;
-        dG[((size_t)(p * g.N + ti) * 16 + c) * g.Ns + r] = (double)a - 2.0 * (double)sh.lat[o];
+        R l = R(0);
+        if (sizeof(R) == sizeof(double)) l = sh.lat[o];
+        else
+            for (int it = tt.lat_item_off[r]; it < tt.lat_item_off[r + 1]; ++it) l += sh.lat[(size_t)it * 16 + c];
+        dG[((size_t)(p * g.N + ti) * 16 + c) * g.Ns + r] = (double)a - 2.0 * (double)l;
     }
 }
 
