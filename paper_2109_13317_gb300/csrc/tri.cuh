@@ -1,5 +1,5 @@
 // Kernels of the TRI core: the flow of all 16 basis functions Gamma^{mu nu} (FP64 state; the
-// vertex products in FP64, or in FP32 for the mixed-precision flow).
+// lookups and vertex products in FP64, or in FP32 for the mixed-precision flow).
 //
 // Included by flow.cu after the forward kernels, whose propagators, node arguments and lookup
 // descriptors it shares.  Equations: arXiv:2109.13317, Sec. 3 (Eqs. frg:flowexplicit:1particle
@@ -37,16 +37,18 @@ struct TabsT {
 
 __device__ __forceinline__ bool tri_mixed(int c) { return ((c >> 2) == 0) != ((c & 3) == 0); }
 
-// Component c of the pair (ref, rep_r) at the descriptor's frequencies.
-__device__ __forceinline__ double tri_value(const double* __restrict__ G, const Desc<double>& d, bool mneg,
-                                            const Tabs& tb, const TabsT& tt, const Geo& g, int r, int c) {
+// Component c of the pair (ref, rep_r) at the descriptor's frequencies, interpolated in the
+// descriptor's weight type W (FP64, or FP32 in the mixed-precision vertex kernel).
+template <typename W>
+__device__ __forceinline__ W tri_value(const double* __restrict__ G, const Desc<W>& d, bool mneg, const Tabs& tb,
+                                       const TabsT& tt, const Geo& g, int r, int c) {
     int rs = r, m = c;
     if (d.swap) { rs = tb.swap_r[r]; m = tt.swap_map[r * 16 + c]; }
     const int cs = m & 15;
     const double* base = G + cs * g.Ns + rs;
-    const double* wgt = (cs & 3) == 0 ? d.wd : d.ws;
-    double acc = 0.0;
-    for (int k = 0; k < d.n; ++k) acc = fma(wgt[k], base[d.off[k]], acc);
+    const W* wgt = (cs & 3) == 0 ? d.wd : d.ws;
+    W acc = W(0);
+    for (int k = 0; k < d.n; ++k) acc = fmadd(wgt[k], (W)base[d.off[k]], acc);
     const bool neg = ((m & 16) != 0) != (mneg && tri_mixed(c));
     return neg ? -acc : acc;
 }
@@ -132,7 +134,7 @@ __device__ __forceinline__ void tri_onsite_acc(const R* __restrict__ A, const R*
 
 template <typename R>
 struct ShT {
-    Desc<double>* desc;   // kQTri * 4
+    Desc<R>* desc;        // kQTri * 4
     int* mneg;            // kQTri * 4
     R* rows;              // kQTri * 2 * 16 Ns (site-major: r * 16 + c)
     R* onrow;             // kQTri * 2 * 16
@@ -147,7 +149,8 @@ __host__ __device__ inline int tri_lat_slots(int Ns, int n_items, size_t rsz) { 
 // Dynamic shared memory of k_gamma_rhs_tri<R> (rsz = sizeof(R)).
 __host__ __device__ inline size_t tri_smem_bytes(int Ns, int NG, int n_items, size_t rsz) {
     auto rnd = [](size_t b) { return (b + 15) & ~size_t(15); };
-    return rnd(sizeof(Desc<double>) * kQTri * 4) + rnd(sizeof(int) * kQTri * 4) + rnd(rsz * kQTri * 2 * 16 * Ns) +
+    const size_t dsz = rsz == sizeof(float) ? sizeof(Desc<float>) : sizeof(Desc<double>);
+    return rnd(dsz * kQTri * 4) + rnd(sizeof(int) * kQTri * 4) + rnd(rsz * kQTri * 2 * 16 * Ns) +
            rnd(rsz * kQTri * 2 * 16) + rnd(rsz * (size_t)NG * Ns * 16) + rnd(rsz * (size_t)tri_lat_slots(Ns, n_items, rsz) * 16);
 }
 
@@ -198,8 +201,8 @@ __host__ __device__ inline int tri_groups(int Ns, int threads) {
 }
 
 // dGamma/dLambda of every stored entry of one frequency triple (one CTA per triple).  R is
-// the type of the interpolated rows, the products and their node sums (double: FP64 flow;
-// float: FP32-mixed flow, lookups and output in FP64).
+// the type of the lookup weights, the interpolated rows, the products and their node sums
+// (double: FP64 flow; float: FP32-mixed flow, reading the FP64 state, output in FP64).
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, TabsT tt, const double* __restrict__ w,
                                                             const double* __restrict__ G, const double* __restrict__ nx,
@@ -211,7 +214,7 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
     {
         size_t off = 0;
         auto take = [&](size_t bytes) { unsigned char* q = smem + off; off += (bytes + 15) & ~size_t(15); return q; };
-        sh.desc = (Desc<double>*)take(sizeof(Desc<double>) * kQTri * 4);
+        sh.desc = (Desc<R>*)take(sizeof(Desc<R>) * kQTri * 4);
         sh.mneg = (int*)take(sizeof(int) * kQTri * 4);
         sh.rows = (R*)take(sizeof(R) * kQTri * 2 * 16 * g.Ns);
         sh.onrow = (R*)take(sizeof(R) * kQTri * 2 * 16);
@@ -251,11 +254,11 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
                 double a, b, c;
                 node_args(ch, rw, x, s, t, u, w1p, w2p, w1, w2, a, b, c);
                 const int exs = ch == 0 ? 0 : (ch == 2 ? 2 : (rw < 2 ? 1 : 2));
-                Desc<double>& d = sh.desc[q * 4 + rw];
+                Desc<R>& d = sh.desc[q * 4 + rw];
                 make_desc(a, b, c, exs, vi, tb, g, d);
                 sh.mneg[q * 4 + rw] = (b < 0.0) != (c < 0.0);
                 if (rw == 0 || rw == 3) {
-                    const double wn = Wp[q0 + q];
+                    const R wn = (R)Wp[q0 + q];
                     for (int k = 0; k < d.n; ++k) { d.wd[k] *= wn; d.ws[k] *= wn; }
                 }
             }
@@ -264,13 +267,13 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
                 const int q = idx / (2 * row), rem = idx % (2 * row);
                 const int rw = rem / row, e = rem % row;
                 const int r = e >> 4, c = e & 15;
-                sh.rows[(q * 2 + rw) * row + e] = (R)tri_value(G, sh.desc[q * 4 + rw], sh.mneg[q * 4 + rw] != 0, tb, tt, g, r, c);
+                sh.rows[(q * 2 + rw) * row + e] = tri_value<R>(G, sh.desc[q * 4 + rw], sh.mneg[q * 4 + rw] != 0, tb, tt, g, r, c);
             }
             if (ch == 1)
                 for (int j = tid; j < qn * 2 * 16; j += blockDim.x) {
                     const int q = j / 32, rr = (j / 16) % 2, c = j % 16;
                     sh.onrow[(q * 2 + rr) * 16 + c] =
-                        (R)tri_value(G, sh.desc[q * 4 + 2 + rr], sh.mneg[q * 4 + 2 + rr] != 0, tb, tt, g, 0, c);
+                        tri_value<R>(G, sh.desc[q * 4 + 2 + rr], sh.mneg[q * 4 + 2 + rr] != 0, tb, tt, g, 0, c);
                 }
             __syncthreads();
             // site-local products: work item (site r, node group gq) owns part[gq][r]
