@@ -5,7 +5,8 @@ Tolerance: 1e-10 relative, normwise per component (max|x - x_ref| / max|x_ref|),
 other FP64 cores.  Models: the kagome antiferromagnet with out-of-plane DM couplings of the
 paper's second worked example (imaginary-class functions generated by the flow), the same
 model rotated in spin space (a DM vector along a generic axis: no spin symmetry left), and
-the Heisenberg-Kitaev model, where the TRI core must reproduce the XYZ core.
+the Heisenberg-Kitaev model, where the TRI core must reproduce the XYZ core, and the
+Heisenberg-Kitaev-Gamma model (symmetric off-diagonal exchange).
 """
 import numpy as np
 import pytest
@@ -52,6 +53,7 @@ MODELS = [
     ("kagome_dm", lambda: W.kagome_dm(1.0, 0.5), 2),
     ("kagome_dm_rotated", lambda: W.rotated(W.kagome_dm(1.0, 0.4), _generic_rotation()), 2),
     ("honeycomb_kitaev", lambda: W.Model(W.honeycomb(), W.honeycomb_kitaev(0.2, -1.0).couplings, "TRI"), 2),
+    ("honeycomb_kitaev_gamma", lambda: W.honeycomb_kitaev_gamma(0.1, -1.0, 0.5), 2),
 ]
 
 

@@ -129,7 +129,7 @@ def test_symmetry_tables_against_unreduced_oracle(model, L):
 
 
 @pytest.mark.parametrize("model,L", [(W.kagome_dm(1.0, 0.5), 2), (W.rotated(W.kagome_dm(1.0, 0.3), np.eye(3)[[1, 2, 0]]), 2),
-                                     (W.nn_heisenberg(W.honeycomb()), 2)])
+                                     (W.nn_heisenberg(W.honeycomb()), 2), (W.honeycomb_kitaev_gamma(0.1, -1.0, 0.5), 3)])
 def test_tri_symmetry_tables_against_unreduced_oracle(model, L):
     """TRI core: every pair (b, j) of the oracle's translation-only storage maps to an
     irreducible site and a signed permutation of the 16 basis functions; after a few flow

@@ -164,6 +164,22 @@ def rotated(model: Model, R: np.ndarray, backend: str = "TRI") -> Model:
     return Model(model.cell, [Coupling(c.frm, c.to, R @ c.M @ R.T) for c in model.couplings], backend)
 
 
+def honeycomb_kitaev_gamma(J: float = 0.1, K: float = -1.0, G: float = 0.5) -> Model:
+    """Heisenberg-Kitaev-Gamma model on the honeycomb lattice: on a bond of type gamma (x, y, z
+    for the three bond directions), J S.S + K S^g S^g + G (S^a S^b + S^b S^a) with (a, b) the other
+    two components.  The symmetric off-diagonal G term needs the TRI core."""
+    c = honeycomb()
+    to = [(0, 0, 0, 1), (0, -1, 0, 1), (-1, 0, 0, 1)]
+    cps = []
+    for g, t in enumerate(to):
+        a, b = [x for x in range(3) if x != g]
+        M = J * I3 + K * _diag(g)
+        M[a, b] += G
+        M[b, a] += G
+        cps.append(Coupling((0, 0, 0, 0), t, M))
+    return Model(c, cps, "TRI")
+
+
 def honeycomb_kitaev_linear():
     """Heisenberg-Kitaev couplings as a linear function of theta = (J, K): the unit cell, the
     coupling sites and the basis matrices B (2, n_couplings, 3, 3) with M_c = J B[0, c] +
