@@ -32,13 +32,17 @@ def _rel(a, b):
 
 
 def _cmp(got, exp, tol=TOL):
-    """Normwise per component of [pair][t][c][r] arrays."""
+    """Normwise per component of [pair][t][c][r] arrays.  A component below 1e-6 of the whole
+    vertex's scale is formed by cancellation (e.g. the mixed functions of the Kitaev-Gamma
+    model early in the flow) and is compared on that floor."""
+    floor = 1e-6 * np.abs(exp).max()
     for c in range(16):
         e = exp[:, :, c]
         if np.abs(e).max() == 0:
             assert np.abs(got[:, :, c]).max() < 1e-14, c
             continue
-        assert _rel(got[:, :, c], e) < tol, (c, _rel(got[:, :, c], e))
+        err = np.abs(got[:, :, c] - e).max() / max(np.abs(e).max(), floor)
+        assert err < tol, (c, err)
 
 
 def _generic_rotation():
