@@ -1820,8 +1820,8 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
             const sr::RpaEntry16& en = lat->rpa16[e];
             unsigned code[32];
             for (int k = 0; k < 16; ++k) {
-                code[k] = (unsigned)(en.rA * 16 + (en.mA[k] & 15)) | ((en.mA[k] & 16) ? 0x8000u : 0u);
-                code[16 + k] = (unsigned)(en.rB * 16 + (en.mB[k] & 15)) | ((en.mB[k] & 16) ? 0x8000u : 0u);
+                code[k] = (unsigned)tri_slot(en.rA, en.mA[k] & 15) | ((en.mA[k] & 16) ? 0x8000u : 0u);
+                code[16 + k] = (unsigned)tri_slot(en.rB, en.mB[k] & 15) | ((en.mB[k] & 16) ? 0x8000u : 0u);
             }
             unsigned wd[16];
             for (int k = 0; k < 16; ++k) wd[k] = code[2 * k] | (code[2 * k + 1] << 16);
@@ -1852,7 +1852,7 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
                             int sg = sr::tri::coef_t(mu, nu, l);
                             if (ma & 16) sg = -sg;
                             if (mb & 16) sg = -sg;
-                            const int ia = en.rA * 16 + (ma & 15), ib = en.rB * 16 + (mb & 15);
+                            const int ia = tri_slot(en.rA, ma & 15), ib = tri_slot(en.rB, mb & 15);
                             lent.push_back(make_int2(ia, sg > 0 ? ib : ~ib));
                         }
                     }

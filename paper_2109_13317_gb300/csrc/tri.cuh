@@ -24,15 +24,15 @@ constexpr int kQTri = 8;   // integration nodes per shared-memory block of the T
 struct TabsT {
     const int* swap_map;    // Ns * 16: component map of the exchanged pair (transposed)
     const int* onsite_map;  // Ns * 16: component map of (rep, rep) onto site 0
-    const uint4* lat_rec;   // P * 4: per lattice-sum table entry, 32 16-bit codes: the row-A index
-                            // (rA * 16 + stored component) of A^{mu l} (codes 0..15, mu * 4 + l)
-                            // and the row-B index of B^{l nu} (codes 16..31), bit 15 = sign
+    const uint4* lat_rec;   // P * 4: per lattice-sum table entry, 32 16-bit codes: the row slot
+                            // (tri_slot(rA, stored component)) of A^{mu l} (codes 0..15, mu * 4 + l)
+                            // and the row slot of B^{l nu} (codes 16..31), bit 15 = sign
     const int4* lat_items;  // n_items: (site r, first entry, end entry, 0), the entries of r split
                             // into chunks; items of a site are consecutive
     const int* lat_item_off;  // Ns + 1: items of each site
     int n_items;
     const int* lat_off;     // Ns * 16 + 1: per output (site, component) its signed products
-    const int2* lat_ent;    // (row-A index, row-B index or its complement for a negative sign)
+    const int2* lat_ent;    // (row-A slot, row-B slot or its complement for a negative sign)
 };
 
 __device__ __forceinline__ bool tri_mixed(int c) { return ((c >> 2) == 0) != ((c & 3) == 0); }
@@ -87,13 +87,18 @@ __global__ void k_sigma_rhs_tri(Geo g, Tabs tb, TabsT tt, const double* __restri
     }
 }
 
+// Shared-memory slot of component c of site r in a row: the 16 components of a site are
+// stored XOR-rotated by the site index, so that lanes reading the same component of different
+// sites (site-local products, lattice-sum entries) fall into different banks.
+__host__ __device__ inline int tri_slot(int r, int c) { return r * 16 + (c ^ (r & 15)); }
+
 // Site-local products of the s (CH = 0) or u (CH = 2) channel at one node, accumulated into
-// o[16] (A, B: the site's two rows).
+// o[16] (A, B: the site's two rows, rotated by sw = r & 15).
 template <int CH, typename R>
-__device__ __forceinline__ void tri_su_acc(const R* __restrict__ A, const R* __restrict__ B, R* o) {
+__device__ __forceinline__ void tri_su_acc(const R* __restrict__ A, const R* __restrict__ B, int sw, R* o) {
     R a[16], b[16];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) { a[k] = A[k]; b[k] = B[k]; }
+    for (int k = 0; k < 16; ++k) { a[k] = A[k ^ sw]; b[k] = B[k ^ sw]; }
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu)
 #pragma unroll
@@ -111,10 +116,10 @@ __device__ __forceinline__ void tri_su_acc(const R* __restrict__ A, const R* __r
 // t-channel on-site terms: A C (C the on-site row of the pair (i2, i2)) and D B (D of (i1, i1)).
 template <typename R>
 __device__ __forceinline__ void tri_onsite_acc(const R* __restrict__ A, const R* __restrict__ B, const R* __restrict__ C,
-                                               const R* __restrict__ D, R* o) {
+                                               const R* __restrict__ D, int sw, R* o) {
     R a[16], b[16], c[16], d[16];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) { a[k] = A[k]; b[k] = B[k]; c[k] = C[k]; d[k] = D[k]; }
+    for (int k = 0; k < 16; ++k) { a[k] = A[k ^ sw]; b[k] = B[k ^ sw]; c[k] = C[k]; d[k] = D[k]; }
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu)
 #pragma unroll
@@ -136,7 +141,7 @@ template <typename R>
 struct ShT {
     Desc<R>* desc;        // kQTri * 4
     int* mneg;            // kQTri * 4
-    R* rows;              // kQTri * 2 * 16 Ns (site-major: r * 16 + c)
+    R* rows;              // kQTri * 2 * 16 Ns (site-major, component c of site r at tri_slot(r, c))
     R* onrow;             // kQTri * 2 * 16
     R* part;              // NG * Ns * 16: per node-group partial sums of the site-local products
     R* lat;               // lattice-sum integrals: per work item (FP32, n_items * 16) or per
@@ -267,7 +272,8 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
                 const int q = idx / (2 * row), rem = idx % (2 * row);
                 const int rw = rem / row, e = rem % row;
                 const int r = e >> 4, c = e & 15;
-                sh.rows[(q * 2 + rw) * row + e] = tri_value<R>(G, sh.desc[q * 4 + rw], sh.mneg[q * 4 + rw] != 0, tb, tt, g, r, c);
+                sh.rows[(q * 2 + rw) * row + tri_slot(r, c)] =
+                    tri_value<R>(G, sh.desc[q * 4 + rw], sh.mneg[q * 4 + rw] != 0, tb, tt, g, r, c);
             }
             if (ch == 1)
                 for (int j = tid; j < qn * 2 * 16; j += blockDim.x) {
@@ -285,8 +291,8 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
                 for (int q = gq; q < qn; q += NG) {
                     const R* A = sh.rows + (q * 2) * row + r * 16;
                     const R* B = A + row;
-                    if (ch == 0) tri_su_acc<0, R>(A, B, o);
-                    else if (ch == 2) tri_su_acc<2, R>(A, B, o);
+                    if (ch == 0) tri_su_acc<0, R>(A, B, r & 15, o);
+                    else if (ch == 2) tri_su_acc<2, R>(A, B, r & 15, o);
                     else {
                         R Cp[16];
                         const R* C0 = sh.onrow + (q * 2) * 16;
@@ -295,7 +301,7 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
                             const int mk = tt.onsite_map[r * 16 + k];
                             Cp[k] = (mk & 16) ? -C0[mk & 15] : C0[mk & 15];
                         }
-                        tri_onsite_acc<R>(A, B, Cp, sh.onrow + (q * 2 + 1) * 16, o);
+                        tri_onsite_acc<R>(A, B, Cp, sh.onrow + (q * 2 + 1) * 16, r & 15, o);
                     }
                 }
                 R* P = sh.part + (size_t)gq * row + r * 16;
