@@ -1545,7 +1545,7 @@ static sr_status run_rhs(sr_flow* f, double lam, const double* gam_s, const doub
         if (f->prec == SR_FP64)
             k_gamma_rhs_tri<double><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, tt, f->w.p, G_s, f->nx.p, f->nW.p, f->ncount.p, dG_o);
         else
-            k_gamma_rhs_tri<float><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, tt, f->w.p, G_s, f->nx.p, f->nW.p, f->ncount.p, dG_o);
+            k_gamma_rhs_tri<float><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, tt, f->w.p, Gf_s, f->nx.p, f->nW.p, f->ncount.p, dG_o);
         if (sr_status s = prof_end(f, 2, e0)) return s;
         CK(cudaGetLastError());
         f->n_rhs++;
@@ -1583,7 +1583,13 @@ static sr_status run_rhs(sr_flow* f, double lam, const double* gam_s, const doub
 }
 
 static sr_status refresh_shadow(sr_flow* f, const double* G_s, float* Gf_s) {
-    if (f->prec != SR_FP32_MIXED || f->g.nc == 16) return SR_OK;   // the TRI kernel reads the FP64 state
+    if (f->prec != SR_FP32_MIXED) return SR_OK;
+    if (f->g.nc == 16) {
+        const long n = f->g.nent;
+        k_shadow_tri<<<(unsigned)((n + 255) / 256), 256, 0, f->stream>>>(n, G_s, Gf_s);
+        CK(cudaGetLastError());
+        return SR_OK;
+    }
     long n = f->g.nentp;
     k_shadow<<<(unsigned)((n + 255) / 256), 256, 0, f->stream>>>(f->g, f->tabs(), G_s, Gf_s, f->has_swap ? 1 : 0);
     CK(cudaGetLastError());
@@ -1880,7 +1886,7 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
     CK(f->G.alloc((size_t)g.nent * ts));
     CK(f->dgam.alloc((size_t)g.N * ts));
     CK(f->dG.alloc((size_t)g.nent * ts));
-    if (precision == SR_FP32_MIXED && g.nc != 16) CK(f->Gf.alloc((size_t)g.nentp * (f->has_swap ? 2 : 1)));
+    if (precision == SR_FP32_MIXED) CK(f->Gf.alloc(g.nc == 16 ? (size_t)g.nent : (size_t)g.nentp * (f->has_swap ? 2 : 1)));
     CK(f->nx.alloc((size_t)3 * g.N * g.nmax));
     CK(f->nW.alloc((size_t)3 * g.N * g.nmax * ts));
     CK(f->nWf.alloc((size_t)3 * g.N * g.nmax));

@@ -39,13 +39,13 @@ __device__ __forceinline__ bool tri_mixed(int c) { return ((c >> 2) == 0) != ((c
 
 // Component c of the pair (ref, rep_r) at the descriptor's frequencies, interpolated in the
 // descriptor's weight type W (FP64, or FP32 in the mixed-precision vertex kernel).
-template <typename W>
-__device__ __forceinline__ W tri_value(const double* __restrict__ G, const Desc<W>& d, bool mneg, const Tabs& tb,
+template <typename W, typename S>
+__device__ __forceinline__ W tri_value(const S* __restrict__ G, const Desc<W>& d, bool mneg, const Tabs& tb,
                                        const TabsT& tt, const Geo& g, int r, int c) {
     int rs = r, m = c;
     if (d.swap) { rs = tb.swap_r[r]; m = tt.swap_map[r * 16 + c]; }
     const int cs = m & 15;
-    const double* base = G + cs * g.Ns + rs;
+    const S* base = G + cs * g.Ns + rs;
     const W* wgt = (cs & 3) == 0 ? d.wd : d.ws;
     W acc = W(0);
     for (int k = 0; k < d.n; ++k) acc = fmadd(wgt[k], (W)base[d.off[k]], acc);
@@ -206,11 +206,12 @@ __host__ __device__ inline int tri_groups(int Ns, int threads) {
 }
 
 // dGamma/dLambda of every stored entry of one frequency triple (one CTA per triple).  R is
-// the type of the lookup weights, the interpolated rows, the products and their node sums
-// (double: FP64 flow; float: FP32-mixed flow, reading the FP64 state, output in FP64).
+// the type of the state read (the FP64 state, or its FP32 copy), of the lookup weights, the
+// interpolated rows, the products and their node sums (double: FP64 flow; float: FP32-mixed
+// flow, output in FP64).
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, TabsT tt, const double* __restrict__ w,
-                                                            const double* __restrict__ G, const double* __restrict__ nx,
+                                                            const R* __restrict__ G, const double* __restrict__ nx,
                                                             const double* __restrict__ nW, const int* __restrict__ ncount,
                                                             double* __restrict__ dG) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -348,6 +349,12 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
             for (int it = tt.lat_item_off[r]; it < tt.lat_item_off[r + 1]; ++it) l += sh.lat[(size_t)it * 16 + c];
         dG[((size_t)(p * g.N + ti) * 16 + c) * g.Ns + r] = (double)a - 2.0 * (double)l;
     }
+}
+
+// FP32 copy of the TRI state (same layout) for the FP32-mixed vertex kernel.
+__global__ void k_shadow_tri(long n, const double* __restrict__ G, float* __restrict__ Gf) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i < n) Gf[i] = (float)G[i];
 }
 
 // Correlations chi^{mu nu}_{b j}, all 16 components (Eq. frg:correlation), one block per
