@@ -315,8 +315,31 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
             // products
             if (ch == 1 && sizeof(R) == sizeof(double))
                 for (int o = tid; o < row; o += blockDim.x) {
+                    // four products at a time: independent FMA chains over the nodes
                     R acc = R(0);
-                    for (int k = tt.lat_off[o]; k < tt.lat_off[o + 1]; ++k) {
+                    const int k0 = tt.lat_off[o], k1 = tt.lat_off[o + 1];
+                    int k = k0;
+                    for (; k + 4 <= k1; k += 4) {
+                        int ia[4], ib[4];
+                        bool ng[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int2 en = tt.lat_ent[k + j];
+                            ng[j] = en.y < 0;
+                            ia[j] = en.x;
+                            ib[j] = ng[j] ? ~en.y : en.y;
+                        }
+                        R a[4] = {R(0), R(0), R(0), R(0)};
+                        for (int q = 0; q < qn; ++q) {
+                            const R* Ar = sh.rows + (q * 2) * row;
+                            const R* Br = Ar + row;
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) a[j] = fmadd(Ar[ia[j]], Br[ib[j]], a[j]);
+                        }
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc += ng[j] ? -a[j] : a[j];
+                    }
+                    for (; k < k1; ++k) {
                         const int2 en = tt.lat_ent[k];
                         const int ib = en.y < 0 ? ~en.y : en.y;
                         R a = R(0);
