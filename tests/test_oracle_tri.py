@@ -276,3 +276,26 @@ def test_tri_rhs_entries_match_full_rhs(dm_flow):
     for e, g in zip(ent, got):
         b, k, si, ti, ui = (int(x) for x in e)
         np.testing.assert_allclose(g, f.block(dG, b)[k, :, pairs.index((si, ui)), ti], rtol=0, atol=1e-15)
+
+
+def test_tri_chi_bare_vertex_closed_form():
+    """Constant Gamma = J/4 with off-diagonal (DM) J: chi^{mu nu}_{ij} = -J^{mu nu}_{ij} /
+    (4 pi^2 Lambda^2) for i != j and every spin pair mu, nu (the product quadrature integrates
+    G^2 exactly, and the direct vertex term is 4 Gamma^{mu nu}); the functions with a density
+    index vanish; on site (J_ii = 0) only the bubble 1/(2 pi Lambda) delta_{mu nu} remains."""
+    mesh = O.mesh_exponential(10, 0.01, 20.0)
+    model = W.kagome_dm(1.0, 0.5)
+    f = O.OracleFlowTRI(model, 2, mesh)
+    lam = 0.8
+    chi = f.chi(lam)
+    for b in range(f.nb):
+        for k, s in enumerate(f.sites(b)):
+            c = chi[b][k].reshape(4, 4)
+            if int(s[3]) == b and not np.any(s[:3]):
+                np.testing.assert_allclose(c, np.eye(4) / (2 * math.pi * lam), rtol=1e-13, atol=1e-17)
+                continue
+            J = f.coupling(b, k)
+            np.testing.assert_allclose(c[1:, 1:].real, -J / (4 * math.pi ** 2 * lam ** 2), rtol=1e-12, atol=1e-16)
+            assert np.abs(c[1:, 1:].imag).max() == 0.0
+            assert np.abs(c[0, :]).max() < 1e-16 and np.abs(c[:, 0]).max() < 1e-16
+    assert np.abs(model.couplings[0].M - model.couplings[0].M.T).max() > 0.9   # DM part present
