@@ -1826,8 +1826,23 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
             const sr::RpaEntry16& en = lat->rpa16[e];
             unsigned code[32];
             for (int k = 0; k < 16; ++k) {
-                code[k] = (unsigned)tri_slot(en.rA, en.mA[k] & 15) | ((en.mA[k] & 16) ? 0x8000u : 0u);
-                code[16 + k] = (unsigned)tri_slot(en.rB, en.mB[k] & 15) | ((en.mB[k] & 16) ? 0x8000u : 0u);
+                code[k] = (unsigned)tri_slot(en.rA, en.mA[k] & 15);
+                code[16 + k] = (unsigned)tri_slot(en.rB, en.mB[k] & 15);
+            }
+            // signs of signed permutations factorise: sign A^{mu l} = alpha(mu) beta(l),
+            // sign B^{l nu} = gamma(l) delta(nu) (with beta(0) = gamma(0) = 1)
+            auto sgn = [](int m) { return (m & 16) ? -1 : 1; };
+            int alpha[4], beta[4], gamma_[4], delta[4];
+            for (int l = 0; l < 4; ++l) { beta[l] = sgn(en.mA[0 * 4 + l]) * sgn(en.mA[0]); gamma_[l] = sgn(en.mB[l * 4 + 0]) * sgn(en.mB[0]); }
+            for (int m = 0; m < 4; ++m) { alpha[m] = sgn(en.mA[m * 4 + 0]); delta[m] = sgn(en.mB[0 * 4 + m]); }
+            for (int m = 0; m < 4; ++m)
+                for (int l = 0; l < 4; ++l)
+                    if (sgn(en.mA[m * 4 + l]) != alpha[m] * beta[l] || sgn(en.mB[l * 4 + m]) != gamma_[l] * delta[m])
+                        return fail(SR_ESYMMETRY, "lattice-sum component map is not a signed permutation");
+            for (int m = 0; m < 4; ++m) {
+                if (alpha[m] < 0) code[m] |= 0x8000u;
+                if (delta[m] < 0) code[4 + m] |= 0x8000u;
+                if (beta[m] * gamma_[m] < 0) code[8 + m] |= 0x8000u;
             }
             unsigned wd[16];
             for (int k = 0; k < 16; ++k) wd[k] = code[2 * k] | (code[2 * k + 1] << 16);

@@ -26,7 +26,8 @@ struct TabsT {
     const int* onsite_map;  // Ns * 16: component map of (rep, rep) onto site 0
     const uint4* lat_rec;   // P * 4: per lattice-sum table entry, 32 16-bit codes: the row slot
                             // (tri_slot(rA, stored component)) of A^{mu l} (codes 0..15, mu * 4 + l)
-                            // and the row slot of B^{l nu} (codes 16..31), bit 15 = sign
+                            // and the row slot of B^{l nu} (codes 16..31); bit 15 of codes 0..11
+                            // carries the factorised signs (tri_lattice_item)
     const int4* lat_items;  // n_items: (site r, first entry, end entry, 0), the entries of r split
                             // into chunks; items of a site are consecutive
     const int* lat_item_off;  // Ns + 1: items of each site
@@ -160,9 +161,13 @@ __host__ __device__ inline size_t tri_smem_bytes(int Ns, int NG, int n_items, si
 }
 
 // Lattice sum of one work item at the nodes of the current block: for every table entry of the
-// item, the 4 x 4 spin matrices A (rows of (ref, j)) and B (rows of (j, i2)) with their
-// signed component maps, out^{mu nu} += sum_l sign(mu, l, nu) A^{mu l} B^{l nu} (the factor 2
-// and the leading minus are applied at the end).
+// item, the 4 x 4 spin matrices A (rows of (ref, j)) and B (rows of (j, i2)) under their signed
+// component maps, out^{mu nu} += sum_l sign(mu, l, nu) A^{mu l} B^{l nu} (the factor 2 and the
+// leading minus are applied at the end).  The signs of a signed permutation factorise,
+// sign A^{mu l} = alpha(mu) beta(l) and sign B^{l nu} = gamma(l) delta(nu): the node sums run
+// on unsigned loads with beta(l) gamma(l) on B, and alpha(mu) delta(nu) multiplies the entry's
+// sum once (codes: row slots in bits 0..14; bit 15 of code mu = alpha(mu) < 0, of code 4 + nu =
+// delta(nu) < 0, of code 8 + l = beta(l) gamma(l) < 0).
 template <typename R>
 __device__ __forceinline__ void tri_lattice_item(const R* __restrict__ rows, int row, int qn, const uint4* __restrict__ rec,
                                                  int e0, int e1, R* acc) {
@@ -171,22 +176,24 @@ __device__ __forceinline__ void tri_lattice_item(const R* __restrict__ rows, int
         const unsigned wd[16] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w,
                                  w2.x, w2.y, w2.z, w2.w, w3.x, w3.y, w3.z, w3.w};
         int off[32];
-        unsigned neg = 0;
+        R sg[12];
 #pragma unroll
         for (int k = 0; k < 32; ++k) {
             const unsigned c = (k & 1) ? (wd[k >> 1] >> 16) : (wd[k >> 1] & 0xffffu);
             off[k] = (int)(c & 0x7fffu);
-            neg |= ((c >> 15) & 1u) << k;
+            if (k < 12) sg[k] = (c & 0x8000u) ? R(-1) : R(1);
         }
+        R t[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) t[k] = R(0);
         for (int q = 0; q < qn; ++q) {
             const R* Ar = rows + (q * 2) * row;
             const R* Br = Ar + row;
             R a[16], b[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
-                const R va = Ar[off[k]], vb = Br[off[16 + k]];
-                a[k] = ((neg >> k) & 1u) ? -va : va;
-                b[k] = ((neg >> (16 + k)) & 1u) ? -vb : vb;
+                a[k] = Ar[off[k]];
+                b[k] = Br[off[16 + k]] * sg[8 + (k >> 2)];
             }
 #pragma unroll
             for (int mu = 0; mu < 4; ++mu)
@@ -194,9 +201,13 @@ __device__ __forceinline__ void tri_lattice_item(const R* __restrict__ rows, int
                 for (int nu = 0; nu < 4; ++nu)
 #pragma unroll
                     for (int l = 0; l < 4; ++l)
-                        acc[mu * 4 + nu] = fmadd(sr::tri::coef_t(mu, nu, l) > 0 ? a[mu * 4 + l] : -a[mu * 4 + l], b[l * 4 + nu],
-                                                 acc[mu * 4 + nu]);
+                        t[mu * 4 + nu] = fmadd(sr::tri::coef_t(mu, nu, l) > 0 ? a[mu * 4 + l] : -a[mu * 4 + l], b[l * 4 + nu],
+                                               t[mu * 4 + nu]);
         }
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+            for (int nu = 0; nu < 4; ++nu) acc[mu * 4 + nu] = fmadd(sg[mu] * sg[4 + nu], t[mu * 4 + nu], acc[mu * 4 + nu]);
     }
 }
 
