@@ -260,3 +260,52 @@ def test_tri_unsupported_requests():
                         torch.zeros(f64.n_gamma, dtype=torch.float64, device="cuda"))
     assert e.value.status == sr.SR_EUNSUPPORTED
     f64.close()
+
+
+@pytest.mark.parametrize("L,N", [(0, 2), (1, 2), (1, 3)])
+def test_tri_edge_cases_against_oracle(L, N):
+    """Degenerate sizes of the TRI core: range 0 (the on-site vertex only, one table entry), the
+    smallest mesh (2 frequencies: one interval per axis), and a 3-point mesh; three Euler steps
+    and the right-hand side against the oracle in FP64 and FP32-mixed."""
+    model = W.kagome_dm(1.0, 0.5)
+    mesh = O.mesh_exponential(N, 0.1, 5.0)
+    lams = [4.0, 3.0, 2.0, 1.5]
+    of = O.OracleFlowTRI(model, L, mesh)
+    for a, b in zip(lams[:-1], lams[1:]):
+        of.euler(a, b)
+    dg_o, dG_o = of.rhs(1.2)
+    lat = sr.Lattice.from_model(model, L, backend=sr.SR_TRI)
+    for prec, tol in ((sr.SR_FP64, TOL), (sr.SR_FP32_MIXED, 1e-3)):
+        fl = sr.Flow(lat, mesh, lams[0], prec)
+        for b in lams[1:]:
+            fl.step(b, sr.SR_EULER)
+        _, G = fl.get_state()
+        _, G_o = of.get_state()
+        torch.cuda.synchronize()
+        _cmp(G.cpu().numpy().reshape(fl.npair, fl.N, 16, lat.N_s), tri_oracle_to_gpu(of, lat, G_o), tol)
+        _load(fl, lat, of, lams[-1])
+        dg, dG = fl.rhs(1.2)
+        torch.cuda.synchronize()
+        assert _rel(dg.cpu().numpy(), dg_o) < 1e-10
+        _cmp(dG.cpu().numpy().reshape(fl.npair, fl.N, 16, lat.N_s), tri_oracle_to_gpu(of, lat, dG_o), tol)
+        fl.close()
+
+
+def test_tri_adaptive_steps_finite():
+    """Adaptive Dormand-Prince steps of the TRI core reach the target cutoff in FP64 and in
+    FP32-mixed with finite states that agree to 1e-3 of the vertex scale (the two controllers
+    take slightly different step sequences: FP32 rounding enters the embedded error estimate)."""
+    lat = sr.Lattice.from_model(W.kagome_dm(1.0, 0.5), 2, backend=sr.SR_TRI)
+    mesh = O.mesh_exponential(8, 0.02, 20.0)
+    states, counts = [], []
+    for prec in (sr.SR_FP64, sr.SR_FP32_MIXED):
+        fl = sr.Flow(lat, mesh, 10.0, prec)
+        reached = fl.step(0.5, sr.SR_RK_ADAPTIVE, rtol=1e-5, atol=1e-9)
+        assert reached == 0.5
+        _, G = fl.get_state()
+        assert torch.isfinite(G).all()
+        states.append(G.cpu().numpy())
+        counts.append(fl.stats()["n_accept"])
+        fl.close()
+    assert np.abs(states[1] - states[0]).max() / np.abs(states[0]).max() < 1e-3
+    assert abs(counts[0] - counts[1]) <= 0.2 * counts[0]
