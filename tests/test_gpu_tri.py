@@ -309,3 +309,44 @@ def test_tri_adaptive_steps_finite():
         fl.close()
     assert np.abs(states[1] - states[0]).max() / np.abs(states[0]).max() < 1e-3
     assert abs(counts[0] - counts[1]) <= 0.2 * counts[0]
+
+
+@pytest.mark.parametrize("prec,tol", [(sr.SR_FP64, TOL), (sr.SR_FP32_MIXED, 1e-3)])
+def test_tri_full_size_sampled_parity(prec, tol):
+    """The bench's TRI workload at full size (kagome DM, range 7, 32 frequencies: N_s = 34,
+    2543 lattice-sum entries of 64 products each) in the launch configuration the bench times:
+    the initial vertex J/4 with a synthetic self-energy gamma(w) (both sides set it; the
+    self-energy flow of the bare vertex vanishes, the propagators do not), right-hand side at
+    Lambda = 0.9 against the oracle on 48 sampled (site, triple) points, all 16 functions."""
+    cfg = W.config("kagome_dm_L7")
+    mesh = O.mesh_exponential(cfg.n_freq, cfg.w_min, cfg.w_max)
+    gam = 0.2 * np.tanh(mesh) + 0.05 * mesh / (1 + mesh)
+    of = O.OracleFlowTRI(cfg.model, cfg.L, mesh)
+    _, G0 = of.get_state()
+    of.set_state(gam, G0)
+    lat = sr.Lattice.from_model(cfg.model, cfg.L)
+    fl = sr.Flow(lat, mesh, cfg.lam_max, prec)
+    _, Gd = fl.get_state()
+    fl.set_state(cfg.lam_max, torch.tensor(gam, device="cuda"), Gd)
+    dg, dG = fl.rhs(0.9)
+    torch.cuda.synchronize()
+    dG = dG.cpu().numpy().reshape(fl.npair, fl.N, 16, lat.N_s)
+    reps = lat.representatives()
+    rng = np.random.default_rng(9)
+    N = cfg.n_freq
+    pairs = [(s, u) for s in range(N) for u in range(s + 1)]
+    ent, where = [], []
+    for _ in range(48):
+        r = int(rng.integers(0, lat.N_s))
+        p = int(rng.integers(0, len(pairs)))
+        ti = int(rng.integers(0, N))
+        k = of.find(0, reps[r][:3], int(reps[r][3]))
+        si, ui = pairs[p]
+        ent.append((0, k, si, ti, ui))
+        where.append((p, ti, r))
+    got_o = of.rhs_entries(0.9, np.array(ent, dtype=np.int32))
+    scale = np.abs(dG).max()
+    assert scale > 0
+    for (p, ti, r), e in zip(where, got_o):
+        assert np.abs(dG[p, ti, :, r] - tri_real(e, 0)).max() / scale < tol
+    fl.close()
