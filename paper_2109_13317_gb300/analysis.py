@@ -125,3 +125,34 @@ def range_spread(records) -> tuple:
             raise ValueError("records must share their cutoff grid")
     v = np.stack([np.asarray(r[1][:n]) for r in records])
     return lam, (v.max(axis=0) - v.min(axis=0)) / np.abs(v.mean(axis=0))
+
+
+def fourier_components(chi_ij: np.ndarray, dr: np.ndarray, kpts) -> np.ndarray:
+    """Momentum-resolved correlations of every stored spin component (Eq. frg:structurefactor
+    for one component instead of the trace): out[k, c] = (1/N_b) sum_{b, j} exp(i k (r_b - r_j))
+    chi^c_{b j} with chi_ij of shape (N_b, N_tot, n_c) and dr the matching (N_b, N_tot, 3)
+    displacements r_b - r_j.  Complex: for a TRI model chi^{mu nu}_{ij} and chi^{mu nu}_{ji}
+    differ (e.g. the antisymmetric part from DM couplings), so the mu != nu components carry an
+    imaginary part; the sum of the xx, yy, zz components is the real structure factor."""
+    c = np.asarray(chi_ij)
+    d = np.asarray(dr, dtype=np.float64)
+    kp = np.asarray(kpts, dtype=np.float64).reshape(-1, 3)
+    ph = np.exp(1j * np.einsum("ka,bja->kbj", kp, d))
+    return np.einsum("kbj,bjc->kc", ph, c) / c.shape[0]
+
+
+def chi_displacements(flow: Flow) -> np.ndarray:
+    """r_b - r_j (shape (N_b, N_tot, 3)) of the flow's correlation pairs, in the order of the
+    chi_ij array that `Flow.measure` returns."""
+    lat = flow.lattice
+    sites = flow.chi_sites()
+    pos = (sites[..., 0:1] * lat.prim[0] + sites[..., 1:2] * lat.prim[1] + sites[..., 2:3] * lat.prim[2] +
+           lat.basis[sites[..., 3]])
+    return lat.basis[:, None, :] - pos
+
+
+def structure_factor_components(flow: Flow, kpts) -> np.ndarray:
+    """`fourier_components` of the flow's current correlations: complex (n_k, n_c), component
+    index as in the state layout (TRI: mu * 4 + nu)."""
+    _, chi_ij = flow.measure(None, want_ij=True)
+    return fourier_components(chi_ij.cpu().numpy(), chi_displacements(flow), kpts)

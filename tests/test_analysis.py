@@ -61,3 +61,32 @@ def test_range_spread():
     np.testing.assert_allclose(sp, [0.0, 0.0, 0.6 / 3.0, 0.4 / (12.4 / 3)])
     with pytest.raises(ValueError):
         range_spread([(lam, lam), (lam * 1.01, lam)])
+
+
+def test_fourier_components_against_oracle_structure_factor():
+    """The host Fourier sum of the oracle's TRI correlations: the xx + yy + zz components give
+    the oracle's structure factor (real), and chi^{xy}(k) = conj(chi^{yx}(k)) (chi^{mu nu}_{ij} =
+    chi^{nu mu}_{ji})."""
+    import workloads as W
+    from oracle import oracle as O
+    from paper_2109_13317_gb300.analysis import fourier_components
+    mesh = O.mesh_exponential(6, 0.05, 10.0)
+    of = O.OracleFlowTRI(W.kagome_dm(1.0, 0.5), 2, mesh)
+    of.euler(5.0, 3.0)
+    chi = of.chi(2.0)
+    nb = of.nb
+    nt = len(chi[0])
+    c = np.zeros((nb, nt, 16), complex)
+    dr = np.zeros((nb, nt, 3))
+    for b in range(nb):
+        c[b] = chi[b]
+        for k, s in enumerate(of.sites(b)):
+            dr[b, k] = of.basis[b] - of.position(s)
+    kp = np.array([[0.0, 0.0, 0.0], [1.1, -0.3, 0.0], [np.pi, 0.7, 0.0]])
+    F = fourier_components(c, dr, kp)
+    np.testing.assert_allclose((F[:, 5] + F[:, 10] + F[:, 15]).real, of.chi_k(2.0, kp, chi), rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose((F[:, 5] + F[:, 10] + F[:, 15]).imag, 0.0, atol=1e-14)
+    np.testing.assert_allclose(F[:, 6], np.conj(F[:, 9]), rtol=1e-12, atol=1e-15)
+    # the DM couplings leave an antisymmetric xy part in real space (its Fourier sum cancels
+    # here: site inversion maps the up onto the down triangles with the same DM vectors)
+    assert np.abs(c[..., 6] - c[..., 9]).max() > 1e-6

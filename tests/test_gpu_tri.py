@@ -350,3 +350,18 @@ def test_tri_full_size_sampled_parity(prec, tol):
     for (p, ti, r), e in zip(where, got_o):
         assert np.abs(dG[p, ti, :, r] - tri_real(e, 0)).max() / scale < tol
     fl.close()
+
+
+def test_tri_structure_factor_components():
+    """analysis.structure_factor_components on a TRI flow: the xx + yy + zz components equal the
+    library's chi(k), and chi^{xy}(k) = conj(chi^{yx}(k))."""
+    from paper_2109_13317_gb300.analysis import structure_factor_components
+    lat = sr.Lattice.from_model(W.kagome_dm(1.0, 0.5), 2, backend=sr.SR_TRI)
+    fl = sr.Flow(lat, O.mesh_exponential(6, 0.05, 10.0), 5.0, sr.SR_FP64)
+    fl.step(3.0, sr.SR_EULER)
+    kp = np.array([[0.0, 0.0, 0.0], [1.1, -0.3, 0.0], [np.pi, 0.7, 0.0]])
+    F = structure_factor_components(fl, kp)
+    ck, _ = fl.measure(kp, want_ij=False)
+    np.testing.assert_allclose((F[:, 5] + F[:, 10] + F[:, 15]).real, ck, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(F[:, 6], np.conj(F[:, 9]), rtol=1e-12, atol=1e-15)
+    fl.close()
