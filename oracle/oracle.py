@@ -105,6 +105,8 @@ def load():
         lib.or_tri_rhs_point.argtypes = [vp, C.c_int, _ip, C.c_int, C.c_double, C.c_double, C.c_double, _dp]
         lib.or_tri_euler_step.argtypes = [vp, C.c_double, C.c_double]
         lib.or_tri_rhs_entries.argtypes = [vp, C.c_int, _ip, _dp]
+        lib.or_tri_dp54_step.restype = C.c_double
+        lib.or_tri_dp54_step.argtypes = [vp, C.c_double, C.c_double, C.c_double, C.c_double]
         lib.or_tri_chi.argtypes = [vp, C.c_double, _dp]
         _lib = lib
         return lib
@@ -417,8 +419,8 @@ class OracleFlowTRI(OracleFlow):
     def euler(self, lam: float, lam_next: float):
         self.lib.or_tri_euler_step(self.st, lam, lam_next)
 
-    def dp54(self, lam, lam_next, rtol, atol):  # pragma: no cover - not provided by the TRI core
-        raise NotImplementedError
+    def dp54(self, lam: float, lam_next: float, rtol: float, atol: float) -> float:
+        return self.lib.or_tri_dp54_step(self.st, lam, lam_next, rtol, atol)
 
     def chi(self, lam: float):
         """Per basis b: complex array (nsite_b, 16) of chi^{mu nu}_{b k}."""

@@ -1292,6 +1292,55 @@ void or_tri_euler_step(OrStateT* st, double lam, double lam_next) {
     free(dg); free(dG);
 }
 
+/* Dormand-Prince 5(4) step of the TRI state (same tableau, stage sums and normwise error as
+ * or_dp54_step; the complex vertex enters the norm through its real and imaginary parts). */
+double or_tri_dp54_step(OrStateT* st, double lam, double lam_next, double rtol, double atol) {
+    const double h = lam_next - lam;
+    const int N = st->f.N;
+    const size_t M = 2 * st->ntot;
+    double* G = (double*)st->G;
+    double* y0g = (double*)malloc(sizeof(double) * N);
+    double* y0G = (double*)malloc(sizeof(double) * M);
+    memcpy(y0g, st->f.gam, sizeof(double) * N);
+    memcpy(y0G, G, sizeof(double) * M);
+    double* kg[7]; double* kG[7];
+    for (int i = 0; i < 7; ++i) { kg[i] = (double*)malloc(sizeof(double) * N); kG[i] = (double*)malloc(sizeof(double) * M); }
+    for (int s = 0; s < 7; ++s) {
+        for (int i = 0; i < N; ++i) {
+            double acc = 0.0;
+            for (int r = 0; r < s; ++r) acc += DP_A[s][r] * kg[r][i];
+            st->f.gam[i] = y0g[i] + h * acc;
+        }
+        for (size_t i = 0; i < M; ++i) {
+            double acc = 0.0;
+            for (int r = 0; r < s; ++r) acc += DP_A[s][r] * kG[r][i];
+            G[i] = y0G[i] + h * acc;
+        }
+        or_tri_rhs(st, lam + DP_C[s] * h, kg[s], kG[s]);
+    }
+    double emax = 0.0, ymax = 0.0;
+    for (int i = 0; i < N; ++i) {
+        double y5 = 0.0, y4 = 0.0;
+        for (int r = 0; r < 7; ++r) { y5 += DP_B5[r] * kg[r][i]; y4 += DP_B4[r] * kg[r][i]; }
+        double yn = y0g[i] + h * y5;
+        emax = fmax(emax, fabs(h * (y5 - y4)));
+        ymax = fmax(ymax, fmax(fabs(y0g[i]), fabs(yn)));
+        st->f.gam[i] = yn;
+    }
+    for (size_t i = 0; i < M; ++i) {
+        double y5 = 0.0, y4 = 0.0;
+        for (int r = 0; r < 7; ++r) { y5 += DP_B5[r] * kG[r][i]; y4 += DP_B4[r] * kG[r][i]; }
+        double yn = y0G[i] + h * y5;
+        emax = fmax(emax, fabs(h * (y5 - y4)));
+        ymax = fmax(ymax, fmax(fabs(y0G[i]), fabs(yn)));
+        G[i] = yn;
+    }
+    double err = emax / (atol + rtol * ymax);
+    for (int i = 0; i < 7; ++i) { free(kg[i]); free(kG[i]); }
+    free(y0g); free(y0G);
+    return err;
+}
+
 /* chi^{mu nu}_{b k}, all 16 components (complex, interleaved): out[((off_b + k) * 16 + o) * 2].
  * Same quadrature as or_chi (C9); the bubble term carries tr(sigma^mu sigma^nu) / 2 =
  * delta_{mu nu} and is local (C8). */

@@ -365,3 +365,26 @@ def test_tri_structure_factor_components():
     np.testing.assert_allclose((F[:, 5] + F[:, 10] + F[:, 15]).real, ck, rtol=1e-12, atol=1e-15)
     np.testing.assert_allclose(F[:, 6], np.conj(F[:, 9]), rtol=1e-12, atol=1e-15)
     fl.close()
+
+
+def test_tri_rk_fixed_step_parity():
+    """One Dormand-Prince 5(4) step of the TRI core (SR_RK_FIXED) against the oracle's TRI step:
+    state within 1e-10 and the same normwise error estimate."""
+    model = W.kagome_dm(1.0, 0.5)
+    L, mesh = 1, O.mesh_exponential(5, 0.05, 10.0)
+    of = O.OracleFlowTRI(model, L, mesh)
+    for a, b in ((6.0, 4.0), (4.0, 3.0)):
+        of.euler(a, b)
+    lat = sr.Lattice.from_model(model, L, backend=sr.SR_TRI)
+    fl = sr.Flow(lat, mesh, 3.0, sr.SR_FP64)
+    _load(fl, lat, of, 3.0)
+    err_o = of.dp54(3.0, 2.2, 1e-6, 1e-10)
+    fl.step(2.2, sr.SR_RK_FIXED, 1e-6, 1e-10)
+    err = fl.stats()["last_err"]
+    g, G = fl.get_state()
+    torch.cuda.synchronize()
+    g_o, G_o = of.get_state()
+    assert _rel(g.cpu().numpy(), g_o) < TOL
+    _cmp(G.cpu().numpy().reshape(fl.npair, fl.N, 16, lat.N_s), tri_oracle_to_gpu(of, lat, G_o))
+    assert abs(err - err_o) <= 1e-6 * err_o
+    fl.close()

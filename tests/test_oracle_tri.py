@@ -299,3 +299,16 @@ def test_tri_chi_bare_vertex_closed_form():
             assert np.abs(c[1:, 1:].imag).max() == 0.0
             assert np.abs(c[0, :]).max() < 1e-16 and np.abs(c[:, 0]).max() < 1e-16
     assert np.abs(model.couplings[0].M - model.couplings[0].M.T).max() > 0.9   # DM part present
+
+
+def test_tri_dp54_step_matches_diagonal_oracle(hk_pair):
+    """The TRI core's Dormand-Prince step on a Kitaev-like model equals the spin-diagonal
+    oracle's step (same tableau and normwise error) on the diagonal functions."""
+    d, t = hk_pair
+    ed = d.dp54(2.5, 2.1, 1e-6, 1e-10)
+    et = t.dp54(2.5, 2.1, 1e-6, 1e-10)
+    np.testing.assert_allclose(et, ed, rtol=1e-10)
+    _, Gd = d.get_state()
+    _, Gt = t.get_state()
+    for b in range(d.nb):
+        np.testing.assert_allclose(t.block(Gt, b)[:, [0, 5, 10, 15]].real, d.block(Gd, b), rtol=1e-12, atol=1e-16)
