@@ -25,8 +25,10 @@
  *
  * Storage is translation-only: for every basis site b of the home cell, the vertex is
  * kept for every lattice site j within bond distance L of b (Sec. 4.1 truncation), with
- * no point-group reduction.  Only spin-diagonal basis functions Gamma^{cc}, c = 0..3,
- * are stored (the SU(2) and XYZ cores of Sec. 3); off-diagonal couplings are rejected.
+ * no point-group reduction.  The first part keeps the spin-diagonal basis functions
+ * Gamma^{cc}, c = 0..3 (the SU(2) and XYZ cores of Sec. 3); the section "General
+ * time-reversal-invariant core" at the end keeps all 16 Gamma^{mu nu} as complex numbers
+ * (the TRI core, any two-spin coupling).
  *
  * Readings of points the paper leaves open (same list as the design notes):
  *   C1  Sigma = -i gamma with gamma real and odd, so G(w) = 1/(i(w + gamma(w))).
