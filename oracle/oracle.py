@@ -5,7 +5,8 @@ the benchmark.  Builds the C file with gcc into ``oracle/_build`` on first use.
 
 The oracle keeps the vertex in translation-only storage: for every basis site b of the home
 cell and every site k within bond distance L of b, the spin-diagonal basis functions
-Gamma^{cc}(s, t, u), c = 0..3, on the octant s >= u (layout [b][k][c][pair(s,u)][t]).
+Gamma^{cc}(s, t, u), c = 0..3, on the octant s >= u (layout [b][k][c][pair(s,u)][t]);
+`OracleFlowTRI` keeps all 16 Gamma^{mu nu} as complex numbers ([b][k][mu nu][pair][t]).
 """
 from __future__ import annotations
 
