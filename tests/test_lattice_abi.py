@@ -187,3 +187,33 @@ def test_frequency_mesh_matches_oracle():
     a = sr.sr_frequency_mesh_exponential(48, 0.001, 100.0)
     b = O.mesh_exponential(48, 0.001, 100.0)
     np.testing.assert_allclose(a, b, rtol=1e-15)
+
+
+@pytest.mark.parametrize("model,L", [(W.kagome_dm(1.0, 0.5), 4), (W.honeycomb_kitaev_gamma(0.1, -1.0, 0.5), 4),
+                                     (W.rotated(W.kagome_dm(1.0, 0.3), np.eye(3)[[2, 0, 1]]), 3)])
+def test_tri_component_maps_are_signed_rotations(model, L):
+    """Every TRI pair map is Gamma^{mu nu} -> s(mu) s(nu) Gamma^{p(mu) p(nu)} with p a permutation
+    fixing 0 and (p, s) a proper rotation among the signed permutations (Sec. 4.1 symmetries
+    combined with a global spin rotation); the kernels' lattice sum relies on this factorised
+    form of the signs."""
+    lat = sr.Lattice.from_model(model, L, backend=sr.SR_TRI)
+    of = O.OracleFlowTRI(model, L, O.mesh_exponential(2, 0.1, 1.0))
+    n = 0
+    for b in range(of.nb):
+        for s in of.sites(b):
+            r, comp, sign = lat.map_pair_components([0, 0, 0, b], s)
+            assert r >= 0
+            p = [comp[5 * m] // 4 for m in range(4)]            # diagonal: (m, m) -> (p(m), p(m))
+            assert p[0] == 0 and sorted(p) == [0, 1, 2, 3]
+            # signs: s(0) = 1, s(m) from the (0, m) functions
+            sg = [1] + [int(sign[m]) for m in range(1, 4)]
+            for mu in range(4):
+                for nu in range(4):
+                    assert comp[mu * 4 + nu] == p[mu] * 4 + p[nu]
+                    assert sign[mu * 4 + nu] == sg[mu] * sg[nu]
+            R = np.zeros((3, 3))
+            for m in range(1, 4):
+                R[p[m] - 1, m - 1] = sg[m]
+            assert abs(np.linalg.det(R) - 1.0) < 1e-12
+            n += 1
+    assert n > 0
