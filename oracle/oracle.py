@@ -100,6 +100,10 @@ def load():
         lib.or_tri_state_set.argtypes = [vp, _dp, _dp]
         lib.or_tri_state_init.argtypes = [vp]
         lib.or_tri_lookup.argtypes = [vp, C.c_int, _ip, C.c_int, C.c_double, C.c_double, C.c_double, _dp]
+        lib.or_sigma_basis_spread.restype = C.c_double
+        lib.or_sigma_basis_spread.argtypes = []
+        lib.or_sigma_basis_spread_reset.restype = None
+        lib.or_sigma_basis_spread_reset.argtypes = []
         lib.or_tri_sigma_imag.restype = C.c_double
         lib.or_tri_rhs.argtypes = [vp, C.c_double, _dp, _dp]
         lib.or_tri_rhs_prepare.argtypes = [vp, C.c_double, _dp]
@@ -309,6 +313,16 @@ class OracleFlow:
                 dr = rb - self.position(s)
                 acc += np.cos(kpts @ dr) * chi[b][k, 1:].sum()
         return acc / self.nb
+
+    @staticmethod
+    def sigma_basis_spread(reset: bool = False) -> float:
+        """Largest relative spread of the self-energy flow across basis sites seen so far
+        (the oracle sets dgamma to NaN when it exceeds 1e-10: inequivalent sites)."""
+        lib = load()
+        v = lib.or_sigma_basis_spread()
+        if reset:
+            lib.or_sigma_basis_spread_reset()
+        return v
 
     @staticmethod
     def set_threads(n: int):

@@ -686,10 +686,42 @@ static void gamma_rhs_at(const OrState* st, int b1, const int d2[3], int b2, dou
     }
 }
 
+/* The state keeps one self-energy for all sites, which presumes that every basis site is
+ * equivalent (Sec. 4.1: the vertex is stored relative to a reference site; the self-energy is
+ * site-independent by the same symmetry).  The flow of Sigma is therefore evaluated at every
+ * basis site; where the sites disagree beyond rounding the lattice has inequivalent sites, the
+ * largest relative difference is recorded and dgamma is set to NaN, so that no result is
+ * silently computed with basis site 0's self-energy. */
+static double g_sigma_basis_spread = 0.0;   /* largest relative spread seen across basis sites */
+#define OR_BASIS_TOL 1e-10
+
+static double basis_spread(const double* ref, const double* other, int N) {
+    double num = 0.0, den = 0.0;
+    for (int i = 0; i < N; ++i) {
+        if (fabs(other[i] - ref[i]) > num) num = fabs(other[i] - ref[i]);
+        if (fabs(ref[i]) > den) den = fabs(ref[i]);
+    }
+    return num == 0.0 ? 0.0 : num / (den > 0.0 ? den : 1e-300);
+}
+
 static void compute_dgam(OrState* st, double lam) {
     st->lam = lam;
     for (int i = 0; i < st->N; ++i) st->dgam[i] = sigma_rhs_at(st, 0, st->w[i], lam);
+    double* other = (double*)malloc(sizeof(double) * st->N);
+    for (int b = 1; b < st->la->nb; ++b) {
+        for (int i = 0; i < st->N; ++i) other[i] = sigma_rhs_at(st, b, st->w[i], lam);
+        double d = basis_spread(st->dgam, other, st->N);
+        if (d > g_sigma_basis_spread) g_sigma_basis_spread = d;
+        if (d > OR_BASIS_TOL)
+            for (int i = 0; i < st->N; ++i) st->dgam[i] = NAN;
+    }
+    free(other);
 }
+
+/* Largest relative spread of the self-energy flow across basis sites seen so far (reset by
+ * or_sigma_basis_spread_reset). */
+double or_sigma_basis_spread(void) { return g_sigma_basis_spread; }
+void or_sigma_basis_spread_reset(void) { g_sigma_basis_spread = 0.0; }
 
 /* Full right-hand side at cutoff lam: dgamma (N) and dGamma (state layout). */
 void or_rhs(OrState* st, double lam, double* dgam, double* dG) {
@@ -1217,9 +1249,19 @@ static void gamma_rhs_atT(const OrStateT* st, int b1, const int d2[3], int b2, d
     }
 }
 
+/* As compute_dgam: the self-energy flow at every basis site, NaN if they disagree. */
 static void compute_dgamT(OrStateT* st, double lam) {
     st->f.lam = lam;
     for (int i = 0; i < st->f.N; ++i) st->f.dgam[i] = sigma_rhs_atT(st, 0, st->f.w[i], lam);
+    double* other = (double*)malloc(sizeof(double) * st->f.N);
+    for (int b = 1; b < st->f.la->nb; ++b) {
+        for (int i = 0; i < st->f.N; ++i) other[i] = sigma_rhs_atT(st, b, st->f.w[i], lam);
+        double d = basis_spread(st->f.dgam, other, st->f.N);
+        if (d > g_sigma_basis_spread) g_sigma_basis_spread = d;
+        if (d > OR_BASIS_TOL)
+            for (int i = 0; i < st->f.N; ++i) st->f.dgam[i] = NAN;
+    }
+    free(other);
 }
 
 /* Full right-hand side: dgamma (N) and dGamma (state layout, interleaved re / im). */

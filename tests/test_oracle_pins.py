@@ -428,6 +428,28 @@ def evolved_square():
     return f
 
 
+def test_self_energy_flow_needs_equivalent_basis_sites():
+    """The oracle keeps one self-energy for all sites (Sec. 4.1 reduction to a reference site),
+    so it evaluates the self-energy flow at every basis site: on lattices whose sites are all
+    equivalent (kagome, honeycomb) they agree to rounding; on the Lieb lattice (corner sites
+    with four neighbours, edge sites with two) they differ, and the oracle returns NaN instead
+    of basis site 0's flow."""
+    mesh = O.mesh_exponential(5, 0.05, 10.0)
+    O.OracleFlow.sigma_basis_spread(reset=True)
+    for cell in (W.kagome(), W.honeycomb()):
+        f = _evolved(W.nn_heisenberg(cell), 2, mesh, [8.0, 4.0, 2.0])
+        dg, _ = f.rhs(1.3)
+        assert np.all(np.isfinite(dg)) and np.abs(dg).max() > 0
+    assert O.OracleFlow.sigma_basis_spread(reset=True) < 1e-12
+    lieb = W.UnitCell("lieb", np.eye(3), np.array([[0, 0, 0], [0.5, 0, 0], [0, 0.5, 0]], dtype=float),
+                      [(0, 1, 0, 0, 0), (1, 0, 1, 0, 0), (0, 2, 0, 0, 0), (2, 0, 0, 1, 0)])
+    f = O.OracleFlow(W.nn_heisenberg(lieb), 2, mesh)
+    f.euler(8.0, 4.0)   # the bare vertex has no self-energy flow; the first step makes one
+    dg = f.prepare(2.0)
+    assert np.all(np.isnan(dg))
+    assert O.OracleFlow.sigma_basis_spread(reset=True) > 1e-3
+
+
 def test_self_energy_flow_is_odd(evolved_square):
     f = evolved_square
     for w in (0.03, 0.5, 1.7, 9.0, 30.0):
