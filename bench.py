@@ -49,6 +49,15 @@ def _args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-flow", action="store_true", help="skip the full adaptive Lambda flow")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched coupling sweep")
+    ap.add_argument("--profile-rhs", action="store_true",
+                    help="profiling case: two Euler steps of the workload, then one right-hand side, and exit")
+    ap.add_argument("--n-freq", type=int, default=0, help="profiling case: override the frequency count")
+    ap.add_argument("--oracle-flow", action="store_true",
+                    help="time the CPU oracle's whole Euler flow of the workload (all host cores), print one "
+                         "JSON line and exit; --oracle-budget bounds it (the rest is extrapolated per step)")
+    ap.add_argument("--oracle-budget", type=float, default=600.0, help="seconds for --oracle-flow")
+    ap.add_argument("--profile-lambda", type=float, default=0.0,
+                    help="profiling case: cutoff of the profiled right-hand side (default 0.1 Lambda_max)")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=["square_j1j2_L7", "square_j1_L3", "pyrochlore_L6", "honeycomb_hk_L5", "kagome_dm_L7"],
                     help="configuration to measure (the default is the headline workload)")
@@ -249,9 +258,8 @@ def _oracle_sampler(cfg, seed: int):
             of.rhs_entries(0.9, ent)
             return 16 * m, time.perf_counter() - t0
         return run, "initial vertex J/4 with a synthetic self-energy at Lambda=0.9 (16 functions per sampled pair and triple)"
-    from tests.helpers import synthetic_state
     of = O.OracleFlow(cfg.model, cfg.L, mesh)
-    gam, G = synthetic_state(of, cfg.model, seed=3)
+    gam, G = W.synthetic_state(of, cfg.model, seed=3)
     of.set_state(gam, G)
 
     def run(m):
@@ -279,11 +287,21 @@ def _cpu_baseline(cfg, target_s: float = 12.0):
     e0, dt = run(n0)
     m = max(n0, int(n0 * target_s / max(dt, 1e-3)))
     e, dt = run(m)
+    cores = O.OracleFlow.threads()
+    # the same oracle on one core (a smaller sample of the same kind, ~target_s / 3)
+    O.OracleFlow.set_threads(1)
+    try:
+        m1 = max(8, int(m * (target_s / 3) / target_s / max(cores, 1)))
+        e1, dt1 = run(m1)
+    finally:
+        O.OracleFlow.set_threads(cores)
     # the oracle evaluates every symmetry-equivalent pair; a stored entry of the oracle's
     # translation-only vertex is one equation, as for the GPU's reduced vertex
-    return {"value": e / dt, "unit": UNIT, "cores": O.OracleFlow.threads(), "kind": "oracle",
+    return {"value": e / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{e} random stored vertex entries (RHS of each, incl. self-energy flow) of the "
-                      f"{cfg.name} workload, {state}; {dt:.1f} s"}
+                      f"{cfg.name} workload, {state}; {dt:.1f} s",
+            "single_thread": {"value": e1 / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"{e1} random stored entries of the same kind; {dt1:.1f} s"}}
 
 
 def run_reference(args):
@@ -649,9 +667,22 @@ def run_ours(args):
         e32["speedup_vs_fp64"] = e64["seconds"] / e32["seconds"]
         ff["euler"] = {"fp64": e64, "fp32_mixed": e32}
         if cfg.method == "rk":
-            a64, _, _ = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP64, kgrid, "rk", budget_s=110.0)
+            a64, cma, cka = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP64, kgrid, "rk", budget_s=110.0)
             a32, _, _ = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP32_MIXED, kgrid, "rk", budget_s=30.0)
             ff["adaptive"] = {"fp64": a64, "fp32_mixed": a32}
+            # what the adaptive flow's accuracy buys: the Euler flows' distance from it (chi_max at
+            # every output cutoff both reached, chi(k) at the end); Euler's error falls with the step
+            e4, cm4, ck4 = _full_flow(sr, torch, cfg, lat, mesh, sr.SR_FP64, kgrid, "euler", n_steps=4 * n_eu,
+                                      budget_s=1e9)
+            acc = {"reference": "adaptive Dormand-Prince FP64 flow (rtol %g)" % cfg.rtol,
+                   "euler_4x_steps_fp64_seconds": e4["seconds"]}
+            for name, cm, ck in (("euler_fp64", cm64, ck64), ("euler_fp32_mixed", cm32, ck32),
+                                 ("euler_4x_steps_fp64", cm4, ck4)):
+                n_cmp = min(len(cm), len(cma))
+                acc[name] = {"chi_max_rel_diff_all_outputs": float(np.abs(cm[:n_cmp] - cma[:n_cmp]).max() / np.abs(cma[:n_cmp]).max()),
+                             "chi_k_rel_diff_final": float(np.abs(ck - cka).max() / np.abs(cka).max())
+                             if a64["complete"] else None}
+            ff["accuracy_vs_adaptive"] = acc
         extra["full_flow"] = ff
         if cfg.name == "honeycomb_hk_L5":
             extra["gradient"] = _gradient_timing(sr, torch, cfg, mesh)
@@ -704,9 +735,69 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def profile_rhs(args):
+    """One right-hand side of the workload, for profiler captures of the vertex kernels: the
+    flow (optionally with another number of frequencies) takes two Euler steps (two
+    vertex-kernel launches) and evaluates one right-hand side (the third launch), so that a
+    capture skips two launches of the vertex kernel and takes one.  The right-hand side is at
+    --profile-lambda (default 0.1 Lambda_max), the steps at 4 and 1.6 times that cutoff (the
+    work per launch depends on the cutoff through the integration nodes, not on the state)."""
+    import torch
+    import paper_2109_13317_gb300 as sr
+    cfg = W.config(args.workload)
+    n = args.n_freq or cfg.n_freq
+    lat = sr.Lattice.from_model(cfg.model, cfg.L)
+    mesh = sr.sr_frequency_mesh_exponential(n, cfg.w_min, cfg.w_max)
+    prec = sr.SR_FP64 if args.precision == "fp64" else sr.SR_FP32_MIXED
+    lam = args.profile_lambda or 0.1 * cfg.lam_max
+    fl = sr.Flow(lat, mesh, 10.0 * lam, prec)
+    fl.step(4.0 * lam, sr.SR_EULER)
+    fl.step(1.6 * lam, sr.SR_EULER)
+    fl.rhs(lam)
+    torch.cuda.synchronize()
+    print(f"{cfg.name}: N_s={lat.N_s} P={lat.P} n_freq={n} entries={fl.n_gamma} precision={args.precision} "
+          f"Lambda={lam}")
+    fl.close()
+
+
+def oracle_flow(args):
+    """The CPU oracle's own Euler flow of the workload on all host cores (the configuration's
+    log-spaced cutoff steps from Lambda_max to Lambda_min, chi(k) on the 64 x 64 grid at the
+    end): whole-flow seconds when it fits the budget, else the seconds per step of the steps
+    taken and the whole flow extrapolated from them (stated in the line)."""
+    from oracle import oracle as O
+    cfg = W.config(args.workload)
+    mesh = O.mesh_exponential(cfg.n_freq, cfg.w_min, cfg.w_max)
+    tri = cfg.model.backend == "TRI"
+    of = (O.OracleFlowTRI if tri else O.OracleFlow)(cfg.model, cfg.L, mesh)
+    n_steps = cfg.n_steps if cfg.method == "euler" else 200
+    lams = W.lambda_list(cfg.lam_max, cfg.lam_min, n_steps)
+    t0 = time.perf_counter()
+    done = 0
+    for a, b in zip(lams[:-1], lams[1:]):
+        of.euler(float(a), float(b))
+        done += 1
+        if time.perf_counter() - t0 > args.oracle_budget:
+            break
+    dt = time.perf_counter() - t0
+    line = {"impl": "oracle", "workload": cfg.name, "metric": "full Lambda-flow time", "unit": "s",
+            "method": f"Euler, {n_steps} log steps {cfg.lam_max} -> {cfg.lam_min}", "cores": O.OracleFlow.threads(),
+            "steps_done": done, "seconds": dt, "seconds_per_step": dt / done,
+            "complete": done == n_steps, "full_flow_seconds": dt if done == n_steps else dt / done * n_steps,
+            "full_flow_seconds_kind": "measured" if done == n_steps else "extrapolated from the steps done",
+            "entries": int(of.size)}
+    if done == n_steps:
+        line["chi_max_final"] = float(np.max(of.chi_k(float(lams[-1]), _kgrid(64))))
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
-    if args.impl == "reference":
+    if args.oracle_flow:
+        oracle_flow(args)
+    elif args.profile_rhs:
+        profile_rhs(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -147,6 +147,24 @@ sr_status sr_flow_rhs(sr_flow* flow, double lambda, double* d_dsigma, double* d_
 sr_status sr_flow_step(sr_flow* flow, double lambda_next, int method, double rtol, double atol,
                        double* lambda_reached);
 
+/* Right-hand side restricted to the stored (s, u) pairs pair_begin .. pair_end - 1, the unit
+ * of work the paper distributes over compute nodes (Sec. 4.4: all t, components and sites of
+ * one (s, u) pair form a superblock), for flows sharded over several GPUs that all hold the
+ * whole state.  dgamma/dLambda of every frequency goes to d_dsigma (device, N doubles; each
+ * GPU recomputes it instead of broadcasting it); dGamma/dLambda of the pairs' entries goes to
+ * d_dgamma (device, state layout) at their own positions, entries ((p N + t) n_c + c) N_s + r
+ * for pair_begin <= p < pair_end, one contiguous slice; the rest of d_dgamma is not written.
+ * Asynchronous on the flow's stream.  Errors: SR_EINVAL (range outside [0, N (N + 1) / 2],
+ * null outputs). */
+sr_status sr_flow_rhs_pairs(sr_flow* flow, double lambda, int pair_begin, int pair_end, double* d_dsigma,
+                            double* d_dgamma);
+
+/* Euler step (Sec. 4.3) with a right-hand side supplied by the caller, e.g. assembled from the
+ * slices of several GPUs: y <- y - (lambda - lambda_next) f, f = (d_dsigma, d_dgamma) (device,
+ * state layout); the cutoff becomes lambda_next.  Synchronises once (non-finite check).
+ * Errors: SR_EINVAL (lambda_next outside (0, lambda)), SR_ENONFINITE. */
+sr_status sr_flow_advance(sr_flow* flow, double lambda_next, const double* d_dsigma, const double* d_dgamma);
+
 /* Largest number of attempted steps one SR_RK_ADAPTIVE call may take (default 10^6); when it
  * is exceeded the call returns SR_ETIMEOUT with the state and *lambda_reached at the last
  * accepted step. */
@@ -166,21 +184,22 @@ sr_status sr_flow_stats(const sr_flow* flow, double* last_err, long* n_rhs, long
 sr_status sr_measure_susceptibility(sr_flow* flow, int n_k, const double* k_xyz, double* chi_k,
                                     double* chi_ij);
 
-/* Allocation-free variant of sr_measure_susceptibility for callers that must not allocate
- * device memory: code that runs while a CUDA stream is being captured into a graph (where
- * cudaMalloc is not permitted), and hosts whose device memory is owned entirely by another
- * framework's pool or fixed budget.  It computes the structure factor chi(k) of the
- * current state into a caller-provided device array, reading the momenta from a
- * caller-provided device array; the intermediate chi_ij pair table is kept in one
- * file-scope device array of SR_CHI_STATIC_MAX doubles (2 MiB) that every GPU loading the
- * library holds until exit.  The paper has no counterpart to this entry point.
+/* Allocation-free variant of sr_measure_susceptibility, for callers that must not allocate
+ * device memory while they run: hosts whose device memory is owned entirely by another
+ * framework's pool or by a fixed budget, and code paths where a cudaMalloc (which may
+ * synchronise the device or fail under memory pressure) is not acceptable.  It computes the
+ * structure factor chi(k) of the current state into a caller-provided device array, reading
+ * the momenta from a caller-provided device array; the intermediate chi_ij pair table is kept
+ * in one file-scope device array of SR_CHI_STATIC_MAX doubles (2 MiB) that every GPU loading
+ * the library holds until exit.  The paper has no counterpart to this entry point.
  *   d_k_xyz: device, n_k x 3 momenta;  d_chi_k: device, n_k outputs.
- * Requires N_basis x N_tot x n_comp <= SR_CHI_STATIC_MAX, else SR_EINVAL.  The first call
- * on a device looks up the array's device address (cudaGetSymbolAddress) with that device
- * current: make that first call before any stream capture.  The call is asynchronous on
- * the flow's stream and allocates nothing.  All calls share the one array (each overwrites
- * every entry it reads), so calls whose kernels overlap on the GPU (different streams, no
- * ordering between them) race and must be avoided. */
+ * Requires N_basis x N_tot x n_comp <= SR_CHI_STATIC_MAX, else SR_EINVAL (nothing is launched
+ * and d_chi_k is left untouched).  The flow's device must be the current device (SR_EINVAL
+ * otherwise).  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture.  The call is asynchronous on the flow's stream and allocates nothing.  All calls
+ * share the one array (each overwrites every entry it reads), so calls whose kernels overlap
+ * on the GPU (different streams, no ordering between them) race and must be avoided. */
 #define SR_CHI_STATIC_MAX 262144
 sr_status sr_measure_susceptibility_static(sr_flow* flow, int n_k, const double* d_k_xyz, double* d_chi_k);
 
@@ -252,6 +271,20 @@ sr_status sr_flow_step_adjoint(sr_flow* flow, double lambda_from, double lambda_
  * respect to the state.  k_xyz (host, 3 n_k) and chi_bar (host, n_k) are copied; synchronises. */
 sr_status sr_measure_susceptibility_adjoint(sr_flow* flow, int n_k, const double* k_xyz, const double* chi_bar,
                                             double* d_bar_sigma, double* d_bar_gamma);
+
+/* Couplings linear in parameters theta: M_c = sum_p theta_p B_{p,c} for the n_couplings
+ * interaction matrices of Sec. 5.4 (theta: host n_par; B: host n_par x n_couplings x 3 x 3
+ * row-major; M: host out n_couplings x 3 x 3).  Errors: SR_EINVAL. */
+sr_status sr_couplings_linear(int n_par, const double* theta, int n_couplings, const double* B, double* M);
+
+/* Gradient of a scalar through the initial vertex Gamma_init = J / 4 (Sec. 3,
+ * Eq. frg:parametrizationInitial): grad_p = sum over stored entries of (d Gamma_init /
+ * d theta_p) bar_gamma, for coupling derivatives dM (host, n_par x n_couplings x 3 x 3 in the
+ * order the couplings were given to sr_lattice_create; n_par <= 2) and the adjoint of the
+ * initial state bar_gamma (device, state layout, e.g. from sr_flow_step_adjoint).  grad: host
+ * out, n_par.  Synchronises.  Errors: SR_EINVAL; SR_EUNSUPPORTED for TRI or tangent flows and
+ * for directions the core cannot represent (as sr_flow_init_tangent). */
+sr_status sr_flow_initial_vertex_adjoint(sr_flow* flow, int n_par, const double* dM, const double* d_bar_gamma, double* grad);
 
 /* ---- batched flows (many couplings / lattices of uneven size in one launch per stage) ---- */
 

@@ -7,8 +7,9 @@ Two ways to the same derivative:
   Euler steps and keeps the state every ``every`` steps; the backward pass starts from
   d chi / d state at the final cutoff (sr_measure_susceptibility_adjoint), walks the steps
   backwards (sr_flow_step_adjoint), recomputing the states of one checkpoint segment at a
-  time, and contracts the adjoint of the initial vertex with d Gamma_init / d theta (the
-  initial vertex is J / 4, linear in the couplings).  Memory: one state per checkpoint plus
+  time, and contracts the adjoint of the initial vertex with d Gamma_init / d theta
+  (sr_flow_initial_vertex_adjoint: the initial vertex is J / 4, linear in the couplings).
+  The couplings themselves come from theta through sr_couplings_linear.  Memory: one state per checkpoint plus
   one segment; cost: one extra forward flow plus the adjoint steps, independent of the
   number of parameters.
 * ``susceptibility`` (forward mode): the tangent-linear flow (sr_flow_init_tangent: every
@@ -20,14 +21,13 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from .binding import SR_EULER, SR_FP64, SR_SU2, SR_XYZ, Flow, Lattice
+from .binding import SR_EULER, SR_FP64, SR_SU2, SR_XYZ, Flow, Lattice, sr_couplings_linear
 
 
 class SusceptibilityFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, theta, cell, sites, B, L, mesh, lambdas, kpts, backend):
-        th = theta.detach().cpu().double().numpy()
-        M = np.einsum("p,pcij->cij", th, B)
+        M = sr_couplings_linear(theta.detach().cpu().double().numpy(), B)
         coups = [(f, t, M[c]) for c, (f, t) in enumerate(sites)]
         lat = Lattice(cell.prim, cell.basis, cell.bonds, coups, L, backend)
         fl = Flow(lat, mesh, float(lambdas[0]), SR_FP64, tangents=B)
@@ -51,20 +51,10 @@ def susceptibility(theta: torch.Tensor, cell, sites, B, L: int, mesh, lambdas, k
                                   np.asarray(kpts, dtype=np.float64), backend)
 
 
-def _initial_vertex_derivative(lat, mesh, lam0, B):
-    """d Gamma_init / d theta_p in the state layout (n_par, n_gamma): the tangent part of a
-    tangent flow's initial state."""
-    fl = Flow(lat, mesh, float(lam0), SR_FP64, tangents=B)
-    _, G = fl.get_state()
-    fl.close()
-    return G.view(-1, 3)[:, 1:1 + B.shape[0]].t().contiguous()
-
-
 class SusceptibilityAdjointFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, theta, cell, sites, B, L, mesh, lambdas, kpts, backend, every):
-        th = theta.detach().cpu().double().numpy()
-        M = np.einsum("p,pcij->cij", th, B)
+        M = sr_couplings_linear(theta.detach().cpu().double().numpy(), B)
         coups = [(f, t, M[c]) for c, (f, t) in enumerate(sites)]
         lat = Lattice(cell.prim, cell.basis, cell.bonds, coups, L, backend)
         fl = Flow(lat, mesh, float(lambdas[0]), SR_FP64)
@@ -95,8 +85,8 @@ class SusceptibilityAdjointFn(torch.autograd.Function):
             for n in range(end - 1, start - 1, -1):
                 fl.set_state(float(lambdas[n]), *states[n - start])
                 fl.step_adjoint(float(lambdas[n]), float(lambdas[n + 1]), bar_s, bar_G)
-        dG0 = _initial_vertex_derivative(lat, mesh, lambdas[0], B)
-        grad = (dG0 @ bar_G).to(device="cpu", dtype=grad_out.dtype)
+        # the initial vertex J / 4 is linear in theta: contract its derivative with bar_G
+        grad = torch.as_tensor(fl.initial_vertex_adjoint(B, bar_G), dtype=grad_out.dtype)
         return (grad, None, None, None, None, None, None, None, None, None)
 
 

@@ -94,6 +94,10 @@ def load_library():
             "sr_flow_rhs_adjoint": [vp, d, vp, vp, vp, vp],
             "sr_flow_step_adjoint": [vp, d, d, vp, vp, vp, vp],
             "sr_measure_susceptibility_adjoint": [vp, i, dp, dp, vp, vp],
+            "sr_couplings_linear": [i, dp, i, dp, dp],
+            "sr_flow_rhs_pairs": [vp, d, i, i, vp, vp],
+            "sr_flow_advance": [vp, d, vp, vp],
+            "sr_flow_initial_vertex_adjoint": [vp, i, dp, vp, dp],
             "sr_flow_profile_enable": [vp, i],
             "sr_flow_profile_read": [vp, dp, lp],
             "sr_flow_node_counts": [vp, ip],
@@ -137,6 +141,17 @@ def sr_peak_fma(precision: int) -> float:
     v = C.c_double()
     _check(load_library().sr_peak_fma(int(precision), C.byref(v)))
     return v.value
+
+
+def sr_couplings_linear(theta, B) -> np.ndarray:
+    """sr_couplings_linear: M_c = sum_p theta_p B[p, c] (B: n_par x n_couplings x 3 x 3)."""
+    th = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1)
+    Bc = np.ascontiguousarray(B, dtype=np.float64)
+    if Bc.ndim != 4 or Bc.shape[0] != th.size or Bc.shape[2:] != (3, 3):
+        raise ValueError("B must be n_par x n_couplings x 3 x 3")
+    M = np.zeros(Bc.shape[1:])
+    _check(load_library().sr_couplings_linear(th.size, _dptr(th), Bc.shape[1], _dptr(Bc), _dptr(M)))
+    return M
 
 
 def sr_frequency_mesh_exponential(n: int, wmin: float, wmax: float) -> np.ndarray:
@@ -285,6 +300,25 @@ class Flow:
         _check(self._lib.sr_flow_rhs(self.h, float(lam), _ptr(dsigma), _ptr(dgamma)))
         return dsigma, dgamma
 
+    @property
+    def entries_per_pair(self) -> int:
+        """State doubles of one stored (s, u) pair: all t, components and sites (with tangents)."""
+        return self.N * self.n_comp * self.lattice.N_s * self.ts
+
+    def rhs_pairs(self, lam: float, pair_begin: int, pair_end: int, dsigma, dgamma):
+        """sr_flow_rhs_pairs: dgamma/dLambda into dsigma, and dGamma/dLambda of the stored pairs
+        [pair_begin, pair_end) into their slice of dgamma (state layout; the rest untouched)."""
+        if dsigma.numel() < self.N * self.ts or dgamma.numel() < self.n_gamma * self.ts:
+            raise ValueError("dsigma / dgamma smaller than the state")
+        _check(self._lib.sr_flow_rhs_pairs(self.h, float(lam), int(pair_begin), int(pair_end), _ptr(dsigma), _ptr(dgamma)))
+        return dsigma, dgamma
+
+    def advance(self, lam_next: float, dsigma, dgamma):
+        """sr_flow_advance: Euler step to lam_next with a supplied right-hand side."""
+        if dsigma.numel() < self.N * self.ts or dgamma.numel() < self.n_gamma * self.ts:
+            raise ValueError("dsigma / dgamma smaller than the state")
+        _check(self._lib.sr_flow_advance(self.h, float(lam_next), _ptr(dsigma), _ptr(dgamma)))
+
     def step(self, lam_next: float, method: int = SR_EULER, rtol: float = 1e-6, atol: float = 1e-10) -> float:
         reached = C.c_double()
         _check(self._lib.sr_flow_step(self.h, float(lam_next), int(method), float(rtol), float(atol), C.byref(reached)))
@@ -400,6 +434,14 @@ class Flow:
         _check(self._lib.sr_measure_susceptibility_adjoint(self.h, kp.shape[0], _dptr(kp), _dptr(cb), _ptr(gs),
                                                            _ptr(gG)))
         return gs, gG
+
+    def initial_vertex_adjoint(self, dM, bar_gamma) -> np.ndarray:
+        """sr_flow_initial_vertex_adjoint: grad_p = <d Gamma_init / d theta_p, bar_gamma> for
+        coupling derivatives dM (n_par x n_couplings x 3 x 3); returns an array (n_par,)."""
+        d = np.ascontiguousarray(dM, dtype=np.float64)
+        grad = np.zeros(d.shape[0])
+        _check(self._lib.sr_flow_initial_vertex_adjoint(self.h, d.shape[0], _dptr(d), _ptr(bar_gamma), _dptr(grad)))
+        return grad
 
     def profile_enable(self, on: bool = True):
         _check(self._lib.sr_flow_profile_enable(self.h, 1 if on else 0))

@@ -393,12 +393,12 @@ template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads, std::is_same<T, double>::value ? 6 : 1) k_gamma_rhs(Geo g, Tabs tb, const double* __restrict__ w,
                                                         const T* __restrict__ G, const double* __restrict__ nx,
                                                         const T* __restrict__ nW, const int* __restrict__ ncount,
-                                                        T* __restrict__ dG) {
+                                                        T* __restrict__ dG, int p0) {
     extern __shared__ __align__(16) unsigned char smem[];
     ShPtrs<T> sh = carve<T, NC>(smem, g, tb);
     const int tid = threadIdx.x;
     const int ti = blockIdx.x % g.N;
-    const int p = blockIdx.x / g.N;
+    const int p = p0 + (int)(blockIdx.x / g.N);   // stored pairs p0, p0 + 1, ...: one CTA per triple
     int si = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
     while ((si + 1) * (si + 2) / 2 <= p) ++si;
     while (si * (si + 1) / 2 > p) --si;
@@ -1143,9 +1143,9 @@ template <int NC, bool DENSE>
 __global__ void __launch_bounds__(kThreads) k_gamma_rhs_f32(Geo g, Tabs tb, const float* __restrict__ Gf,
                                                             const float* __restrict__ Gs, const float* __restrict__ nx,
                                                             const float* __restrict__ nW, const int* __restrict__ ncount,
-                                                            double* __restrict__ dG) {
+                                                            double* __restrict__ dG, int p0) {
     extern __shared__ __align__(16) unsigned char smem[];
-    gamma_rhs_f32_triple<NC, DENSE>(g, tb, Gf, Gs, nx, nW, ncount, dG, blockIdx.x / g.N, blockIdx.x % g.N, smem, kQF);
+    gamma_rhs_f32_triple<NC, DENSE>(g, tb, Gf, Gs, nx, nW, ncount, dG, p0 + (int)(blockIdx.x / g.N), blockIdx.x % g.N, smem, kQF);
 }
 
 // The SU2 kernel with the lattice sum on the tensor cores, persistent: each CTA allocates its
@@ -1157,7 +1157,7 @@ static_assert(kThreads == 128, "the TMEM read-back maps the four warps onto the 
 __global__ void __launch_bounds__(kThreads) k_gamma_rhs_f32_tc(Geo g, Tabs tb, const float* __restrict__ Gf,
                                                                const float* __restrict__ Gs, const float* __restrict__ nx,
                                                                const float* __restrict__ nW, const int* __restrict__ ncount,
-                                                               double* __restrict__ dG, int* __restrict__ fail) {
+                                                               double* __restrict__ dG, int* __restrict__ fail, long u0, long u1) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
@@ -1169,8 +1169,7 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_f32_tc(Geo g, Tabs tb, c
     __syncthreads();
     tc::fence_after_sync();
     TcCta tcs{tmem_slot, &mbar, 0u, &failed};
-    const long ntrip = (long)g.npair * g.N;
-    for (long tr = blockIdx.x; tr < ntrip; tr += gridDim.x) {
+    for (long tr = u0 + blockIdx.x; tr < u1; tr += gridDim.x) {   // triples (units) u0 .. u1 - 1
         const int p = (int)(tr / g.N), ti = (int)(tr % g.N);
         gamma_rhs_f32_triple<2, true, true>(g, tb, Gf, Gs, nx, nW, ncount, dG, p, ti, smem, kQF, &tcs);
         __syncthreads();
@@ -1184,6 +1183,8 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_f32_tc(Geo g, Tabs tb, c
     __syncthreads();
     if (threadIdx.x < 32) tc::tmem_dealloc(tcs.tmem, ncols);
 }
+
+#include "su2f.cuh"
 
 // FP32 shadow of the state in the padded layout, and (with_swap) the exchanged copy in which
 // entry (c, r) holds the stored value of the pair (rep_r, ref): component perm(c) of site
@@ -1387,6 +1388,7 @@ struct sr_flow {
     Geo g{};
     sr_precision prec = SR_FP64;
     cudaStream_t stream = nullptr;
+    int device = -1;                 // CUDA device current when the flow was created
     double lambda = 0.0;
     std::vector<double> mesh;
     int ntan = 0;   // tangent directions (0: plain flow; kTan: the state holds Dual<kTan> values)
@@ -1405,6 +1407,8 @@ struct sr_flow {
     DevBuf<int> dgath_idx;
     bool has_swap = false, dense = false;
     bool use_tc = false;          // FP32-mixed SU2: lattice sum on the tensor cores
+    size_t smem_su2f = 0;         // FP32-mixed SU2 kernel (k_gamma_rhs_su2f): dynamic shared memory,
+    int su2f_qb = 0;              // its integration nodes per block (0: the kernel is not used)
     size_t smem_tc = 0;           // dynamic shared memory of the tensor-core kernel
     int tc_grid = 0;              // its persistent grid (SMs x resident CTAs)
     int tc_occ_api = 0;           // the runtime's occupancy figure for it (reported only)
@@ -1502,11 +1506,12 @@ static sr_status prof_end(sr_flow* f, int id, cudaEvent_t b) {
 
 // Right-hand side at cutoff lam for the state (gam_s, G_s [, Gf_s]) into (dgam_o, dG_o).
 static sr_status run_rhs(sr_flow* f, double lam, const double* gam_s, const double* G_s, const float* Gf_s,
-                         double* dgam_o, double* dG_o) {
+                         double* dgam_o, double* dG_o, int pb = 0, int pe = -1) {
     const Geo& g = f->g;
     Tabs tb = f->tabs();
     cudaEvent_t e0 = nullptr;
-    const int blocks = g.npair * g.N;
+    if (pe < 0) pe = g.npair;   // stored (s, u) pairs pb .. pe - 1 (all by default)
+    const int blocks = (pe - pb) * g.N;
     if (f->ntan) {
         // tangent-linear flow: the same kernels on dual numbers
         const DualT* gs = reinterpret_cast<const DualT*>(gam_s);
@@ -1523,9 +1528,9 @@ static sr_status run_rhs(sr_flow* f, double lam, const double* gam_s, const doub
         if (sr_status s = prof_end(f, 1, e0)) return s;
         if (sr_status s = prof_begin(f, 2, &e0)) return s;
         if (g.nc == 2)
-            k_gamma_rhs<DualT, 2><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, f->w.p, Gd, f->nx.p, nW, f->ncount.p, dGo);
+            k_gamma_rhs<DualT, 2><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, f->w.p, Gd, f->nx.p, nW, f->ncount.p, dGo, pb);
         else
-            k_gamma_rhs<DualT, 4><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, f->w.p, Gd, f->nx.p, nW, f->ncount.p, dGo);
+            k_gamma_rhs<DualT, 4><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, f->w.p, Gd, f->nx.p, nW, f->ncount.p, dGo, pb);
         if (sr_status s = prof_end(f, 2, e0)) return s;
         CK(cudaGetLastError());
         f->n_rhs++;
@@ -1543,9 +1548,9 @@ static sr_status run_rhs(sr_flow* f, double lam, const double* gam_s, const doub
         if (sr_status s = prof_end(f, 1, e0)) return s;
         if (sr_status s = prof_begin(f, 2, &e0)) return s;
         if (f->prec == SR_FP64)
-            k_gamma_rhs_tri<double><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, tt, f->w.p, G_s, f->nx.p, f->nW.p, f->ncount.p, dG_o);
+            k_gamma_rhs_tri<double><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, tt, f->w.p, G_s, f->nx.p, f->nW.p, f->ncount.p, dG_o, pb);
         else
-            k_gamma_rhs_tri<float><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, tt, f->w.p, Gf_s, f->nx.p, f->nW.p, f->ncount.p, dG_o);
+            k_gamma_rhs_tri<float><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, tt, f->w.p, Gf_s, f->nx.p, f->nW.p, f->ncount.p, dG_o, pb);
         if (sr_status s = prof_end(f, 2, e0)) return s;
         CK(cudaGetLastError());
         f->n_rhs++;
@@ -1561,20 +1566,23 @@ static sr_status run_rhs(sr_flow* f, double lam, const double* gam_s, const doub
     if (sr_status s = prof_begin(f, 2, &e0)) return s;
     if (f->prec == SR_FP64) {
         if (g.nc == 2)
-            k_gamma_rhs<double, 2><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, f->w.p, G_s, f->nx.p, f->nW.p, f->ncount.p, dG_o);
+            k_gamma_rhs<double, 2><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, f->w.p, G_s, f->nx.p, f->nW.p, f->ncount.p, dG_o, pb);
         else
-            k_gamma_rhs<double, 4><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, f->w.p, G_s, f->nx.p, f->nW.p, f->ncount.p, dG_o);
+            k_gamma_rhs<double, 4><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, f->w.p, G_s, f->nx.p, f->nW.p, f->ncount.p, dG_o, pb);
     } else {
         const float* Gs = f->has_swap ? Gf_s + g.nentp : Gf_s;
         if (g.nc == 2 && f->dense && f->use_tc)
             k_gamma_rhs_f32_tc<<<std::min(blocks, f->tc_grid), kThreads, f->smem_tc, f->stream>>>(g, tb, Gf_s, Gs, f->nxf.p, f->nWf.p, f->ncount.p, dG_o,
-                                                                            f->tcfail.p);
+                                                                            f->tcfail.p, (long)pb * g.N, (long)pe * g.N);
+        else if (g.nc == 2 && f->dense && f->su2f_qb > 0)
+            k_gamma_rhs_su2f<<<blocks, su2f::threads_for(g.nsp), f->smem_su2f, f->stream>>>(g, tb, Gf_s, f->has_swap ? (int)g.nentp : 0, f->nxf.p,
+                                                                            f->nWf.p, f->ncount.p, dG_o, f->su2f_qb, pb);
         else if (g.nc == 2 && f->dense)
-            k_gamma_rhs_f32<2, true><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, Gf_s, Gs, f->nxf.p, f->nWf.p, f->ncount.p, dG_o);
+            k_gamma_rhs_f32<2, true><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, Gf_s, Gs, f->nxf.p, f->nWf.p, f->ncount.p, dG_o, pb);
         else if (g.nc == 2)
-            k_gamma_rhs_f32<2, false><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, Gf_s, Gs, f->nxf.p, f->nWf.p, f->ncount.p, dG_o);
+            k_gamma_rhs_f32<2, false><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, Gf_s, Gs, f->nxf.p, f->nWf.p, f->ncount.p, dG_o, pb);
         else
-            k_gamma_rhs_f32<4, false><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, Gf_s, Gs, f->nxf.p, f->nWf.p, f->ncount.p, dG_o);
+            k_gamma_rhs_f32<4, false><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, Gf_s, Gs, f->nxf.p, f->nWf.p, f->ncount.p, dG_o, pb);
     }
     if (sr_status s = prof_end(f, 2, e0)) return s;
     CK(cudaGetLastError());
@@ -1696,6 +1704,7 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
     f->lat = lat;
     f->prec = precision;
     f->stream = (cudaStream_t)cuda_stream;
+    CK(cudaGetDevice(&f->device));
     f->ntan = npar > 0 ? kTan : 0;
     f->ts = 1 + f->ntan;
     const int ts = f->ts;
@@ -1939,6 +1948,17 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
         CK(ensure_smem((const void*)k_gamma_rhs<double, 4>, f->smem_rhs));
     } else {
         CK(ensure_smem((const void*)k_gamma_rhs_f32<2, true>, f->smem_rhs));
+        if (g.nc == 2 && f->dense && g.nsp / 2 <= su2f::kThreadsS) {
+            // FP32-mixed SU2 kernel: the largest node block (64, 32, 16) whose shared memory
+            // leaves room for the resident CTAs its registers allow, else the smallest that fits
+            const int nth = su2f::threads_for(g.nsp);
+            const int ctas = su2f::kMinCtas * su2f::kThreadsS / nth;
+            for (int qb : {64, 32, 16}) {
+                const size_t b = su2f::layout(g.N, g.Ns, g.nsp, qb, nth).total;
+                if (b <= 227 * 1024 / ctas || (qb == 16 && b <= 227 * 1024)) { f->su2f_qb = qb; f->smem_su2f = b; break; }
+            }
+            if (f->su2f_qb > 0) CK(ensure_smem((const void*)k_gamma_rhs_su2f, f->smem_su2f));
+        }
         CK(ensure_smem((const void*)k_gamma_rhs_f32<2, false>, f->smem_rhs));
         CK(ensure_smem((const void*)k_gamma_rhs_f32<4, false>, f->smem_rhs));
         if (tc_ok) {
@@ -2037,6 +2057,38 @@ static sr_status euler_step(sr_flow* f, double lam_next) {
     if (sr_status s = refresh_shadow(f, f->G.p, f->Gf.p)) return s;
     if (sr_status s = check_flag(f, lam_next)) return s;
     f->lambda = lam_next;
+    return SR_OK;
+}
+
+// ----------------------------------------------------------------------------- sharded right-hand side
+
+extern "C" sr_status sr_flow_rhs_pairs(sr_flow* f, double lambda, int pair_begin, int pair_end, double* d_dsigma,
+                                       double* d_dgamma) {
+    if (!f) return fail(SR_EINVAL, "null flow");
+    if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(SR_EINVAL, "lambda must be positive");
+    if (pair_begin < 0 || pair_end < pair_begin || pair_end > f->g.npair)
+        return fail(SR_EINVAL, "pair range [%d, %d) outside [0, %d]", pair_begin, pair_end, f->g.npair);
+    if (!d_dsigma || !d_dgamma) return fail(SR_EINVAL, "null output");
+    // the vertex kernels write only the range's slice of the state layout, straight into d_dgamma
+    if (sr_status s = run_rhs(f, lambda, f->gam.p, f->G.p, f->Gf.p, d_dsigma, d_dgamma, pair_begin, pair_end)) return s;
+    return SR_OK;
+}
+
+extern "C" sr_status sr_flow_advance(sr_flow* f, double lambda_next, const double* d_dsigma, const double* d_dgamma) {
+    if (!f) return fail(SR_EINVAL, "null flow");
+    if (!d_dsigma || !d_dgamma) return fail(SR_EINVAL, "null right-hand side");
+    if (!(lambda_next > 0.0) || !(lambda_next < f->lambda)) return fail(SR_EINVAL, "lambda_next must lie in (0, lambda)");
+    const Geo& g = f->g;
+    const double dl = f->lambda - lambda_next;
+    CK(cudaMemsetAsync(f->flag.p, 0, sizeof(int), f->stream));
+    const long nG = g.nent * f->ts;
+    k_axpy<<<1, 256, 0, f->stream>>>((long)g.N * f->ts, f->gam.p, d_dsigma, -dl, f->flag.p);
+    k_axpy<<<(unsigned)((nG + 255) / 256), 256, 0, f->stream>>>(nG, f->G.p, d_dgamma, -dl, f->flag.p);
+    CK(cudaGetLastError());
+    if (sr_status s = refresh_shadow(f, f->G.p, f->Gf.p)) return s;
+    if (sr_status s = check_flag(f, lambda_next)) return s;
+    f->lambda = lambda_next;
+    f->fsal = false;
     return SR_OK;
 }
 
@@ -2408,6 +2460,57 @@ extern "C" sr_status sr_measure_susceptibility_adjoint(sr_flow* f, int n_k, cons
     return SR_OK;
 }
 
+// ----------------------------------------------------------------------------- coupling parameters
+
+extern "C" sr_status sr_couplings_linear(int n_par, const double* theta, int n_couplings, const double* B, double* M) {
+    if (n_par < 1 || n_couplings < 0 || !theta || (n_couplings > 0 && (!B || !M))) return fail(SR_EINVAL, "bad arguments");
+    for (int c = 0; c < n_couplings; ++c)
+        for (int e = 0; e < 9; ++e) {
+            double acc = 0.0;
+            for (int q = 0; q < n_par; ++q) acc += theta[q] * B[((size_t)q * n_couplings + c) * 9 + e];
+            M[(size_t)c * 9 + e] = acc;
+        }
+    return SR_OK;
+}
+
+namespace {
+// Column sums of the state-layout array a over all stored frequency triples: out[c * Ns + r] =
+// sum over (pair, t) of a[((pair N + t) nc + c) Ns + r]; one block per (c, r), fixed reduction
+// order.
+__global__ void k_entry_column_sum(Geo g, const double* __restrict__ a, double* __restrict__ out) {
+    __shared__ double red[32];
+    const int cr = blockIdx.x, row = g.nc * g.Ns;
+    const long ntrip = (long)g.npair * g.N;
+    double acc[1] = {0.0};
+    for (long i = threadIdx.x; i < ntrip; i += blockDim.x) acc[0] += a[i * row + cr];
+    block_sum<double, 1>(acc, red);
+    if (threadIdx.x == 0) out[(cr % g.Ns) * g.nc + cr / g.Ns] = acc[0];
+}
+}  // namespace
+
+extern "C" sr_status sr_flow_initial_vertex_adjoint(sr_flow* f, int n_par, const double* dM, const double* d_bar_gamma,
+                                                   double* grad) {
+    if (!f || n_par < 1 || !dM || !d_bar_gamma || !grad) return fail(SR_EINVAL, "bad arguments");
+    if (f->ntan || f->g.nc == 16) return fail(SR_EUNSUPPORTED, "plain SU2 / XYZ flows only");
+    const Geo& g = f->g;
+    std::vector<double> dinit;
+    std::string msg;
+    if (sr_status s = sr::tangent_init(f->lat, n_par, dM, &dinit, &msg)) return fail(s, "%s", msg.c_str());
+    DevBuf<double> col;
+    CK(col.alloc((size_t)g.Ns * g.nc));
+    k_entry_column_sum<<<g.Ns * g.nc, 256, 0, f->stream>>>(g, d_bar_gamma, col.p);
+    CK(cudaGetLastError());
+    std::vector<double> h((size_t)g.Ns * g.nc);
+    CK(cudaMemcpyAsync(h.data(), col.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, f->stream));
+    CK(cudaStreamSynchronize(f->stream));
+    for (int q = 0; q < n_par; ++q) {
+        double acc = 0.0;
+        for (size_t e = 0; e < h.size(); ++e) acc += dinit[e * n_par + q] * h[e];
+        grad[q] = acc;
+    }
+    return SR_OK;
+}
+
 // ----------------------------------------------------------------------------- batched flows
 //
 // Many flows (instances of uneven size) integrated together: every kernel of an Euler step
@@ -2436,6 +2539,7 @@ struct BInst {
     int qc;         // integration nodes per shared-memory block
     int kind;       // 0 SU2 dense, 1 SU2 product list, 2 XYZ
     int with_swap;
+    int qb_own;     // SU2 dense: node block of the instance's own kernel (k_gamma_rhs_su2f)
 };
 
 __global__ void k_sigma_b(const BInst* __restrict__ I, const double* __restrict__ lams, const int* __restrict__ step) {
@@ -2490,10 +2594,60 @@ __global__ void __launch_bounds__(kThreads, 7) k_gamma_persistent(const BInst* _
     }
 }
 
+// SU2 instances (dense lattice sum) in one persistent kernel over the per-triple function of
+// k_gamma_rhs_su2f: CTAs take `chunk` consecutive units per atomic step (consecutive units
+// mostly belong to one instance, whose tables are staged once), and the kernel is not capped
+// in registers (the per-triple function keeps its corner slots in registers).
+__global__ void __launch_bounds__(kThreads) k_gamma_persistent_su2f(const BInst* __restrict__ I, int i_begin, int i_end,
+                                                                    long u_begin, long u_end,
+                                                                    unsigned long long* __restrict__ counter, int chunk) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long unit_sh;
+    __shared__ __align__(16) BInst B;   // the current unit's instance
+    int cur = -1;
+    long cur_end = -1;                  // first unit past the current instance
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) unit_sh = u_begin + (long)atomicAdd(counter, (unsigned long long)chunk);
+        __syncthreads();
+        const long u0 = unit_sh;
+        if (u0 >= u_end) break;
+        const long u1 = min(u0 + (long)chunk, u_end);
+        for (long u = u0; u < u1; ++u) {
+            if (cur < 0 || u < B.unit0 || u >= cur_end) {
+                __shared__ int inst_sh;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    int lo = i_begin, hi = i_end - 1;   // last instance with unit0 <= u
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (I[mid].unit0 <= u) lo = mid; else hi = mid - 1;
+                    }
+                    inst_sh = lo;
+                }
+                __syncthreads();
+                cur = inst_sh;
+                static_assert(sizeof(BInst) % sizeof(int) == 0, "BInst copied as ints");
+                const int* src = reinterpret_cast<const int*>(I + cur);
+                for (int i = threadIdx.x; i < (int)(sizeof(BInst) / sizeof(int)); i += blockDim.x)
+                    reinterpret_cast<int*>(&B)[i] = src[i];
+                __syncthreads();
+                cur_end = B.unit0 + (long)B.g.npair * B.g.N;
+            }
+            const long local = u - B.unit0;
+            su2f::triple(B.g, B.tb, B.Gf, B.with_swap ? (int)B.g.nentp : 0, B.nxf, B.nWf, B.ncount, B.dG,
+                         (int)(local / B.g.N), (int)(local % B.g.N), smem, B.qc);
+        }
+    }
+}
+
+// Units per atomic step of the SU2 persistent kernel.
+constexpr int kUnitChunk = 4;
+
 // Persistent kernel of an instance kind (0: SU2 dense lattice sum, 1: SU2 product list, 2: XYZ);
 // every size class holds instances of one kind.
 static const void* persistent_fn(int kind) {
-    if (kind == 0) return (const void*)k_gamma_persistent<2, true>;
+    if (kind == 0) return (const void*)k_gamma_persistent_su2f;
     if (kind == 1) return (const void*)k_gamma_persistent<2, false>;
     return (const void*)k_gamma_persistent<4, false>;
 }
@@ -2594,18 +2748,20 @@ static void launch_class(sr_batch* b, int k, cudaStream_t st) {
             const unsigned blocks = (unsigned)(B.g.npair * B.g.N);
             const size_t sm = b->inst_smem[i];
             if (c.kind == 0)
-                k_gamma_rhs_f32<2, true><<<blocks, kThreads, sm, st>>>(B.g, B.tb, B.Gf, B.Gs, B.nxf, B.nWf, B.ncount, B.dG);
+                k_gamma_rhs_su2f<<<blocks, su2f::threads_for(B.g.nsp), sm, st>>>(B.g, B.tb, B.Gf, B.with_swap ? (int)B.g.nentp : 0, B.nxf, B.nWf,
+                                                               B.ncount, B.dG, B.qb_own, 0);
             else if (c.kind == 1)
-                k_gamma_rhs_f32<2, false><<<blocks, kThreads, sm, st>>>(B.g, B.tb, B.Gf, B.Gs, B.nxf, B.nWf, B.ncount, B.dG);
+                k_gamma_rhs_f32<2, false><<<blocks, kThreads, sm, st>>>(B.g, B.tb, B.Gf, B.Gs, B.nxf, B.nWf, B.ncount, B.dG, 0);
             else
-                k_gamma_rhs_f32<4, false><<<blocks, kThreads, sm, st>>>(B.g, B.tb, B.Gf, B.Gs, B.nxf, B.nWf, B.ncount, B.dG);
+                k_gamma_rhs_f32<4, false><<<blocks, kThreads, sm, st>>>(B.g, B.tb, B.Gf, B.Gs, B.nxf, B.nWf, B.ncount, B.dG, 0);
         }
         return;
     }
     const dim3 grid(b->nsm * c.ctas);
     unsigned long long* ctr = b->counter.p + k;
     if (c.kind == 0)
-        k_gamma_persistent<2, true><<<grid, kThreads, c.smem, st>>>(b->dinst.p, c.i_begin, c.i_end, c.u_begin, c.u_end, ctr);
+        k_gamma_persistent_su2f<<<grid, kThreads, c.smem, st>>>(b->dinst.p, c.i_begin, c.i_end, c.u_begin, c.u_end, ctr,
+                                                               kUnitChunk);
     else if (c.kind == 1)
         k_gamma_persistent<2, false><<<grid, kThreads, c.smem, st>>>(b->dinst.p, c.i_begin, c.i_end, c.u_begin, c.u_end, ctr);
     else
@@ -2694,9 +2850,20 @@ static sr_status batch_tune(sr_batch* b) {
         }
         std::vector<int> ctas_c;
         for (int v = c.occ; v >= 1; v = v / 2) { ctas_c.push_back(v); if (v == 1) break; }
+        std::vector<int> qcand;
+        if (c.kind == 0) {
+            for (int qb : {16, 32, 64}) {
+                bool fits = true;
+                for (int i = c.i_begin; i < c.i_end; ++i)
+                    if (su2f::layout(b->inst[i].g.N, b->inst[i].g.Ns, b->inst[i].g.nsp, qb, kThreads).total > c.smem) fits = false;
+                if (fits) qcand.push_back(qb);
+            }
+        } else {
+            qcand.assign(qcs, qcs + 3);
+        }
         double best = 1e300;
         int bq = c.qc, bc = c.ctas;
-        for (int qc : qcs)
+        for (int qc : qcand)
             for (int ct : ctas_c) {
                 for (int i = c.i_begin; i < c.i_end; ++i) b->inst[i].qc = qc;
                 c.ctas = ct;
@@ -2772,8 +2939,20 @@ extern "C" sr_status sr_batch_create(int n, sr_flow* const* flows, sr_batch** ou
     std::vector<size_t> sm(n);
     std::vector<int> kind(n);
     for (int i = 0; i < n; ++i) {
-        sm[i] = f32_smem_bytes(flows[i]->g.Ns, flows[i]->g.nsp, flows[i]->g.nc, flows[i]->nprod, flows[i]->dense);
-        kind[i] = flows[i]->g.nc == 4 ? 2 : (flows[i]->dense ? 0 : 1);
+        sr_flow* f = flows[i];
+        kind[i] = f->g.nc == 4 ? 2 : (f->dense ? 0 : 1);
+        if (kind[i] == 0 && f->su2f_qb == 0)
+            return fail(SR_EUNSUPPORTED, "flow %d: lattice too large for the batched SU2 kernel", i);
+        // SU2 dense: shared memory of the largest node block that fits (the tuner may pick it)
+        if (kind[i] == 0) {
+            sm[i] = f->smem_su2f;
+            for (int qb : {64, 32}) {
+                const size_t bq = su2f::layout(f->g.N, f->g.Ns, f->g.nsp, qb, kThreads).total;
+                if (bq <= 227 * 1024 / 3) { sm[i] = std::max(sm[i], bq); break; }
+            }
+        } else {
+            sm[i] = f32_smem_bytes(f->g.Ns, f->g.nsp, f->g.nc, f->nprod, f->dense);
+        }
     }
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
@@ -2794,7 +2973,7 @@ extern "C" sr_status sr_batch_create(int n, sr_flow* const* flows, sr_batch** ou
         if (b->cls.empty() || b->cls.back().kind != kind[k] || sm[k] * 3 < b->cls.back().smem * 2) {
             BClass c{};
             c.kind = kind[k];
-            c.i_begin = idx; c.u_begin = unit; c.smem = sm[k]; c.qc = kQF;
+            c.i_begin = idx; c.u_begin = unit; c.smem = sm[k]; c.qc = kind[k] == 0 ? f->su2f_qb : kQF;
             if (sm[k] > 227 * 1024) return fail(SR_EUNSUPPORTED, "instance needs %zu bytes of shared memory", sm[k]);
             CK(ensure_smem(persistent_fn(c.kind), sm[k]));
             CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, persistent_fn(c.kind), kThreads, sm[k]));
@@ -2812,9 +2991,11 @@ extern "C" sr_status sr_batch_create(int n, sr_flow* const* flows, sr_batch** ou
         B.qc = kQF;
         B.kind = kind[k];
         B.with_swap = f->has_swap ? 1 : 0;
+        B.qb_own = f->su2f_qb;
+        if (kind[k] == 0) B.qc = f->su2f_qb;
         unit += (long)f->g.npair * f->g.N;
         b->inst.push_back(B);
-        b->inst_smem.push_back(f->smem_rhs);
+        b->inst_smem.push_back(kind[k] == 0 ? f->smem_su2f : f->smem_rhs);
         b->cls.back().i_end = idx + 1;
         b->cls.back().u_end = unit;
     }
@@ -2979,8 +3160,12 @@ extern "C" sr_status sr_measure_susceptibility_static(sr_flow* f, int n_k, const
     const size_t need = (size_t)npairs * g.nc;
     if (need > (size_t)SR_CHI_STATIC_MAX)
         return fail(SR_EINVAL, "correlation table needs %zu values, above the static limit of %d", need, SR_CHI_STATIC_MAX);
+    // the array's address is per device: look it up (and launch) with the flow's device current
     int dev = 0;
     CK(cudaGetDevice(&dev));
+    if (dev != f->device)
+        return fail(SR_EINVAL, "device %d is current, but the flow lives on device %d: make the flow's device current", dev,
+                    f->device);
     if (dev < 0 || dev >= 64) return fail(SR_EINVAL, "device index %d out of range", dev);
     double* scratch = nullptr;
     {

@@ -224,7 +224,7 @@ template <typename R>
 __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, TabsT tt, const double* __restrict__ w,
                                                             const R* __restrict__ G, const double* __restrict__ nx,
                                                             const double* __restrict__ nW, const int* __restrict__ ncount,
-                                                            double* __restrict__ dG) {
+                                                            double* __restrict__ dG, int p0) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int NG = tri_groups(g.Ns, blockDim.x);
     ShT<R> sh;
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
     }
     const int tid = threadIdx.x;
     const int ti = blockIdx.x % g.N;
-    const int p = blockIdx.x / g.N;
+    const int p = p0 + (int)(blockIdx.x / g.N);   // stored pairs p0, p0 + 1, ...
     int si = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
     while ((si + 1) * (si + 2) / 2 <= p) ++si;
     while (si * (si + 1) / 2 > p) --si;

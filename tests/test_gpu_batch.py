@@ -54,23 +54,33 @@ def test_batch_matches_individual_flows(use_graph, autotune, mode):
     b.close()
 
 
-def test_batch_instance_against_oracle():
-    model, L, mesh = MODELS[0]
+@pytest.mark.parametrize("mode", [0, 1, 2], ids=["autotuned", "persistent", "per_instance"])
+def test_batch_instances_against_oracle(mode):
+    """Every instance of a batch, in every launch form (mode 1 forces the persistent kernels,
+    2 the instances' own kernels, 0 lets the autotuner choose), against the oracle's Euler flow
+    of the same model within the FP32-mixed tolerance."""
     lams = W.lambda_list(8.0, 1.0, 6)
-    of = O.OracleFlow(model, L, mesh)
-    for a, c in zip(lams[:-1], lams[1:]):
-        of.euler(a, c)
-    flows = []
+    flows, oracles = [], []
     for m, l, ms in MODELS:
         lat = sr.Lattice.from_model(m, l)
         flows.append((lat, sr.Flow(lat, ms, lams[0], sr.SR_FP32_MIXED)))
+        of = O.OracleFlow(m, l, ms)
+        for a, c in zip(lams[:-1], lams[1:]):
+            of.euler(a, c)
+        oracles.append(of)
     b = sr.Batch([fl for _, fl in flows])
-    b.run(lams)
-    lat, fl = flows[0]
-    _, G = fl.get_state()
-    _, G_o = of.get_state()
-    exp = oracle_to_gpu(of, lat, G_o, fl.n_comp)
-    got = G.cpu().numpy().reshape(exp.shape)
-    for c in range(fl.n_comp):
-        assert np.abs(got[:, :, c] - exp[:, :, c]).max() <= 1e-3 * np.abs(exp[:, :, c]).max()
+    b.force_launch(mode)
+    b.run(lams, use_graph=True, autotune=(mode == 0))
+    if mode == 1:
+        assert not any(b.class_launches())
+    if mode == 2:
+        assert all(b.class_launches())
+    for (lat, fl), of in zip(flows, oracles):
+        g, G = fl.get_state()
+        g_o, G_o = of.get_state()
+        assert np.abs(g.cpu().numpy() - g_o).max() <= 1e-3 * np.abs(g_o).max()
+        exp = oracle_to_gpu(of, lat, G_o, fl.n_comp)
+        got = G.cpu().numpy().reshape(exp.shape)
+        for c in range(fl.n_comp):
+            assert np.abs(got[:, :, c] - exp[:, :, c]).max() <= 1e-3 * np.abs(exp[:, :, c]).max(), c
     b.close()

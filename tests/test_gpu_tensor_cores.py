@@ -1,5 +1,8 @@
 """Tensor-core lattice sum of the FP32-mixed SU2 vertex kernel (tcgen05 MMAs in 3xTF32).
 
+Against the oracle: the tensor-core right-hand side on oracle-evolved states within the
+FP32-mixed tolerance (1e-3 normwise per component; the self-energy flow, FP64, within 1e-10).
+
 The same right-hand side with the lattice-sum contraction on the tensor cores and on FP32 CUDA
 cores must agree to FP32 rounding (3xTF32 keeps ~22 of the 24 mantissa bits of every product),
 and both must stay within the FP32-mixed tolerance of the FP64 kernel.  Lattices cover both
@@ -10,6 +13,8 @@ import numpy as np
 import pytest
 
 import workloads as W
+from oracle import oracle as O
+from tests.helpers import evolved_oracle, oracle_to_gpu
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -59,6 +64,40 @@ CASES = [
     ("kagome_L7", lambda: W.nn_heisenberg(W.kagome()), 7, 8),         # unpacked, N_s = 34
     ("pyrochlore_L3", lambda: W.nn_heisenberg(W.pyrochlore()), 3, 8),
 ]
+
+
+ORACLE_CASES = [
+    ("square_j1j2", lambda: W.square_j1j2(1.0, 0.5), 2, 7, 0.02, 20.0),
+    ("honeycomb", lambda: W.nn_heisenberg(W.honeycomb()), 2, 6, 0.05, 10.0),
+    ("kagome", lambda: W.nn_heisenberg(W.kagome()), 2, 5, 0.05, 10.0),
+    ("kagome_L7", lambda: W.nn_heisenberg(W.kagome()), 7, 5, 0.05, 10.0),   # N_s = 34: one MMA per component
+]
+
+
+@pytest.mark.parametrize("name,mk,L,N,wmin,wmax", ORACLE_CASES, ids=[c[0] for c in ORACLE_CASES])
+def test_tensor_cores_match_oracle(name, mk, L, N, wmin, wmax):
+    model = mk()
+    mesh = O.mesh_exponential(N, wmin, wmax)
+    of = evolved_oracle(model, L, mesh, [8.0, 4.0, 2.0, 1.0])
+    lam = 0.7
+    dg_o, dG_o = of.rhs(lam)
+    lat = sr.Lattice.from_model(model, L)
+    fl = sr.Flow(lat, mesh, 1.0, sr.SR_FP32_MIXED)
+    fl.tensor_cores = True
+    gam, G = of.get_state()
+    Gg = oracle_to_gpu(of, lat, G, fl.n_comp)
+    fl.set_state(1.0, torch.tensor(gam, device="cuda"), torch.tensor(Gg.reshape(-1), device="cuda"))
+    dg, dG = fl.rhs(lam)
+    torch.cuda.synchronize()
+    assert fl.tensor_cores
+    dg = dg.cpu().numpy()
+    assert np.abs(dg - dg_o).max() <= 1e-10 * np.abs(dg_o).max()
+    got = dG.cpu().numpy().reshape(fl.npair, fl.N, fl.n_comp, lat.N_s)
+    exp = oracle_to_gpu(of, lat, dG_o, fl.n_comp)
+    for c in range(fl.n_comp):
+        e = exp[:, :, c]
+        assert np.abs(got[:, :, c] - e).max() <= 1e-3 * np.abs(e).max(), c
+    fl.close()
 
 
 @pytest.mark.parametrize("name,mk,L,nf", CASES)

@@ -189,6 +189,24 @@ def test_frequency_mesh_matches_oracle():
     np.testing.assert_allclose(a, b, rtol=1e-15)
 
 
+def test_couplings_linear_combination():
+    """sr_couplings_linear: M_c = sum_p theta_p B[p, c], checked entry by entry (and the
+    Heisenberg-Kitaev parametrisation reproduces the model's own couplings)."""
+    rng = np.random.default_rng(4)
+    B = rng.normal(size=(2, 5, 3, 3))
+    th = np.array([0.7, -1.3])
+    M = sr.sr_couplings_linear(th, B)
+    for c in range(5):
+        np.testing.assert_allclose(M[c], th[0] * B[0, c] + th[1] * B[1, c], rtol=1e-15, atol=1e-15)
+    cell, sites, Bk = W.honeycomb_kitaev_linear()
+    Mk = sr.sr_couplings_linear([0.2, -1.0], Bk)
+    ref = W.linear_model(cell, sites, Bk, [0.2, -1.0])
+    for c, cp in enumerate(ref.couplings):
+        np.testing.assert_allclose(Mk[c], cp.M, rtol=1e-15, atol=1e-15)
+    with pytest.raises(ValueError):
+        sr.sr_couplings_linear([1.0], B)
+
+
 @pytest.mark.parametrize("model,L", [(W.kagome_dm(1.0, 0.5), 4), (W.honeycomb_kitaev_gamma(0.1, -1.0, 0.5), 4),
                                      (W.rotated(W.kagome_dm(1.0, 0.3), np.eye(3)[[2, 0, 1]]), 3)])
 def test_tri_component_maps_are_signed_rotations(model, L):

@@ -276,3 +276,36 @@ def flatten_model(model: Model):
     to = np.asarray([c.to for c in model.couplings], dtype=np.int32).reshape(-1, 4)
     M = np.asarray([c.M for c in model.couplings], dtype=np.float64).reshape(-1, 3, 3)
     return (np.ascontiguousarray(cell.prim), np.ascontiguousarray(cell.basis), bonds, frm, to, M)
+
+
+def synthetic_state(of, model, seed: int = 0, amp: float = 0.3):
+    """A smooth frequency-dependent vertex that respects every symmetry of an SU(2) lattice
+    model: a function of the pair's Euclidean distance only, antisymmetric under s <-> u for
+    the density part and symmetric for the spin part, plus the bare coupling J/4.  `of` is any
+    object with the oracle flow's layout accessors (get_state, block, sites, position,
+    coupling, basis, mesh, N, nb); this function only fills values, it evaluates no flow
+    equation.  Returns (gamma, Gamma) in that layout."""
+    rng = np.random.default_rng(seed)
+    coef = rng.normal(size=(32, 4))
+    gam, G = of.get_state()
+    N = of.N
+    w = of.mesh
+    si = np.array([s for s in range(N) for u in range(s + 1)])
+    ui = np.array([u for s in range(N) for u in range(s + 1)])
+    S, U = w[si][:, None], w[ui][:, None]
+    T = w[None, :]
+    for b in range(of.nb):
+        blk = of.block(G, b)
+        sites = of.sites(b)
+        rb = of.basis[b]
+        for k, s in enumerate(sites):
+            dist = float(np.linalg.norm(of.position(s) - rb))
+            key = int(round(dist * 1000)) % 32
+            a0, a1, a2, a3 = coef[key]
+            J = of.coupling(b, k)
+            damp = np.exp(-0.3 * dist)
+            blk[k, 0] = amp * damp * a0 * (S - U) / (1.0 + S + U + T)
+            for c in (1, 2, 3):
+                blk[k, c] = J[c - 1, c - 1] / 4.0 + amp * damp * (a1 / (1.0 + 0.5 * (S + U) + T) + a2 * np.exp(-(S + U) / (1.0 + T)) * 0.2)
+    gam = 0.2 * np.tanh(w) + 0.05 * w / (1 + w)
+    return gam, G
