@@ -198,11 +198,11 @@ def _algorithmic_flops(counts: np.ndarray, N: int, Ns: int, nc: int, P: int, npr
 
 
 def _kernel_hash() -> str:
-    """Hash of the device code of the vertex kernels: kernels.cuh, tc.cuh and flow.cu up to its
-    host-side objects (changes to host code leave committed ncu figures valid)."""
+    """Hash of the device code of the vertex kernels: kernels.cuh, tc.cuh, su2f.cuh and flow.cu
+    up to its host-side objects (changes to host code leave committed ncu figures valid)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2109_13317_gb300", "csrc")
-    for f in ("kernels.cuh", "tc.cuh"):
+    for f in ("kernels.cuh", "tc.cuh", "su2f.cuh"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     with open(os.path.join(csrc, "flow.cu"), "rb") as fh:

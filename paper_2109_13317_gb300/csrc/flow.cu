@@ -1574,9 +1574,12 @@ static sr_status run_rhs(sr_flow* f, double lam, const double* gam_s, const doub
         if (g.nc == 2 && f->dense && f->use_tc)
             k_gamma_rhs_f32_tc<<<std::min(blocks, f->tc_grid), kThreads, f->smem_tc, f->stream>>>(g, tb, Gf_s, Gs, f->nxf.p, f->nWf.p, f->ncount.p, dG_o,
                                                                             f->tcfail.p, (long)pb * g.N, (long)pe * g.N);
+        else if (g.nc == 2 && f->dense && f->su2f_qb > 0 && su2f::cache_for(g.nsp))
+            k_gamma_rhs_su2f<true><<<blocks, su2f::threads_for(g.nsp), f->smem_su2f, f->stream>>>(
+                g, tb, Gf_s, f->has_swap ? (int)g.nentp : 0, f->nxf.p, f->nWf.p, f->ncount.p, dG_o, f->su2f_qb, pb);
         else if (g.nc == 2 && f->dense && f->su2f_qb > 0)
-            k_gamma_rhs_su2f<<<blocks, su2f::threads_for(g.nsp), f->smem_su2f, f->stream>>>(g, tb, Gf_s, f->has_swap ? (int)g.nentp : 0, f->nxf.p,
-                                                                            f->nWf.p, f->ncount.p, dG_o, f->su2f_qb, pb);
+            k_gamma_rhs_su2f<false><<<blocks, su2f::threads_for(g.nsp), f->smem_su2f, f->stream>>>(
+                g, tb, Gf_s, f->has_swap ? (int)g.nentp : 0, f->nxf.p, f->nWf.p, f->ncount.p, dG_o, f->su2f_qb, pb);
         else if (g.nc == 2 && f->dense)
             k_gamma_rhs_f32<2, true><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, Gf_s, Gs, f->nxf.p, f->nWf.p, f->ncount.p, dG_o, pb);
         else if (g.nc == 2)
@@ -1952,12 +1955,14 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
             // FP32-mixed SU2 kernel: the largest node block (64, 32, 16) whose shared memory
             // leaves room for the resident CTAs its registers allow, else the smallest that fits
             const int nth = su2f::threads_for(g.nsp);
-            const int ctas = su2f::kMinCtas * su2f::kThreadsS / nth;
+            const int ctas = (su2f::cache_for(g.nsp) ? su2f::kMinCtasCached : su2f::kMinCtas) * su2f::kThreadsS / nth;
             for (int qb : {64, 32, 16}) {
                 const size_t b = su2f::layout(g.N, g.Ns, g.nsp, qb, nth).total;
                 if (b <= 227 * 1024 / ctas || (qb == 16 && b <= 227 * 1024)) { f->su2f_qb = qb; f->smem_su2f = b; break; }
             }
-            if (f->su2f_qb > 0) CK(ensure_smem((const void*)k_gamma_rhs_su2f, f->smem_su2f));
+            if (f->su2f_qb > 0)
+                CK(ensure_smem(su2f::cache_for(g.nsp) ? (const void*)k_gamma_rhs_su2f<true> : (const void*)k_gamma_rhs_su2f<false>,
+                               f->smem_su2f));
         }
         CK(ensure_smem((const void*)k_gamma_rhs_f32<2, false>, f->smem_rhs));
         CK(ensure_smem((const void*)k_gamma_rhs_f32<4, false>, f->smem_rhs));
@@ -2598,7 +2603,7 @@ __global__ void __launch_bounds__(kThreads, 7) k_gamma_persistent(const BInst* _
 // k_gamma_rhs_su2f: CTAs take `chunk` consecutive units per atomic step (consecutive units
 // mostly belong to one instance, whose tables are staged once), and the kernel is not capped
 // in registers (the per-triple function keeps its corner slots in registers).
-__global__ void __launch_bounds__(kThreads) k_gamma_persistent_su2f(const BInst* __restrict__ I, int i_begin, int i_end,
+__global__ void __launch_bounds__(su2f::kThreadsS, su2f::kMinCtas - 1) k_gamma_persistent_su2f(const BInst* __restrict__ I, int i_begin, int i_end,
                                                                     long u_begin, long u_end,
                                                                     unsigned long long* __restrict__ counter, int chunk) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -2635,7 +2640,7 @@ __global__ void __launch_bounds__(kThreads) k_gamma_persistent_su2f(const BInst*
                 cur_end = B.unit0 + (long)B.g.npair * B.g.N;
             }
             const long local = u - B.unit0;
-            su2f::triple(B.g, B.tb, B.Gf, B.with_swap ? (int)B.g.nentp : 0, B.nxf, B.nWf, B.ncount, B.dG,
+            su2f::triple<false>(B.g, B.tb, B.Gf, B.with_swap ? (int)B.g.nentp : 0, B.nxf, B.nWf, B.ncount, B.dG,
                          (int)(local / B.g.N), (int)(local % B.g.N), smem, B.qc);
         }
     }
@@ -2703,6 +2708,7 @@ struct BClass {
     long u_begin, u_end;  // work units
     size_t smem;
     int occ, ctas, qc;
+    int threads;          // CTA size of the class's persistent kernel
     double ms;            // autotuned vertex-flow time of the class
     bool per_inst;        // the instances' own vertex kernels, one launch each, instead of the
                           // class's persistent kernel
@@ -2747,9 +2753,12 @@ static void launch_class(sr_batch* b, int k, cudaStream_t st) {
             const BInst& B = b->inst[i];
             const unsigned blocks = (unsigned)(B.g.npair * B.g.N);
             const size_t sm = b->inst_smem[i];
-            if (c.kind == 0)
-                k_gamma_rhs_su2f<<<blocks, su2f::threads_for(B.g.nsp), sm, st>>>(B.g, B.tb, B.Gf, B.with_swap ? (int)B.g.nentp : 0, B.nxf, B.nWf,
-                                                               B.ncount, B.dG, B.qb_own, 0);
+            if (c.kind == 0 && su2f::cache_for(B.g.nsp))
+                k_gamma_rhs_su2f<true><<<blocks, su2f::threads_for(B.g.nsp), sm, st>>>(
+                    B.g, B.tb, B.Gf, B.with_swap ? (int)B.g.nentp : 0, B.nxf, B.nWf, B.ncount, B.dG, B.qb_own, 0);
+            else if (c.kind == 0)
+                k_gamma_rhs_su2f<false><<<blocks, su2f::threads_for(B.g.nsp), sm, st>>>(
+                    B.g, B.tb, B.Gf, B.with_swap ? (int)B.g.nentp : 0, B.nxf, B.nWf, B.ncount, B.dG, B.qb_own, 0);
             else if (c.kind == 1)
                 k_gamma_rhs_f32<2, false><<<blocks, kThreads, sm, st>>>(B.g, B.tb, B.Gf, B.Gs, B.nxf, B.nWf, B.ncount, B.dG, 0);
             else
@@ -2760,7 +2769,7 @@ static void launch_class(sr_batch* b, int k, cudaStream_t st) {
     const dim3 grid(b->nsm * c.ctas);
     unsigned long long* ctr = b->counter.p + k;
     if (c.kind == 0)
-        k_gamma_persistent_su2f<<<grid, kThreads, c.smem, st>>>(b->dinst.p, c.i_begin, c.i_end, c.u_begin, c.u_end, ctr,
+        k_gamma_persistent_su2f<<<grid, c.threads, c.smem, st>>>(b->dinst.p, c.i_begin, c.i_end, c.u_begin, c.u_end, ctr,
                                                                kUnitChunk);
     else if (c.kind == 1)
         k_gamma_persistent<2, false><<<grid, kThreads, c.smem, st>>>(b->dinst.p, c.i_begin, c.i_end, c.u_begin, c.u_end, ctr);
@@ -2855,7 +2864,7 @@ static sr_status batch_tune(sr_batch* b) {
             for (int qb : {16, 32, 64}) {
                 bool fits = true;
                 for (int i = c.i_begin; i < c.i_end; ++i)
-                    if (su2f::layout(b->inst[i].g.N, b->inst[i].g.Ns, b->inst[i].g.nsp, qb, kThreads).total > c.smem) fits = false;
+                    if (su2f::layout(b->inst[i].g.N, b->inst[i].g.Ns, b->inst[i].g.nsp, qb, c.threads).total > c.smem) fits = false;
                 if (fits) qcand.push_back(qb);
             }
         } else {
@@ -2945,9 +2954,10 @@ extern "C" sr_status sr_batch_create(int n, sr_flow* const* flows, sr_batch** ou
             return fail(SR_EUNSUPPORTED, "flow %d: lattice too large for the batched SU2 kernel", i);
         // SU2 dense: shared memory of the largest node block that fits (the tuner may pick it)
         if (kind[i] == 0) {
+            const int nth = su2f::threads_for(f->g.nsp);
             sm[i] = f->smem_su2f;
             for (int qb : {64, 32}) {
-                const size_t bq = su2f::layout(f->g.N, f->g.Ns, f->g.nsp, qb, kThreads).total;
+                const size_t bq = su2f::layout(f->g.N, f->g.Ns, f->g.nsp, qb, nth).total;
                 if (bq <= 227 * 1024 / 3) { sm[i] = std::max(sm[i], bq); break; }
             }
         } else {
@@ -2974,9 +2984,10 @@ extern "C" sr_status sr_batch_create(int n, sr_flow* const* flows, sr_batch** ou
             BClass c{};
             c.kind = kind[k];
             c.i_begin = idx; c.u_begin = unit; c.smem = sm[k]; c.qc = kind[k] == 0 ? f->su2f_qb : kQF;
+            c.threads = kind[k] == 0 ? su2f::threads_for(f->g.nsp) : kThreads;
             if (sm[k] > 227 * 1024) return fail(SR_EUNSUPPORTED, "instance needs %zu bytes of shared memory", sm[k]);
             CK(ensure_smem(persistent_fn(c.kind), sm[k]));
-            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, persistent_fn(c.kind), kThreads, sm[k]));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, persistent_fn(c.kind), c.threads, sm[k]));
             if (c.occ < 1) return fail(SR_EUNSUPPORTED, "persistent kernel cannot be resident with %zu bytes", sm[k]);
             c.ctas = c.occ;
             b->cls.push_back(c);

@@ -31,6 +31,14 @@ constexpr int kMinCtas = 6;      // resident CTAs of kThreadsS threads the regis
 // per SM: cheaper barriers, measured faster), else 128 (enough row threads per node block).
 __host__ __device__ inline int threads_for(int nsp) { return nsp <= 32 ? 64 : kThreadsS; }
 
+// Whether the row threads keep the four corners of their row in registers from node to node
+// (a corner shared by consecutive nodes is loaded once): it saves L1 traffic but costs about
+// 45 registers, which pays off for wide rows (long streams at 128 threads), not for narrow ones
+// (measured: pyrochlore range 6, 48 sites, 13.8 -> 12.8 ms; square range 7, 20 sites,
+// 1.54 -> 1.70 ms).
+__host__ __device__ inline bool cache_for(int nsp) { return nsp > 32; }
+constexpr int kMinCtasCached = 4;   // resident CTAs of kThreadsS threads for the cached variant
+
 // Descriptor of one vertex row: the four corners (two mesh points along each interpolated axis)
 // with their element offsets in the shadow [Gf | Gs] and weights.
 struct __align__(16) DescS {
@@ -58,7 +66,8 @@ __device__ __forceinline__ void axis2(const float* w, const float* invh, const G
 // (s -> -s and u -> -u exchange the sites: the row is read from the exchanged shadow Gs); the
 // two other axes give the four corners.  The exact axis after the fold is selected
 // arithmetically, so lanes of a warp take one path.  wn multiplies every weight (the node
-// weight of weighted rows).
+// weight of weighted rows).  SLOTS: corners in parity-slot order (for the register cache).
+template <bool SLOTS = false>
 __device__ __forceinline__ void make_desc_s(float s, float t, float u, int ex_slot, int ex_idx, int swap_off,
                                             const float* w, const float* invh, const Geo& g, int rowp, float wn,
                                             DescS* dst) {
@@ -93,6 +102,26 @@ __device__ __forceinline__ void make_desc_s(float s, float t, float u, int ex_sl
         off[k] = ((hi * (hi + 1) / 2 + lo) * g.N + jt) * rowp + so;
         wd[k] = (flip != below) ? -wt : wt;
         ws[k] = wt;
+    }
+    if (SLOTS) {
+        // corner (b0, b1) has mesh-index parities (k0 ^ b0, k1 ^ b1) & 1: put it in slot
+        // k ^ x, x = parities of corner (0, 0), so that a corner shared by consecutive nodes
+        // keeps its slot (two layers of selects, static register indices)
+        const bool q0 = k0 & 1, q1 = k1 & 1;
+        int o1[4];
+        float d1[4], s1[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            o1[j] = q0 ? off[j ^ 1] : off[j];
+            d1[j] = q0 ? wd[j ^ 1] : wd[j];
+            s1[j] = q0 ? ws[j ^ 1] : ws[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            off[j] = q1 ? o1[j ^ 2] : o1[j];
+            wd[j] = q1 ? d1[j ^ 2] : d1[j];
+            ws[j] = q1 ? s1[j ^ 2] : s1[j];
+        }
     }
     *reinterpret_cast<int4*>(dst->off) = make_int4(off[0], off[1], off[2], off[3]);
     *reinterpret_cast<float4*>(dst->wd) = make_float4(wd[0], wd[1], wd[2], wd[3]);
@@ -155,6 +184,7 @@ __host__ __device__ inline Layout layout(int N, int Ns, int nsp, int qb, int thr
 // components, written to dG (FP64).  Gf: FP32 shadow (padded layout); the exchanged shadow
 // starts swap_off floats later (swap_off = 0 when the site exchange is trivial).  qb:
 // integration nodes per shared-memory block.  Needs blockDim.x >= nsp / 2 (one stream).
+template <bool CACHE>
 __device__ void triple(const Geo& g, const Tabs& tb, const float* __restrict__ Gf, const int swap_off,
                        const float* __restrict__ nx, const float* __restrict__ nW, const int* __restrict__ ncount,
                        double* __restrict__ dG, const int p, const int ti, unsigned char* smem, const int qb) {
@@ -232,7 +262,7 @@ __device__ void triple(const Geo& g, const Tabs& tb, const float* __restrict__ G
                 // the node weight rides on row A (all channels) and on the on-site row D
                 const float wn = (rw == 0 || rw == 3) ? Wp[q0 + q] : 1.0f;
                 if (rw < 2) {
-                    make_desc_s(a, b, c, exs, vi, swap_off, wm, ih, g, rowp, wn, &desc[q * 2 + rw]);
+                    make_desc_s<CACHE>(a, b, c, exs, vi, swap_off, wm, ih, g, rowp, wn, &desc[q * 2 + rw]);
                 } else {
                     float v0, v1;
                     onsite_values(a, b, c, exs, vi, wm, ih, g, rowp, Gf, wn, v0, v1);
@@ -246,6 +276,14 @@ __device__ void triple(const Geo& g, const Tabs& tb, const float* __restrict__ G
             {
                 const int L = (qn + S - 1) / S;
                 const int qa = stream * L, qe = min(qa + L, qn);
+                float4 c0[4], c1[4];   // corner rows of this thread's sites, both components
+                int tag[4];            // CACHE: offset of the corner each slot holds
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    c0[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    c1[k] = c0[k];
+                    tag[k] = -1;
+                }
                 for (int j = 0; j < L; ++j) {
                     const int q = qa + j;
                     const bool act = in_stream && q < qe;
@@ -255,15 +293,15 @@ __device__ void triple(const Geo& g, const Tabs& tb, const float* __restrict__ G
                         const int4 off = *reinterpret_cast<const int4*>(d.off);
                         const float4 wd = *reinterpret_cast<const float4*>(d.wd);
                         const float4 ws = *reinterpret_cast<const float4*>(d.ws);
-                        float4 c0[4], c1[4];
-                        c0[0] = __ldg(reinterpret_cast<const float4*>(pb0 + off.x));
-                        c0[1] = __ldg(reinterpret_cast<const float4*>(pb0 + off.y));
-                        c0[2] = __ldg(reinterpret_cast<const float4*>(pb0 + off.z));
-                        c0[3] = __ldg(reinterpret_cast<const float4*>(pb0 + off.w));
-                        c1[0] = __ldg(reinterpret_cast<const float4*>(pb1 + off.x));
-                        c1[1] = __ldg(reinterpret_cast<const float4*>(pb1 + off.y));
-                        c1[2] = __ldg(reinterpret_cast<const float4*>(pb1 + off.z));
-                        c1[3] = __ldg(reinterpret_cast<const float4*>(pb1 + off.w));
+                        const int o4[4] = {off.x, off.y, off.z, off.w};
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            if (!CACHE || o4[k] != tag[k]) {
+                                c0[k] = __ldg(reinterpret_cast<const float4*>(pb0 + o4[k]));
+                                c1[k] = __ldg(reinterpret_cast<const float4*>(pb1 + o4[k]));
+                                tag[k] = o4[k];
+                            }
+                        }
                         v0 = wsum4(c0, wd);
                         v1 = wsum4(c1, ws);
                     }
@@ -397,11 +435,14 @@ __device__ void triple(const Geo& g, const Tabs& tb, const float* __restrict__ G
 
 }  // namespace su2f
 
-// FP32-mixed SU(2) vertex flow, one CTA per stored frequency triple.
-__global__ void __launch_bounds__(su2f::kThreadsS, su2f::kMinCtas) k_gamma_rhs_su2f(Geo g, Tabs tb, const float* __restrict__ Gf, int swap_off,
+// FP32-mixed SU(2) vertex flow, one CTA per stored frequency triple (CACHE: corner rows kept in
+// registers from node to node).
+template <bool CACHE>
+__global__ void __launch_bounds__(su2f::kThreadsS, CACHE ? su2f::kMinCtasCached : su2f::kMinCtas)
+k_gamma_rhs_su2f(Geo g, Tabs tb, const float* __restrict__ Gf, int swap_off,
                                                              const float* __restrict__ nx, const float* __restrict__ nW,
                                                              const int* __restrict__ ncount, double* __restrict__ dG, int qb,
                                                              int p0) {
     extern __shared__ __align__(16) unsigned char smem[];
-    su2f::triple(g, tb, Gf, swap_off, nx, nW, ncount, dG, p0 + (int)(blockIdx.x / g.N), blockIdx.x % g.N, smem, qb);
+    su2f::triple<CACHE>(g, tb, Gf, swap_off, nx, nW, ncount, dG, p0 + (int)(blockIdx.x / g.N), blockIdx.x % g.N, smem, qb);
 }
