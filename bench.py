@@ -470,6 +470,15 @@ def _batched_sweep(sr, torch, steps=20):
     parallel = b.parallel_classes
     batched_ms = info["run_ms"]
     after_b = [f.get_state()[1] for f in flows]
+    # each launch form on its own over the same window (the persistent form tuned for itself)
+    forms = {}
+    for mode, name in ((1, "persistent_kernels"), (2, "per_instance_kernels")):
+        for f, (g, G) in zip(flows, saved):
+            f.set_state(float(window[0]), g, G)
+        b.force_launch(mode)
+        b.run(window, use_graph=True, autotune=True)
+        forms[name] = {"ms_per_step": b.info()["run_ms"] / steps, "parallel_classes": b.parallel_classes}
+    b.force_launch(0)
     for f, (g, G) in zip(flows, saved):
         f.set_state(float(window[0]), g, G)
     torch.cuda.synchronize()
@@ -491,6 +500,7 @@ def _batched_sweep(sr, torch, steps=20):
             "batched_ms_per_step": batched_ms / steps, "batched_entries_per_s": n_ent * steps / (batched_ms * 1e-3),
             "sequential_ms_per_step": seq_ms / steps, "sequential_entries_per_s": n_ent * steps / (seq_ms * 1e-3),
             "speedup": seq_ms / batched_ms, "size_classes": classes, "parallel_classes": parallel,
+            "launch_forms": forms,
             "max_rel_diff_batched_vs_sequential": diff}
 
 
