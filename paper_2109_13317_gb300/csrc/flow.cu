@@ -1830,7 +1830,7 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
         const int Ns = lat->Ns;
         std::vector<int> sm((size_t)Ns * 16), om((size_t)Ns * 16);
         for (int r = 0; r < Ns; ++r)
-            for (int c = 0; c < 16; ++c) { sm[r * 16 + c] = lat->swap_map16[r][c]; om[r * 16 + c] = lat->onsite_map16[r][c]; }
+            for (int c = 0; c < 16; ++c) { sm[c * Ns + r] = lat->swap_map16[r][c]; om[r * 16 + c] = lat->onsite_map16[r][c]; }
         if (Ns * 16 > 0x7fff) return fail(SR_EUNSUPPORTED, "TRI lattice-sum table: too many irreducible sites (%d)", Ns);
         const long P = (long)lat->rpa16.size();
         std::vector<uint4> rec((size_t)P * 4);

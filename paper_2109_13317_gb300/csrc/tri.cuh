@@ -22,7 +22,8 @@ namespace {
 constexpr int kQTri = 8;   // integration nodes per shared-memory block of the TRI kernel
 
 struct TabsT {
-    const int* swap_map;    // Ns * 16: component map of the exchanged pair (transposed)
+    const int* swap_map;    // 16 * Ns, component-major ([c * Ns + r]): component map of the
+                            // exchanged pair (transposed)
     const int* onsite_map;  // Ns * 16: component map of (rep, rep) onto site 0
     const uint4* lat_rec;   // P * 4: per lattice-sum table entry, 32 16-bit codes: the row slot
                             // (tri_slot(rA, stored component)) of A^{mu l} (codes 0..15, mu * 4 + l)
@@ -44,7 +45,7 @@ template <typename W, typename S>
 __device__ __forceinline__ W tri_value(const S* __restrict__ G, const Desc<W>& d, bool mneg, const Tabs& tb,
                                        const TabsT& tt, const Geo& g, int r, int c) {
     int rs = r, m = c;
-    if (d.swap) { rs = tb.swap_r[r]; m = tt.swap_map[r * 16 + c]; }
+    if (d.swap) { rs = tb.swap_r[r]; m = tt.swap_map[c * g.Ns + r]; }
     const int cs = m & 15;
     const S* base = G + cs * g.Ns + rs;
     const W* wgt = (cs & 3) == 0 ? d.wd : d.ws;
@@ -253,6 +254,27 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
     for (int o = tid; o < NG * row; o += blockDim.x) sh.part[o] = R(0);
     for (int o = tid; o < tri_lat_slots(g.Ns, tt.n_items, sizeof(R)) * 16; o += blockDim.x) sh.lat[o] = R(0);
 
+    // row entries e = tid + k blockDim.x (e = c Ns + r: component c of site r) of this thread,
+    // when they fit in registers: the shared-memory slot, the plain read (offset c Ns + r in
+    // the entry block of a corner; bit 30: density weights, bit 29: imaginary-class function)
+    // and the read through the site exchange (offset of the mapped component and site; bit
+    // 30: density weights, bit 28: sign of the map)
+    constexpr int kRE = 8;
+    const bool rows_reg = row <= kRE * (int)blockDim.x;
+    int e_slot[kRE], e_pl[kRE], e_sw[kRE];
+#pragma unroll
+    for (int k = 0; k < kRE; ++k) {
+        const int e = tid + k * (int)blockDim.x;
+        e_slot[k] = e_pl[k] = e_sw[k] = 0;
+        if (rows_reg && e < row) {
+            const int c = e / g.Ns, r = e - c * g.Ns;
+            e_slot[k] = tri_slot(r, c);
+            e_pl[k] = (c * g.Ns + r) | (((c & 3) == 0) << 30) | ((int)tri_mixed(c) << 29);
+            const int m = tt.swap_map[c * g.Ns + r], cs = m & 15;
+            e_sw[k] = (cs * g.Ns + tb.swap_r[r]) | (((cs & 3) == 0) << 30) | (((m & 16) != 0) << 28);
+        }
+    }
+
     for (int ch = 0; ch < 3; ++ch) {
         const int vi = ch == 0 ? si : (ch == 1 ? ti : ui);
         const int cidx = ch * g.N + vi;
@@ -280,12 +302,49 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
                 }
             }
             __syncthreads();
-            for (int idx = tid; idx < qn * 2 * row; idx += blockDim.x) {
-                const int q = idx / (2 * row), rem = idx % (2 * row);
-                const int rw = rem / row, e = rem % row;
-                const int r = e >> 4, c = e & 15;
-                sh.rows[(q * 2 + rw) * row + tri_slot(r, c)] =
-                    tri_value<R>(G, sh.desc[q * 4 + rw], sh.mneg[q * 4 + rw] != 0, tb, tt, g, r, c);
+            // rows, with the sites fastest so that a warp reads consecutive sites of one stored
+            // component (coalesced corner loads)
+            if (rows_reg) {
+                // every thread owns the same row entries at every node: descriptor in registers
+                // per (node, row), entry maps resolved once per CTA
+                for (int qr = 0; qr < qn * 2; ++qr) {
+                    const int dq = (qr >> 1) * 4 + (qr & 1);
+                    const Desc<R>& d = sh.desc[dq];
+                    const int n = d.n, sw = d.swap, mn = sh.mneg[dq];
+                    int o[4];
+                    R wd[4], ws[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) { o[j] = d.off[j]; wd[j] = d.wd[j]; ws[j] = d.ws[j]; }
+                    R* dst = sh.rows + qr * row;
+#pragma unroll
+                    for (int k = 0; k < kRE; ++k)
+                        if (tid + k * (int)blockDim.x < row) {
+                            const int pe = sw ? e_sw[k] : e_pl[k];
+                            const R* src = G + (pe & 0x0fffffff);
+                            const bool dens = (pe >> 30) & 1;
+                            R acc = R(0);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                if (j < n) acc = fmadd(dens ? wd[j] : ws[j], (R)src[o[j]], acc);
+                            const bool neg = (sw && ((e_sw[k] >> 28) & 1)) != (mn && ((e_pl[k] >> 29) & 1));
+                            dst[e_slot[k]] = neg ? -acc : acc;
+                        }
+                }
+            } else {
+                // a thread's item (node q, row rw, component c, site r) advances by blockDim.x
+                // without divisions
+                int qr = tid / row;                         // q * 2 + rw
+                int c = (tid - qr * row) / g.Ns;
+                int r = tid - qr * row - c * g.Ns;
+                const int dc = (int)blockDim.x / g.Ns, dr = (int)blockDim.x - dc * g.Ns;
+                for (int idx = tid; idx < qn * 2 * row; idx += blockDim.x) {
+                    const int dq = (qr >> 1) * 4 + (qr & 1);
+                    sh.rows[qr * row + tri_slot(r, c)] = tri_value<R>(G, sh.desc[dq], sh.mneg[dq] != 0, tb, tt, g, r, c);
+                    r += dr;
+                    c += dc;
+                    if (r >= g.Ns) { r -= g.Ns; ++c; }
+                    while (c >= 16) { c -= 16; ++qr; }
+                }
             }
             if (ch == 1)
                 for (int j = tid; j < qn * 2 * 16; j += blockDim.x) {
