@@ -2601,9 +2601,11 @@ __global__ void __launch_bounds__(kThreads, 7) k_gamma_persistent(const BInst* _
 
 // SU2 instances (dense lattice sum) in one persistent kernel over the per-triple function of
 // k_gamma_rhs_su2f: CTAs take `chunk` consecutive units per atomic step (consecutive units
-// mostly belong to one instance, whose tables are staged once), and the kernel is not capped
-// in registers (the per-triple function keeps its corner slots in registers).
-__global__ void __launch_bounds__(su2f::kThreadsS, su2f::kMinCtas - 1) k_gamma_persistent_su2f(const BInst* __restrict__ I, int i_begin, int i_end,
+// mostly belong to one instance, whose tables are staged once), with the register budget of
+// the instances' own kernel.  CACHE: the corner-row cache of k_gamma_rhs_su2f<true> (classes of
+// wide rows).
+template <bool CACHE>
+__global__ void __launch_bounds__(su2f::kThreadsS, CACHE ? su2f::kMinCtasCached : su2f::kMinCtas) k_gamma_persistent_su2f(const BInst* __restrict__ I, int i_begin, int i_end,
                                                                     long u_begin, long u_end,
                                                                     unsigned long long* __restrict__ counter, int chunk) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -2640,8 +2642,12 @@ __global__ void __launch_bounds__(su2f::kThreadsS, su2f::kMinCtas - 1) k_gamma_p
                 cur_end = B.unit0 + (long)B.g.npair * B.g.N;
             }
             const long local = u - B.unit0;
-            su2f::triple<false>(B.g, B.tb, B.Gf, B.with_swap ? (int)B.g.nentp : 0, B.nxf, B.nWf, B.ncount, B.dG,
-                         (int)(local / B.g.N), (int)(local % B.g.N), smem, B.qc);
+            // the instance's geometry and tables as locals: the per-triple function's stores to
+            // shared memory would otherwise force re-reads of every field from the shared copy
+            const Geo g = B.g;
+            const Tabs tb = B.tb;
+            su2f::triple<CACHE>(g, tb, B.Gf, B.with_swap ? (int)g.nentp : 0, B.nxf, B.nWf, B.ncount, B.dG,
+                                (int)(local / g.N), (int)(local % g.N), smem, B.qc);
         }
     }
 }
@@ -2651,8 +2657,8 @@ constexpr int kUnitChunk = 4;
 
 // Persistent kernel of an instance kind (0: SU2 dense lattice sum, 1: SU2 product list, 2: XYZ);
 // every size class holds instances of one kind.
-static const void* persistent_fn(int kind) {
-    if (kind == 0) return (const void*)k_gamma_persistent_su2f;
+static const void* persistent_fn(int kind, bool cache = false) {
+    if (kind == 0) return cache ? (const void*)k_gamma_persistent_su2f<true> : (const void*)k_gamma_persistent_su2f<false>;
     if (kind == 1) return (const void*)k_gamma_persistent<2, false>;
     return (const void*)k_gamma_persistent<4, false>;
 }
@@ -2709,6 +2715,7 @@ struct BClass {
     size_t smem;
     int occ, ctas, qc;
     int threads;          // CTA size of the class's persistent kernel
+    bool cache;           // SU2: the corner-row cache (k_gamma_rhs_su2f<true>) for wide rows
     double ms;            // autotuned vertex-flow time of the class
     bool per_inst;        // the instances' own vertex kernels, one launch each, instead of the
                           // class's persistent kernel
@@ -2769,8 +2776,8 @@ static void launch_class(sr_batch* b, int k, cudaStream_t st) {
     const dim3 grid(b->nsm * c.ctas);
     unsigned long long* ctr = b->counter.p + k;
     if (c.kind == 0)
-        k_gamma_persistent_su2f<<<grid, c.threads, c.smem, st>>>(b->dinst.p, c.i_begin, c.i_end, c.u_begin, c.u_end, ctr,
-                                                               kUnitChunk);
+        (c.cache ? k_gamma_persistent_su2f<true> : k_gamma_persistent_su2f<false>)<<<grid, c.threads, c.smem, st>>>(
+            b->dinst.p, c.i_begin, c.i_end, c.u_begin, c.u_end, ctr, kUnitChunk);
     else if (c.kind == 1)
         k_gamma_persistent<2, false><<<grid, kThreads, c.smem, st>>>(b->dinst.p, c.i_begin, c.i_end, c.u_begin, c.u_end, ctr);
     else
@@ -2857,33 +2864,43 @@ static sr_status batch_tune(sr_batch* b) {
             total += ms;
             continue;
         }
-        std::vector<int> ctas_c;
-        for (int v = c.occ; v >= 1; v = v / 2) { ctas_c.push_back(v); if (v == 1) break; }
-        std::vector<int> qcand;
+        // candidates (node block, shared memory, resident CTAs per SM): SU2 launches with the
+        // shared memory its node block needs, so small blocks raise the occupancy
+        struct Cand { int qc; size_t smem; int occ; };
+        std::vector<Cand> cand;
         if (c.kind == 0) {
             for (int qb : {16, 32, 64}) {
-                bool fits = true;
+                size_t need = 0;
                 for (int i = c.i_begin; i < c.i_end; ++i)
-                    if (su2f::layout(b->inst[i].g.N, b->inst[i].g.Ns, b->inst[i].g.nsp, qb, c.threads).total > c.smem) fits = false;
-                if (fits) qcand.push_back(qb);
+                    need = std::max(need, su2f::layout(b->inst[i].g.N, b->inst[i].g.Ns, b->inst[i].g.nsp, qb, c.threads).total);
+                if (need > 227 * 1024) continue;
+                CK(ensure_smem(persistent_fn(c.kind, c.cache), need));
+                int occ = 0;
+                CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_fn(c.kind, c.cache), c.threads, need));
+                if (occ >= 1) cand.push_back({qb, need, occ});
             }
         } else {
-            qcand.assign(qcs, qcs + 3);
+            for (int qb : qcs) cand.push_back({qb, c.smem, c.occ});
         }
+        if (cand.empty()) return fail(SR_EUNSUPPORTED, "size class %d: no node block fits the persistent kernel", k);
         double best = 1e300;
         int bq = c.qc, bc = c.ctas;
-        for (int qc : qcand)
-            for (int ct : ctas_c) {
-                for (int i = c.i_begin; i < c.i_end; ++i) b->inst[i].qc = qc;
+        size_t bs = c.smem;
+        for (const Cand& q : cand)
+            for (int ct = q.occ; ct >= 1; ct = ct > 2 ? ct - (ct + 3) / 4 : ct - 1) {
+                for (int i = c.i_begin; i < c.i_end; ++i) b->inst[i].qc = q.qc;
                 c.ctas = ct;
+                c.smem = q.smem;
                 if (sr_status s = batch_upload(b)) return s;
                 double ms = 0;
                 if (sr_status s = batch_time_class(b, k, &ms)) return s;
-                if (ms < best) { best = ms; bq = qc; bc = ct; }
+                if (ms < best) { best = ms; bq = q.qc; bc = ct; bs = q.smem; }
+                if (ct <= q.occ / 2) break;   // fewer CTAs than half the occupancy: not worth timing
             }
         for (int i = c.i_begin; i < c.i_end; ++i) b->inst[i].qc = bq;
         c.ctas = bc;
         c.qc = bq;
+        c.smem = bs;
         c.ms = best;
         if (b->force == 0) {
             c.per_inst = true;
@@ -2966,8 +2983,12 @@ extern "C" sr_status sr_batch_create(int n, sr_flow* const* flows, sr_batch** ou
     }
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
+    // SU2 instances whose own kernel is k_gamma_rhs_su2f<true> (wide rows) form classes of their
+    // own, so that every class's persistent kernel has its instances' CTA size and variant
+    auto wide = [&](int i) { return kind[i] == 0 && su2f::cache_for(flows[i]->g.nsp); };
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
         if (kind[a] != kind[c]) return kind[a] < kind[c];
+        if (wide(a) != wide(c)) return wide(a);
         if (sm[a] != sm[c]) return sm[a] > sm[c];
         return flows[a]->g.nent > flows[c]->g.nent;
     });
@@ -2978,16 +2999,18 @@ extern "C" sr_status sr_batch_create(int n, sr_flow* const* flows, sr_batch** ou
     for (int idx = 0; idx < n; ++idx) {
         const int k = order[idx];
         sr_flow* f = flows[k];
-        // a new class for a new kind, or when the shared memory drops below 2/3 of the
-        // class's largest
-        if (b->cls.empty() || b->cls.back().kind != kind[k] || sm[k] * 3 < b->cls.back().smem * 2) {
+        // a new class for a new kind or row width, or when the shared memory drops below 2/3 of
+        // the class's largest
+        if (b->cls.empty() || b->cls.back().kind != kind[k] || b->cls.back().cache != wide(k) ||
+            sm[k] * 3 < b->cls.back().smem * 2) {
             BClass c{};
             c.kind = kind[k];
             c.i_begin = idx; c.u_begin = unit; c.smem = sm[k]; c.qc = kind[k] == 0 ? f->su2f_qb : kQF;
             c.threads = kind[k] == 0 ? su2f::threads_for(f->g.nsp) : kThreads;
+            c.cache = kind[k] == 0 && su2f::cache_for(f->g.nsp);
             if (sm[k] > 227 * 1024) return fail(SR_EUNSUPPORTED, "instance needs %zu bytes of shared memory", sm[k]);
-            CK(ensure_smem(persistent_fn(c.kind), sm[k]));
-            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, persistent_fn(c.kind), c.threads, sm[k]));
+            CK(ensure_smem(persistent_fn(c.kind, c.cache), sm[k]));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, persistent_fn(c.kind, c.cache), c.threads, sm[k]));
             if (c.occ < 1) return fail(SR_EUNSUPPORTED, "persistent kernel cannot be resident with %zu bytes", sm[k]);
             c.ctas = c.occ;
             b->cls.push_back(c);

@@ -84,3 +84,43 @@ def test_batch_instances_against_oracle(mode):
         for c in range(fl.n_comp):
             assert np.abs(got[:, :, c] - exp[:, :, c]).max() <= 1e-3 * np.abs(exp[:, :, c]).max(), c
     b.close()
+
+
+def test_batch_wide_rows_persistent_cached_kernel():
+    """A size class of wide rows (kagome range 7: 34 irreducible sites, more than 32) runs the
+    persistent kernel with the corner-row cache (k_gamma_persistent_su2f<true>); forced
+    persistent, it matches the same flows stepped one by one and the oracle."""
+    lams = W.lambda_list(8.0, 1.0, 5)
+    models = [(W.nn_heisenberg(W.kagome()), 7, O.mesh_exponential(4, 0.05, 10.0)),
+              (W.square_j1j2(1.0, 0.3), 2, O.mesh_exponential(5, 0.02, 20.0))]
+    single, batched, oracles = [], [], []
+    for m, L, ms in models:
+        lat = sr.Lattice.from_model(m, L)
+        single.append(sr.Flow(lat, ms, lams[0], sr.SR_FP32_MIXED))
+        batched.append((lat, sr.Flow(lat, ms, lams[0], sr.SR_FP32_MIXED)))
+        of = O.OracleFlow(m, L, ms)
+        for a, c in zip(lams[:-1], lams[1:]):
+            of.euler(a, c)
+        oracles.append(of)
+    assert batched[0][0].N_s > 32
+    for fl in single:
+        for lam in lams[1:]:
+            fl.step(lam, sr.SR_EULER)
+    b = sr.Batch([fl for _, fl in batched])
+    b.force_launch(1)
+    b.run(lams, use_graph=True, autotune=True)
+    assert not any(b.class_launches())
+    for f1, (lat, f2), of in zip(single, batched, oracles):
+        g1, G1 = f1.get_state()
+        g2, G2 = f2.get_state()
+        assert (G1 - G2).abs().max().item() <= 1e-5 * G1.abs().max().item()
+        assert (g1 - g2).abs().max().item() <= 1e-5 * g1.abs().max().item()
+        g_o, G_o = of.get_state()
+        assert np.abs(g2.cpu().numpy() - g_o).max() <= 1e-3 * np.abs(g_o).max()
+        exp = oracle_to_gpu(of, lat, G_o, f2.n_comp)
+        got = G2.cpu().numpy().reshape(exp.shape)
+        for c in range(f2.n_comp):
+            assert np.abs(got[:, :, c] - exp[:, :, c]).max() <= 1e-3 * np.abs(exp[:, :, c]).max(), c
+    b.close()
+    for f in single:
+        f.close()
