@@ -293,7 +293,9 @@ typedef struct sr_batch sr_batch;
 /* Group flows (all SR_FP32_MIXED, on the current device; the batch keeps pointers to them,
  * so they must outlive it).  The vertex flow of every instance runs in one persistent kernel
  * whose CTAs take (instance, stored triple) units from an atomic counter, largest instances
- * first; the paper's analogue is its dynamically balanced work units (Sec. 4.4). */
+ * first; the paper's analogue is its dynamically balanced work units (Sec. 4.4).  TRI flows
+ * (16 basis functions) run their own vertex kernel inside the batch's step; their self-energy
+ * flow, integration nodes, update and FP32 copy share the batch's launches. */
 sr_status sr_batch_create(int n, sr_flow* const* flows, sr_batch** out);
 
 /* Integrate every flow with Euler steps (Sec. 4.3) through the common cutoff list

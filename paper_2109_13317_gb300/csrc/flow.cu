@@ -2529,6 +2529,7 @@ namespace {
 struct BInst {
     Geo g;
     Tabs tb;
+    TabsT tt;       // TRI tables (kind 3)
     double* gam;
     double* G;
     float* Gf;
@@ -2542,7 +2543,7 @@ struct BInst {
     int* ncount;
     long unit0;     // first work unit (stored triple) of this instance
     int qc;         // integration nodes per shared-memory block
-    int kind;       // 0 SU2 dense, 1 SU2 product list, 2 XYZ
+    int kind;       // 0 SU2 dense, 1 SU2 product list, 2 XYZ, 3 TRI
     int with_swap;
     int qb_own;     // SU2 dense: node block of the instance's own kernel (k_gamma_rhs_su2f)
 };
@@ -2550,7 +2551,8 @@ struct BInst {
 __global__ void k_sigma_b(const BInst* __restrict__ I, const double* __restrict__ lams, const int* __restrict__ step) {
     const BInst& B = I[blockIdx.y];
     if ((int)blockIdx.x >= B.g.N) return;
-    sigma_rhs_block<double>(B.g, B.tb, B.tb.w, B.gam, B.G, lams[*step], B.dgam, blockIdx.x);
+    if (B.kind == 3) sigma_rhs_tri_block(B.g, B.tb, B.tt, B.tb.w, B.gam, B.G, lams[*step], B.dgam, blockIdx.x);
+    else sigma_rhs_block<double>(B.g, B.tb, B.tb.w, B.gam, B.G, lams[*step], B.dgam, blockIdx.x);
 }
 
 __global__ void k_nodes_b(const BInst* __restrict__ I, const double* __restrict__ lams, const int* __restrict__ step) {
@@ -2594,8 +2596,10 @@ __global__ void __launch_bounds__(kThreads, 7) k_gamma_persistent(const BInst* _
             __syncthreads();
         }
         const long local = u - B.unit0;
-        const int p = (int)(local / B.g.N), ti = (int)(local % B.g.N);
-        gamma_rhs_f32_triple<NC, DENSE>(B.g, B.tb, B.Gf, B.Gs, B.nxf, B.nWf, B.ncount, B.dG, p, ti, smem, B.qc);
+        const Geo g = B.g;   // locals: see k_gamma_persistent_su2f
+        const Tabs tb = B.tb;
+        const int p = (int)(local / g.N), ti = (int)(local % g.N);
+        gamma_rhs_f32_triple<NC, DENSE>(g, tb, B.Gf, B.Gs, B.nxf, B.nWf, B.ncount, B.dG, p, ti, smem, B.qc);
     }
 }
 
@@ -2655,8 +2659,9 @@ __global__ void __launch_bounds__(su2f::kThreadsS, CACHE ? su2f::kMinCtasCached 
 // Units per atomic step of the SU2 persistent kernel.
 constexpr int kUnitChunk = 4;
 
-// Persistent kernel of an instance kind (0: SU2 dense lattice sum, 1: SU2 product list, 2: XYZ);
-// every size class holds instances of one kind.
+// Persistent kernel of an instance kind (0: SU2 dense lattice sum, 1: SU2 product list, 2: XYZ;
+// TRI instances, kind 3, always run their own kernels); every size class holds instances of
+// one kind.
 static const void* persistent_fn(int kind, bool cache = false) {
     if (kind == 0) return cache ? (const void*)k_gamma_persistent_su2f<true> : (const void*)k_gamma_persistent_su2f<false>;
     if (kind == 1) return (const void*)k_gamma_persistent<2, false>;
@@ -2686,6 +2691,11 @@ __global__ void k_shadow_b(const BInst* __restrict__ I) {
     const Geo& g = B.g;
     const int rowp = g.nc * g.nsp;
     const long stride = (long)gridDim.x * blockDim.x;
+    if (B.kind == 3) {
+        // TRI: FP32 copy of the state in its own layout
+        for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.nent; i += stride) B.Gf[i] = (float)B.G[i];
+        return;
+    }
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.nentp; i += stride) {
         const long pt = i / rowp;
         const int rem = (int)(i % rowp);
@@ -2754,7 +2764,7 @@ struct sr_batch {
 
 static void launch_class(sr_batch* b, int k, cudaStream_t st) {
     const BClass& c = b->cls[k];
-    if (c.per_inst) {
+    if (c.per_inst || c.kind == 3) {
         // the instances' own vertex kernels (as a single flow launches them), back to back
         for (int i = c.i_begin; i < c.i_end; ++i) {
             const BInst& B = b->inst[i];
@@ -2768,6 +2778,8 @@ static void launch_class(sr_batch* b, int k, cudaStream_t st) {
                     B.g, B.tb, B.Gf, B.with_swap ? (int)B.g.nentp : 0, B.nxf, B.nWf, B.ncount, B.dG, B.qb_own, 0);
             else if (c.kind == 1)
                 k_gamma_rhs_f32<2, false><<<blocks, kThreads, sm, st>>>(B.g, B.tb, B.Gf, B.Gs, B.nxf, B.nWf, B.ncount, B.dG, 0);
+            else if (c.kind == 3)
+                k_gamma_rhs_tri<float><<<blocks, kThreads, sm, st>>>(B.g, B.tb, B.tt, B.tb.w, B.Gf, B.nx, B.nW, B.ncount, B.dG, 0);
             else
                 k_gamma_rhs_f32<4, false><<<blocks, kThreads, sm, st>>>(B.g, B.tb, B.Gf, B.Gs, B.nxf, B.nWf, B.ncount, B.dG, 0);
         }
@@ -2856,7 +2868,7 @@ static sr_status batch_tune(sr_batch* b) {
     for (int k = 0; k < (int)b->cls.size(); ++k) {
         BClass& c = b->cls[k];
         c.per_inst = false;
-        if (b->force == 2) {
+        if (b->force == 2 || c.kind == 3) {
             c.per_inst = true;
             double ms = 0;
             if (sr_status s = batch_time_class(b, k, &ms)) return s;
@@ -2956,7 +2968,6 @@ extern "C" sr_status sr_batch_create(int n, sr_flow* const* flows, sr_batch** ou
         sr_flow* f = flows[i];
         if (!f) return fail(SR_EINVAL, "null flow %d", i);
         if (f->prec != SR_FP32_MIXED) return fail(SR_EUNSUPPORTED, "batched flows use the FP32-mixed kernels (flow %d is FP64)", i);
-        if (f->g.nc == 16) return fail(SR_EUNSUPPORTED, "batched flows are provided for the SU2 and XYZ cores (flow %d is TRI)", i);
         b->flows.push_back(f);
     }
     // instances grouped by kind and by the shared memory their vertex flow needs (each class
@@ -2966,7 +2977,7 @@ extern "C" sr_status sr_batch_create(int n, sr_flow* const* flows, sr_batch** ou
     std::vector<int> kind(n);
     for (int i = 0; i < n; ++i) {
         sr_flow* f = flows[i];
-        kind[i] = f->g.nc == 4 ? 2 : (f->dense ? 0 : 1);
+        kind[i] = f->g.nc == 16 ? 3 : (f->g.nc == 4 ? 2 : (f->dense ? 0 : 1));
         if (kind[i] == 0 && f->su2f_qb == 0)
             return fail(SR_EUNSUPPORTED, "flow %d: lattice too large for the batched SU2 kernel", i);
         // SU2 dense: shared memory of the largest node block that fits (the tuner may pick it)
@@ -2977,6 +2988,8 @@ extern "C" sr_status sr_batch_create(int n, sr_flow* const* flows, sr_batch** ou
                 const size_t bq = su2f::layout(f->g.N, f->g.Ns, f->g.nsp, qb, nth).total;
                 if (bq <= 227 * 1024 / 3) { sm[i] = std::max(sm[i], bq); break; }
             }
+        } else if (kind[i] == 3) {
+            sm[i] = f->smem_rhs;
         } else {
             sm[i] = f32_smem_bytes(f->g.Ns, f->g.nsp, f->g.nc, f->nprod, f->dense);
         }
@@ -3009,15 +3022,21 @@ extern "C" sr_status sr_batch_create(int n, sr_flow* const* flows, sr_batch** ou
             c.threads = kind[k] == 0 ? su2f::threads_for(f->g.nsp) : kThreads;
             c.cache = kind[k] == 0 && su2f::cache_for(f->g.nsp);
             if (sm[k] > 227 * 1024) return fail(SR_EUNSUPPORTED, "instance needs %zu bytes of shared memory", sm[k]);
-            CK(ensure_smem(persistent_fn(c.kind, c.cache), sm[k]));
-            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, persistent_fn(c.kind, c.cache), c.threads, sm[k]));
-            if (c.occ < 1) return fail(SR_EUNSUPPORTED, "persistent kernel cannot be resident with %zu bytes", sm[k]);
+            if (c.kind == 3) {
+                c.occ = 1;   // no persistent kernel: the instances' own launches
+                c.per_inst = true;
+            } else {
+                CK(ensure_smem(persistent_fn(c.kind, c.cache), sm[k]));
+                CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, persistent_fn(c.kind, c.cache), c.threads, sm[k]));
+                if (c.occ < 1) return fail(SR_EUNSUPPORTED, "persistent kernel cannot be resident with %zu bytes", sm[k]);
+            }
             c.ctas = c.occ;
             b->cls.push_back(c);
         }
         BInst B;
         B.g = f->g;
         B.tb = f->tabs();
+        B.tt = kind[k] == 3 ? f->tabs_tri() : TabsT{};
         B.gam = f->gam.p; B.G = f->G.p; B.Gf = f->Gf.p; B.Gs = f->has_swap ? f->Gf.p + f->g.nentp : f->Gf.p;
         B.dgam = f->dgam.p; B.dG = f->dG.p; B.nx = f->nx.p; B.nW = f->nW.p; B.nWf = f->nWf.p; B.nxf = f->nxf.p;
         B.ncount = f->ncount.p;
@@ -3029,7 +3048,7 @@ extern "C" sr_status sr_batch_create(int n, sr_flow* const* flows, sr_batch** ou
         if (kind[k] == 0) B.qc = f->su2f_qb;
         unit += (long)f->g.npair * f->g.N;
         b->inst.push_back(B);
-        b->inst_smem.push_back(kind[k] == 0 ? f->smem_su2f : f->smem_rhs);
+        b->inst_smem.push_back(kind[k] == 0 ? f->smem_su2f : f->smem_rhs);   // TRI: k_gamma_rhs_tri<float>
         b->cls.back().i_end = idx + 1;
         b->cls.back().u_end = unit;
     }
@@ -3140,7 +3159,7 @@ extern "C" sr_status sr_batch_force_launch(sr_batch* b, int mode) {
     if (!b || mode < 0 || mode > 2) return fail(SR_EINVAL, "mode must be 0 (autotune), 1 (persistent) or 2 (per instance)");
     b->force = mode;
     if (mode != 0)
-        for (BClass& c : b->cls) c.per_inst = mode == 2;
+        for (BClass& c : b->cls) c.per_inst = mode == 2 || c.kind == 3;
     return SR_OK;
 }
 

@@ -57,10 +57,11 @@ __device__ __forceinline__ W tri_value(const S* __restrict__ G, const Desc<W>& d
 
 // Self-energy flow (spin trace): dgamma(w) = -(1/2pi) sum_{w2 = +-Lambda} H / (w2 + gamma(w2)),
 // H = 2 sum_j Gamma^00_{ref j}(w+w2, 0, w-w2) - sum_k Gamma^kk_{ref ref}(w+w2, w2-w, 0).
-__global__ void k_sigma_rhs_tri(Geo g, Tabs tb, TabsT tt, const double* __restrict__ w, const double* __restrict__ gam,
-                                const double* __restrict__ G, double lam, double* __restrict__ dgam) {
+// (block n: the frequency w[n]; any block size up to 1024 threads)
+__device__ void sigma_rhs_tri_block(const Geo& g, const Tabs& tb, const TabsT& tt, const double* __restrict__ w,
+                                    const double* __restrict__ gam, const double* __restrict__ G, double lam,
+                                    double* __restrict__ dgam, int n) {
     __shared__ double red[2 * 32];
-    const int n = blockIdx.x;
     const double w1 = w[n];
     double H[2] = {0.0, 0.0};
     for (int sg = 0; sg < 2; ++sg) {
@@ -87,6 +88,11 @@ __global__ void k_sigma_rhs_tri(Geo g, Tabs tb, TabsT tt, const double* __restri
         acc += H[1] / (-lam + interp_odd(w, tb.invh, g.N, gam, -lam));
         dgam[n] = -acc / (2.0 * kPi);
     }
+}
+
+__global__ void k_sigma_rhs_tri(Geo g, Tabs tb, TabsT tt, const double* __restrict__ w, const double* __restrict__ gam,
+                                const double* __restrict__ G, double lam, double* __restrict__ dgam) {
+    sigma_rhs_tri_block(g, tb, tt, w, gam, G, lam, dgam, blockIdx.x);
 }
 
 // Shared-memory slot of component c of site r in a row: the 16 components of a site are

@@ -250,9 +250,6 @@ def test_tri_unsupported_requests():
     with pytest.raises(sr.SrError) as e:
         fl.tensor_cores = True
     assert e.value.status == sr.SR_EUNSUPPORTED
-    with pytest.raises(sr.SrError) as e:
-        sr.Batch([fl])
-    assert e.value.status == sr.SR_EUNSUPPORTED
     fl.close()
     f64 = sr.Flow(lat, mesh, 5.0, sr.SR_FP64)
     with pytest.raises(sr.SrError) as e:
@@ -260,6 +257,47 @@ def test_tri_unsupported_requests():
                         torch.zeros(f64.n_gamma, dtype=torch.float64, device="cuda"))
     assert e.value.status == sr.SR_EUNSUPPORTED
     f64.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["autotuned", "persistent_others"])
+def test_tri_flows_in_a_batch(mode):
+    """TRI instances inside a batch (beside an SU2 and an XYZ instance): their own vertex kernel
+    in the batch's captured step, the self-energy flow, nodes, update and FP32 copy in the
+    batch's launches.  Bit for bit the same TRI flow stepped alone, and within the FP32-mixed
+    tolerance of the oracle's TRI flow; forcing the persistent kernels (mode 1) leaves the TRI
+    class on its own kernels."""
+    lams = [8.0, 5.0, 3.0, 2.0, 1.4, 1.0]
+    tri_models = [W.kagome_dm(1.0, 0.5), W.rotated(W.kagome_dm(1.0, 0.4), _generic_rotation())]
+    mesh = O.mesh_exponential(5, 0.05, 10.0)
+    lats = [sr.Lattice.from_model(m, 2, backend=sr.SR_TRI) for m in tri_models]
+    alone = [sr.Flow(lat, mesh, lams[0], sr.SR_FP32_MIXED) for lat in lats]
+    inb = [sr.Flow(lat, mesh, lams[0], sr.SR_FP32_MIXED) for lat in lats]
+    others = [sr.Flow(sr.Lattice.from_model(W.square_j1j2(1.0, 0.3), 2), mesh, lams[0], sr.SR_FP32_MIXED),
+              sr.Flow(sr.Lattice.from_model(W.honeycomb_kitaev(0.2, -1.0), 1), mesh, lams[0], sr.SR_FP32_MIXED)]
+    for fl in alone:
+        for lam in lams[1:]:
+            fl.step(lam, sr.SR_EULER)
+    b = sr.Batch(inb + others)
+    b.force_launch(mode)
+    b.run(lams, use_graph=True, autotune=True)
+    launches = b.class_launches()
+    classes = b.classes()
+    assert len(launches) == len(classes)
+    assert launches[-1]            # the TRI class (sorted last) runs the instances' own kernels
+    for model, lat, f1, f2 in zip(tri_models, lats, alone, inb):
+        g1, G1 = f1.get_state()
+        g2, G2 = f2.get_state()
+        assert f2.lam == lams[-1]
+        assert torch.equal(G1, G2) and torch.equal(g1, g2)
+        of = O.OracleFlowTRI(model, 2, mesh)
+        for a, c in zip(lams[:-1], lams[1:]):
+            of.euler(a, c)
+        gam_o, G_o = of.get_state()
+        assert _rel(g2.cpu().numpy(), gam_o) < 1e-3
+        _cmp(G2.cpu().numpy().reshape(f2.npair, f2.N, 16, lat.N_s), tri_oracle_to_gpu(of, lat, G_o), 1e-3)
+    b.close()
+    for f in alone + inb + others:
+        f.close()
 
 
 @pytest.mark.parametrize("L,N", [(0, 2), (1, 2), (1, 3)])
