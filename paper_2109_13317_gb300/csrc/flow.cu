@@ -2927,28 +2927,48 @@ static sr_status batch_tune(sr_batch* b) {
     b->qc = b->cls.empty() ? kQF : b->cls[0].qc;
     b->ctas = b->cls.empty() ? 1 : b->cls[0].ctas;
     if (sr_status s = batch_upload(b)) return s;
-    // then the classes together: parallel branches or one after another, whichever is faster
+    // then the classes together: parallel branches or one after another, for the per-class
+    // choices and (unless a form is forced) for every class persistent and every class on its
+    // instances' own kernels, since classes timed alone miss how their tails overlap; the
+    // fastest combination is kept
     if (b->cls.size() > 1) {
+        const int nk = (int)b->cls.size();
+        std::vector<std::vector<bool>> forms;
+        std::vector<bool> tuned(nk);
+        for (int k = 0; k < nk; ++k) tuned[k] = b->cls[k].per_inst;
+        forms.push_back(tuned);
+        if (b->force == 0) {
+            std::vector<bool> pers(nk), own(nk, true);
+            for (int k = 0; k < nk; ++k) pers[k] = b->cls[k].kind == 3;
+            forms.push_back(pers);
+            forms.push_back(own);
+        }
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
-        double best[2] = {1e300, 1e300};
-        for (int rep = 0; rep < 2; ++rep)
-            for (int mode = 0; mode < 2; ++mode) {
-                b->parallel = mode == 1;
-                CK(cudaMemsetAsync(b->counter.p, 0, sizeof(unsigned long long) * b->cls.size(), b->stream));
-                CK(cudaEventRecord(e0, b->stream));
-                if (sr_status s = launch_classes(b)) return s;
-                CK(cudaEventRecord(e1, b->stream));
-                CK(cudaEventSynchronize(e1));
-                float t = 0.f;
-                CK(cudaEventElapsedTime(&t, e0, e1));
-                best[mode] = std::min(best[mode], (double)t);
-            }
+        double best = 1e300;
+        size_t best_form = 0;
+        bool best_par = false;
+        for (size_t fi = 0; fi < forms.size(); ++fi) {
+            for (int k = 0; k < nk; ++k) b->cls[k].per_inst = forms[fi][k];
+            for (int rep = 0; rep < 2; ++rep)
+                for (int mode = 0; mode < 2; ++mode) {
+                    b->parallel = mode == 1;
+                    CK(cudaMemsetAsync(b->counter.p, 0, sizeof(unsigned long long) * b->cls.size(), b->stream));
+                    CK(cudaEventRecord(e0, b->stream));
+                    if (sr_status s = launch_classes(b)) return s;
+                    CK(cudaEventRecord(e1, b->stream));
+                    CK(cudaEventSynchronize(e1));
+                    float t = 0.f;
+                    CK(cudaEventElapsedTime(&t, e0, e1));
+                    if (t < best) { best = t; best_form = fi; best_par = mode == 1; }
+                }
+        }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        b->parallel = best[1] < best[0];
-        b->tune_ms = std::min(best[0], best[1]);
+        for (int k = 0; k < nk; ++k) b->cls[k].per_inst = forms[best_form][k];
+        b->parallel = best_par;
+        b->tune_ms = best;
     }
     return SR_OK;
 }
@@ -3096,15 +3116,23 @@ extern "C" sr_status sr_batch_run(sr_batch* b, int n_lambda, const double* lambd
     const int nsteps = n_lambda - 1;
     int done = 0;
     if (autotune) {
-        // tune on the node tables of the first step (self-energy flow and nodes of step 0),
-        // then run that step untimed with the chosen configuration
+        // tune on node tables at the middle cutoff of the run (self-energy flow and nodes of
+        // the current state at that cutoff): the integration nodes, and with them the work per
+        // stored triple, grow as the cutoff falls, and the launch forms' ranking with them, so
+        // the first step's tables under-represent the run
         const int ni = (int)b->inst.size();
         int maxN = 0;
         for (const BInst& B : b->inst) maxN = std::max(maxN, B.g.N);
+        const int mid = nsteps / 2;
+        CK(cudaMemcpyAsync(b->step.p, &mid, sizeof(int), cudaMemcpyHostToDevice, b->stream));
         k_sigma_b<<<dim3(maxN, ni), 64, 0, b->stream>>>(b->dinst.p, b->lams.p, b->step.p);
         k_nodes_b<<<dim3(3 * maxN, ni), 128, 0, b->stream>>>(b->dinst.p, b->lams.p, b->step.p);
         CK(cudaGetLastError());
         if (sr_status s = batch_tune(b)) return s;
+        // back to the first step, with the work counters the tuning launches consumed reset
+        // (a persistent kernel started on a spent counter would skip the first step's units)
+        CK(cudaMemsetAsync(b->step.p, 0, sizeof(int), b->stream));
+        CK(cudaMemsetAsync(b->counter.p, 0, sizeof(unsigned long long) * b->cls.size(), b->stream));
     }
     if (use_graph) {
         cudaGraph_t graph;
