@@ -232,9 +232,12 @@ sr_status sr_flow_tensor_cores(const sr_flow* flow, int* on);
  * The initial tangent is dJ/4 (Eq. frg:parametrizationInitial); every kernel then applies
  * the chain rule exactly (forward-mode dual numbers), so sr_flow_step (SR_EULER only)
  * integrates the tangent-linear flow beside the flow.  get/set_state and sr_flow_rhs see
- * interleaved (value, d/dtheta_1, d/dtheta_2) triples.  Errors: SR_ESYMMETRY if a direction
+ * interleaved (value, d/dtheta_1, d/dtheta_2) triples.  All three cores (SU2, XYZ, TRI; the
+ * TRI kernel holds its rows as dual numbers in shared memory, so a TRI tangent flow takes
+ * three times the shared memory of the FP64 flow).  Errors: SR_ESYMMETRY if a direction
  * is not invariant under the symmetries used to reduce the lattice (it could not be stored),
- * SR_EUNSUPPORTED if it has couplings the core cannot represent. */
+ * SR_EUNSUPPORTED if it has couplings the core cannot represent or the lattice needs more
+ * shared memory than a CTA has. */
 sr_status sr_flow_init_tangent(const sr_lattice* lat, int n_freq, const double* freq_pos, double lambda_init,
                                int n_par, const double* dM, void* cuda_stream, sr_flow** out);
 sr_status sr_flow_tangents(const sr_flow* flow, int* n_tangent);

@@ -1520,14 +1520,20 @@ static sr_status run_rhs(sr_flow* f, double lam, const double* gam_s, const doub
         DualT* dGo = reinterpret_cast<DualT*>(dG_o);
         DualT* nW = reinterpret_cast<DualT*>(f->nW.p);
         if (sr_status s = prof_begin(f, 0, &e0)) return s;
-        k_sigma_rhs<DualT><<<g.N, 64, 0, f->stream>>>(g, tb, f->w.p, gs, Gd, lam, dgo);
+        if (g.nc == 16)
+            k_sigma_rhs_tri<DualT><<<g.N, 64, 0, f->stream>>>(g, tb, f->tabs_tri(), f->w.p, gs, Gd, lam, dgo);
+        else
+            k_sigma_rhs<DualT><<<g.N, 64, 0, f->stream>>>(g, tb, f->w.p, gs, Gd, lam, dgo);
         if (sr_status s = prof_end(f, 0, e0)) return s;
         if (sr_status s = prof_begin(f, 1, &e0)) return s;
         k_channel_nodes<DualT><<<3 * g.N, 128, 0, f->stream>>>(g, f->w.p, f->invh.p, gs, dgo, lam, f->nx.p, nW, nullptr, f->ncount.p,
                                                               nullptr);
         if (sr_status s = prof_end(f, 1, e0)) return s;
         if (sr_status s = prof_begin(f, 2, &e0)) return s;
-        if (g.nc == 2)
+        if (g.nc == 16)
+            k_gamma_rhs_tri<DualT><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, f->tabs_tri(), f->w.p, Gd, f->nx.p, nW,
+                                                                                   f->ncount.p, dGo, pb);
+        else if (g.nc == 2)
             k_gamma_rhs<DualT, 2><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, f->w.p, Gd, f->nx.p, nW, f->ncount.p, dGo, pb);
         else
             k_gamma_rhs<DualT, 4><<<blocks, kThreads, f->smem_rhs, f->stream>>>(g, tb, f->w.p, Gd, f->nx.p, nW, f->ncount.p, dGo, pb);
@@ -1931,7 +1937,7 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
     if (sr_status s2 = refresh_shadow(f.get(), f->G.p, f->Gf.p)) return s2;
     const bool tc_ok = precision == SR_FP32_MIXED && tc_supported(g.nc, g.nsp, f->dense);
     f->smem_rhs = g.nc == 16 ? tri_smem_bytes(g.Ns, tri_groups(g.Ns, kThreads), f->tlat_n_items,
-                                              precision == SR_FP64 ? sizeof(double) : sizeof(float))
+                                              precision == SR_FP64 ? (f->ntan ? sizeof(DualT) : sizeof(double)) : sizeof(float))
                   : precision == SR_FP32_MIXED ? f32_smem_bytes(g.Ns, g.nsp, g.nc, f->nprod, f->dense)
                                                : rhs_smem_bytes(g, f->nprod, f->ntan ? sizeof(DualT) : sizeof(double));
     if (tc_ok) f->smem_tc = f32_smem_bytes(g.Ns, g.nsp, g.nc, f->nprod, f->dense, true);
@@ -1941,7 +1947,8 @@ static sr_status flow_create(const sr_lattice* lat, int n_freq, const double* fr
     CK(cudaMemsetAsync(f->tcfail.p, 0, sizeof(int), st));
     if (f->smem_rhs > 227 * 1024) return fail(SR_EUNSUPPORTED, "lattice too large for one CTA's shared memory (%zu bytes)", f->smem_rhs);
     if (g.nc == 16) {
-        if (precision == SR_FP64) CK(ensure_smem((const void*)k_gamma_rhs_tri<double>, f->smem_rhs));
+        if (f->ntan) CK(ensure_smem((const void*)k_gamma_rhs_tri<DualT>, f->smem_rhs));
+        else if (precision == SR_FP64) CK(ensure_smem((const void*)k_gamma_rhs_tri<double>, f->smem_rhs));
         else CK(ensure_smem((const void*)k_gamma_rhs_tri<float>, f->smem_rhs));
     } else if (f->ntan) {
         CK(ensure_smem((const void*)k_gamma_rhs<DualT, 2>, f->smem_rhs));
@@ -2267,7 +2274,11 @@ extern "C" sr_status sr_measure_susceptibility_tangent(sr_flow* f, int n_k, cons
     const int npairs = (int)lat->chi_map.size();
     Tabs tb = f->tabs();
     DualT* chi = reinterpret_cast<DualT*>(f->chi.p);
-    if (g.nc == 2)
+    if (g.nc == 16)
+        k_chi_tri<DualT><<<npairs, 128, 0, f->stream>>>(g, tb, f->tabs_tri(), f->w.p, reinterpret_cast<const DualT*>(f->gam.p),
+                                                        reinterpret_cast<const DualT*>(f->G.p), f->lambda, f->chi_r16.p,
+                                                        f->chi_m16.p, f->chi_onsite.p, lat->Ntot, chi);
+    else if (g.nc == 2)
         k_chi<DualT, 2><<<npairs, 128, 0, f->stream>>>(g, tb, f->w.p, reinterpret_cast<const DualT*>(f->gam.p),
                                                         reinterpret_cast<const DualT*>(f->G.p), f->lambda, f->chi_map.p,
                                                         f->chi_onsite.p, lat->Ntot, chi);
@@ -2279,8 +2290,12 @@ extern "C" sr_status sr_measure_susceptibility_tangent(sr_flow* f, int n_k, cons
     if (f->kbuf.n < (size_t)3 * n_k) CK(f->kbuf.alloc((size_t)3 * n_k));
     if (f->chik.n < (size_t)n_k * f->ts) CK(f->chik.alloc((size_t)n_k * f->ts));
     CK(cudaMemcpyAsync(f->kbuf.p, k_xyz, sizeof(double) * 3 * n_k, cudaMemcpyHostToDevice, f->stream));
-    k_chi_k<DualT><<<(n_k + 127) / 128, 128, 0, f->stream>>>(n_k, f->kbuf.p, chi, f->chi_dr.p, npairs, lat->nb, g.nc,
-                                                             reinterpret_cast<DualT*>(f->chik.p));
+    if (g.nc == 16)
+        k_chi_k_tri<DualT><<<(n_k + 127) / 128, 128, 0, f->stream>>>(n_k, f->kbuf.p, chi, f->chi_dr.p, npairs, lat->nb,
+                                                                     reinterpret_cast<DualT*>(f->chik.p));
+    else
+        k_chi_k<DualT><<<(n_k + 127) / 128, 128, 0, f->stream>>>(n_k, f->kbuf.p, chi, f->chi_dr.p, npairs, lat->nb, g.nc,
+                                                                 reinterpret_cast<DualT*>(f->chik.p));
     CK(cudaGetLastError());
     std::vector<double> h((size_t)n_k * f->ts);
     CK(cudaMemcpyAsync(h.data(), f->chik.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, f->stream));

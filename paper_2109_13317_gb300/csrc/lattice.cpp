@@ -508,9 +508,38 @@ std::array<double, 9> pair_coupling(const sr_lattice* lat, int b1, const SiteKey
 
 sr_status tangent_init(const sr_lattice* lat, int npar, const double* dM, std::vector<double>* out, std::string* msg) {
     const int nc = lat->nc, Ns = lat->Ns;
-    if (nc == 16) { *msg = "tangent flows are provided for the SU2 and XYZ cores"; return SR_EUNSUPPORTED; }
     const size_t ncoup = lat->couplings.size();
     out->assign((size_t)Ns * nc * npar, 0.0);
+    if (nc == 16) {
+        // TRI: the initial vertex J_ab / 4 in the slots (a, b), a, b = x, y, z (as the flow's
+        // own initial vertex), and every pair's derivative must be the signed image of its
+        // stored pair under the pair's component map
+        for (int p = 0; p < npar; ++p) {
+            const double* Ms = dM + (size_t)p * ncoup * 9;
+            for (int r = 0; r < Ns; ++r) {
+                const auto J = pair_coupling(lat, 0, lat->sites[lat->rep[r]], Ms);
+                for (int a = 1; a < 4; ++a)
+                    for (int b = 1; b < 4; ++b) (*out)[((size_t)r * 16 + a * 4 + b) * npar + p] = J[3 * (a - 1) + (b - 1)] / 4.0;
+            }
+            for (size_t i = 0; i < lat->chi_sites.size(); ++i) {
+                const int b = (int)(i / lat->Ntot);
+                const SiteKey& j = lat->chi_sites[i];
+                const auto J = pair_coupling(lat, b, SiteKey{{j.n[0], j.n[1], j.n[2]}, j.b}, Ms);
+                const PairMap16& pm = lat->chi_map16[i];
+                for (int c = 0; c < 16; ++c) {
+                    const int mu = c / 4, nu = c % 4;
+                    const double want = (mu > 0 && nu > 0) ? J[3 * (mu - 1) + (nu - 1)] / 4.0 : 0.0;
+                    const int m = pm.m[c];
+                    const double img = (*out)[((size_t)pm.r * 16 + (m & 15)) * npar + p] * ((m & 16) ? -1.0 : 1.0);
+                    if (std::fabs(want - img) > lat->eps) {
+                        *msg = "tangent direction " + std::to_string(p) + " breaks a symmetry used to reduce the lattice";
+                        return SR_ESYMMETRY;
+                    }
+                }
+            }
+        }
+        return SR_OK;
+    }
     for (int p = 0; p < npar; ++p) {
         const double* Ms = dM + (size_t)p * ncoup * 9;
         std::vector<std::array<double, 9>> rep(Ns);

@@ -39,60 +39,70 @@ struct TabsT {
 
 __device__ __forceinline__ bool tri_mixed(int c) { return ((c >> 2) == 0) != ((c & 3) == 0); }
 
+// Value type of a lookup with weights W in a state of type S: W, or the dual number of a
+// tangent flow's state.
+template <typename W, typename S> struct TriVal { using type = W; };
+template <typename W, int P> struct TriVal<W, Dual<P>> { using type = Dual<P>; };
+
 // Component c of the pair (ref, rep_r) at the descriptor's frequencies, interpolated in the
-// descriptor's weight type W (FP64, or FP32 in the mixed-precision vertex kernel).
+// descriptor's weight type W (FP64, or FP32 in the mixed-precision vertex kernel; dual
+// numbers for a tangent flow's state).
 template <typename W, typename S>
-__device__ __forceinline__ W tri_value(const S* __restrict__ G, const Desc<W>& d, bool mneg, const Tabs& tb,
-                                       const TabsT& tt, const Geo& g, int r, int c) {
+__device__ __forceinline__ typename TriVal<W, S>::type tri_value(const S* __restrict__ G, const Desc<W>& d, bool mneg,
+                                                                 const Tabs& tb, const TabsT& tt, const Geo& g, int r, int c) {
+    using V = typename TriVal<W, S>::type;
     int rs = r, m = c;
     if (d.swap) { rs = tb.swap_r[r]; m = tt.swap_map[c * g.Ns + r]; }
     const int cs = m & 15;
     const S* base = G + cs * g.Ns + rs;
     const W* wgt = (cs & 3) == 0 ? d.wd : d.ws;
-    W acc = W(0);
-    for (int k = 0; k < d.n; ++k) acc = fmadd(wgt[k], (W)base[d.off[k]], acc);
+    V acc = V(0);
+    for (int k = 0; k < d.n; ++k) acc = fmadd((V)base[d.off[k]], wgt[k], acc);
     const bool neg = ((m & 16) != 0) != (mneg && tri_mixed(c));
     return neg ? -acc : acc;
 }
 
 // Self-energy flow (spin trace): dgamma(w) = -(1/2pi) sum_{w2 = +-Lambda} H / (w2 + gamma(w2)),
 // H = 2 sum_j Gamma^00_{ref j}(w+w2, 0, w-w2) - sum_k Gamma^kk_{ref ref}(w+w2, w2-w, 0).
-// (block n: the frequency w[n]; any block size up to 1024 threads)
+// (block n: the frequency w[n]; any block size up to 1024 threads; T: double, or the dual
+// numbers of a tangent flow)
+template <typename T>
 __device__ void sigma_rhs_tri_block(const Geo& g, const Tabs& tb, const TabsT& tt, const double* __restrict__ w,
-                                    const double* __restrict__ gam, const double* __restrict__ G, double lam,
-                                    double* __restrict__ dgam, int n) {
-    __shared__ double red[2 * 32];
+                                    const T* __restrict__ gam, const T* __restrict__ G, double lam,
+                                    T* __restrict__ dgam, int n) {
+    __shared__ double red[2 * 32 * (sizeof(T) / sizeof(double))];
     const double w1 = w[n];
-    double H[2] = {0.0, 0.0};
+    T H[2] = {T(0.0), T(0.0)};
     for (int sg = 0; sg < 2; ++sg) {
         const double w2 = sg == 0 ? lam : -lam;
         Desc<double> d;
         make_desc(w1 + w2, 0.0, w1 - w2, 1, 0, tb, g, d);
         const bool mn = (w1 - w2) < 0.0;
-        double h = 0.0;
+        T h = T(0.0);
         for (int r = threadIdx.x; r < g.Ns; r += blockDim.x) h += (double)tb.mult[r] * tri_value(G, d, mn, tb, tt, g, r, 0);
         h = 2.0 * h;
         if (threadIdx.x == 0) {
             Desc<double> e;
             make_desc(w1 + w2, w2 - w1, 0.0, 2, 0, tb, g, e);
             const bool me = (w2 - w1) < 0.0;
-            double f = 0.0;
+            T f = T(0.0);
             for (int k = 0; k < 4; ++k) f += tri_value(G, e, me, tb, tt, g, 0, 5 * k);
             h -= f;
         }
         H[sg] = h;
     }
-    block_sum<double, 2>(H, red);
+    block_sum<T, 2>(H, red);
     if (threadIdx.x == 0) {
-        double acc = H[0] / (lam + interp_odd(w, tb.invh, g.N, gam, lam));
+        T acc = H[0] / (lam + interp_odd(w, tb.invh, g.N, gam, lam));
         acc += H[1] / (-lam + interp_odd(w, tb.invh, g.N, gam, -lam));
         dgam[n] = -acc / (2.0 * kPi);
     }
 }
 
-__global__ void k_sigma_rhs_tri(Geo g, Tabs tb, TabsT tt, const double* __restrict__ w, const double* __restrict__ gam,
-                                const double* __restrict__ G, double lam, double* __restrict__ dgam) {
-    sigma_rhs_tri_block(g, tb, tt, w, gam, G, lam, dgam, blockIdx.x);
+template <typename T>
+__global__ void k_sigma_rhs_tri(Geo g, Tabs tb, TabsT tt, const double* __restrict__ w, const T* __restrict__ gam,
+                                const T* __restrict__ G, double lam, T* __restrict__ dgam) {
+    sigma_rhs_tri_block<T>(g, tb, tt, w, gam, G, lam, dgam, blockIdx.x);
 }
 
 // Shared-memory slot of component c of site r in a row: the 16 components of a site are
@@ -147,7 +157,9 @@ __device__ __forceinline__ void tri_onsite_acc(const R* __restrict__ A, const R*
 
 template <typename R>
 struct ShT {
-    Desc<R>* desc;        // kQTri * 4
+    Desc<typename WeightOf<R>::type>* desc;   // kQTri * 4
+    R* wq;                // kQTri * 4: node weights of rows 0 and 3 (dual numbers only; otherwise
+                          // folded into the corner weights)
     int* mneg;            // kQTri * 4
     R* rows;              // kQTri * 2 * 16 Ns (site-major, component c of site r at tri_slot(r, c))
     R* onrow;             // kQTri * 2 * 16
@@ -163,7 +175,8 @@ __host__ __device__ inline int tri_lat_slots(int Ns, int n_items, size_t rsz) { 
 __host__ __device__ inline size_t tri_smem_bytes(int Ns, int NG, int n_items, size_t rsz) {
     auto rnd = [](size_t b) { return (b + 15) & ~size_t(15); };
     const size_t dsz = rsz == sizeof(float) ? sizeof(Desc<float>) : sizeof(Desc<double>);
-    return rnd(dsz * kQTri * 4) + rnd(sizeof(int) * kQTri * 4) + rnd(rsz * kQTri * 2 * 16 * Ns) +
+    return rnd(dsz * kQTri * 4) + (rsz > sizeof(double) ? rnd(rsz * kQTri * 4) : 0) + rnd(sizeof(int) * kQTri * 4) +
+           rnd(rsz * kQTri * 2 * 16 * Ns) +
            rnd(rsz * kQTri * 2 * 16) + rnd(rsz * (size_t)NG * Ns * 16) + rnd(rsz * (size_t)tri_lat_slots(Ns, n_items, rsz) * 16);
 }
 
@@ -226,19 +239,26 @@ __host__ __device__ inline int tri_groups(int Ns, int threads) {
 // dGamma/dLambda of every stored entry of one frequency triple (one CTA per triple).  R is
 // the type of the state read (the FP64 state, or its FP32 copy), of the lookup weights, the
 // interpolated rows, the products and their node sums (double: FP64 flow; float: FP32-mixed
-// flow, output in FP64).
+// flow, output in FP64; DualT: the tangent-linear flow, FP64 descriptors with the node weights
+// applied to the rows).
+template <typename R> using TriOut = typename std::conditional<std::is_same<R, float>::value, double, R>::type;
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, TabsT tt, const double* __restrict__ w,
                                                             const R* __restrict__ G, const double* __restrict__ nx,
-                                                            const double* __restrict__ nW, const int* __restrict__ ncount,
-                                                            double* __restrict__ dG, int p0) {
+                                                            const TriOut<R>* __restrict__ nW, const int* __restrict__ ncount,
+                                                            TriOut<R>* __restrict__ dG, int p0) {
+    using D = typename WeightOf<R>::type;                 // descriptor weights
+    constexpr bool kFold = std::is_same<D, R>::value;     // node weights folded into the corner weights
+    constexpr bool kF32 = std::is_same<R, float>::value;
     extern __shared__ __align__(16) unsigned char smem[];
     const int NG = tri_groups(g.Ns, blockDim.x);
     ShT<R> sh;
     {
         size_t off = 0;
         auto take = [&](size_t bytes) { unsigned char* q = smem + off; off += (bytes + 15) & ~size_t(15); return q; };
-        sh.desc = (Desc<R>*)take(sizeof(Desc<R>) * kQTri * 4);
+        sh.desc = (Desc<D>*)take(sizeof(Desc<D>) * kQTri * 4);
+        sh.wq = kFold ? nullptr : (R*)take(sizeof(R) * kQTri * 4);
         sh.mneg = (int*)take(sizeof(int) * kQTri * 4);
         sh.rows = (R*)take(sizeof(R) * kQTri * 2 * 16 * g.Ns);
         sh.onrow = (R*)take(sizeof(R) * kQTri * 2 * 16);
@@ -286,7 +306,7 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
         const int cidx = ch * g.N + vi;
         const int nq = ncount[cidx];
         const double* X = nx + (size_t)cidx * g.nmax;
-        const double* Wp = nW + (size_t)cidx * g.nmax;
+        const TriOut<R>* Wp = nW + (size_t)cidx * g.nmax;
         const int nrow = ch == 1 ? 4 : 2;
         for (int q0 = 0; q0 < nq; q0 += kQTri) {
             const int qn = min(kQTri, nq - q0);
@@ -299,12 +319,16 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
                 double a, b, c;
                 node_args(ch, rw, x, s, t, u, w1p, w2p, w1, w2, a, b, c);
                 const int exs = ch == 0 ? 0 : (ch == 2 ? 2 : (rw < 2 ? 1 : 2));
-                Desc<R>& d = sh.desc[q * 4 + rw];
+                Desc<D>& d = sh.desc[q * 4 + rw];
                 make_desc(a, b, c, exs, vi, tb, g, d);
                 sh.mneg[q * 4 + rw] = (b < 0.0) != (c < 0.0);
                 if (rw == 0 || rw == 3) {
-                    const R wn = (R)Wp[q0 + q];
-                    for (int k = 0; k < d.n; ++k) { d.wd[k] *= wn; d.ws[k] *= wn; }
+                    if constexpr (kFold) {
+                        const R wn = (R)Wp[q0 + q];
+                        for (int k = 0; k < d.n; ++k) { d.wd[k] *= wn; d.ws[k] *= wn; }
+                    } else {
+                        sh.wq[q * 4 + rw] = Wp[q0 + q];
+                    }
                 }
             }
             __syncthreads();
@@ -315,10 +339,10 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
                 // per (node, row), entry maps resolved once per CTA
                 for (int qr = 0; qr < qn * 2; ++qr) {
                     const int dq = (qr >> 1) * 4 + (qr & 1);
-                    const Desc<R>& d = sh.desc[dq];
+                    const Desc<D>& d = sh.desc[dq];
                     const int n = d.n, sw = d.swap, mn = sh.mneg[dq];
                     int o[4];
-                    R wd[4], ws[4];
+                    D wd[4], ws[4];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) { o[j] = d.off[j]; wd[j] = d.wd[j]; ws[j] = d.ws[j]; }
                     R* dst = sh.rows + qr * row;
@@ -331,7 +355,9 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
                             R acc = R(0);
 #pragma unroll
                             for (int j = 0; j < 4; ++j)
-                                if (j < n) acc = fmadd(dens ? wd[j] : ws[j], (R)src[o[j]], acc);
+                                if (j < n) acc = fmadd((R)src[o[j]], dens ? wd[j] : ws[j], acc);
+                            if constexpr (!kFold)
+                                if ((qr & 1) == 0) acc = acc * sh.wq[(qr >> 1) * 4];
                             const bool neg = (sw && ((e_sw[k] >> 28) & 1)) != (mn && ((e_pl[k] >> 29) & 1));
                             dst[e_slot[k]] = neg ? -acc : acc;
                         }
@@ -345,7 +371,10 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
                 const int dc = (int)blockDim.x / g.Ns, dr = (int)blockDim.x - dc * g.Ns;
                 for (int idx = tid; idx < qn * 2 * row; idx += blockDim.x) {
                     const int dq = (qr >> 1) * 4 + (qr & 1);
-                    sh.rows[qr * row + tri_slot(r, c)] = tri_value<R>(G, sh.desc[dq], sh.mneg[dq] != 0, tb, tt, g, r, c);
+                    R v = tri_value<D>(G, sh.desc[dq], sh.mneg[dq] != 0, tb, tt, g, r, c);
+                    if constexpr (!kFold)
+                        if ((qr & 1) == 0) v = v * sh.wq[(qr >> 1) * 4];
+                    sh.rows[qr * row + tri_slot(r, c)] = v;
                     r += dr;
                     c += dc;
                     if (r >= g.Ns) { r -= g.Ns; ++c; }
@@ -355,8 +384,10 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
             if (ch == 1)
                 for (int j = tid; j < qn * 2 * 16; j += blockDim.x) {
                     const int q = j / 32, rr = (j / 16) % 2, c = j % 16;
-                    sh.onrow[(q * 2 + rr) * 16 + c] =
-                        tri_value<R>(G, sh.desc[q * 4 + 2 + rr], sh.mneg[q * 4 + 2 + rr] != 0, tb, tt, g, 0, c);
+                    R v = tri_value<D>(G, sh.desc[q * 4 + 2 + rr], sh.mneg[q * 4 + 2 + rr] != 0, tb, tt, g, 0, c);
+                    if constexpr (!kFold)
+                        if (rr == 1) v = v * sh.wq[q * 4 + 3];
+                    sh.onrow[(q * 2 + rr) * 16 + c] = v;
                 }
             __syncthreads();
             // site-local products: work item (site r, node group gq) owns part[gq][r]
@@ -389,7 +420,7 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
             // thread, 4 x 4 spin matrices per entry (half a shared-memory load per FMA); FP64
             // (bound by the FP64 pipe): every output (site, component) integrates its signed
             // products
-            if (ch == 1 && sizeof(R) == sizeof(double))
+            if (ch == 1 && !kF32)
                 for (int o = tid; o < row; o += blockDim.x) {
                     // four products at a time: independent FMA chains over the nodes
                     R acc = R(0);
@@ -424,17 +455,19 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
                     }
                     sh.lat[o] += acc;
                 }
-            if (ch == 1 && sizeof(R) == sizeof(float))
-                for (int it = tid; it < tt.n_items; it += blockDim.x) {
-                    const int4 item = tt.lat_items[it];
-                    R acc[16];
+            if constexpr (kF32) {
+                if (ch == 1)
+                    for (int it = tid; it < tt.n_items; it += blockDim.x) {
+                        const int4 item = tt.lat_items[it];
+                        R acc[16];
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) acc[k] = R(0);
-                    tri_lattice_item<R>(sh.rows, row, qn, tt.lat_rec, item.y, item.z, acc);
-                    R* L = sh.lat + (size_t)it * 16;
+                        for (int k = 0; k < 16; ++k) acc[k] = R(0);
+                        tri_lattice_item<R>(sh.rows, row, qn, tt.lat_rec, item.y, item.z, acc);
+                        R* L = sh.lat + (size_t)it * 16;
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) L[k] += acc[k];
-                }
+                        for (int k = 0; k < 16; ++k) L[k] += acc[k];
+                    }
+            }
         }
     }
     __syncthreads();
@@ -443,10 +476,10 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
         for (int k = 0; k < NG; ++k) a += sh.part[(size_t)k * row + o];
         const int r = o >> 4, c = o & 15;
         R l = R(0);
-        if (sizeof(R) == sizeof(double)) l = sh.lat[o];
+        if constexpr (!kF32) l = sh.lat[o];
         else
             for (int it = tt.lat_item_off[r]; it < tt.lat_item_off[r + 1]; ++it) l += sh.lat[(size_t)it * 16 + c];
-        dG[((size_t)(p * g.N + ti) * 16 + c) * g.Ns + r] = (double)a - 2.0 * (double)l;
+        dG[((size_t)(p * g.N + ti) * 16 + c) * g.Ns + r] = TriOut<R>(a) - 2.0 * TriOut<R>(l);
     }
 }
 
@@ -457,14 +490,17 @@ __global__ void k_shadow_tri(long n, const double* __restrict__ G, float* __rest
 }
 
 // Correlations chi^{mu nu}_{b j}, all 16 components (Eq. frg:correlation), one block per
-// (b, j): bubble delta_{mu nu} (local) and the product-trapezoid vertex term.
-__global__ void k_chi_tri(Geo g, Tabs tb, TabsT tt, const double* __restrict__ w, const double* __restrict__ gam,
-                          const double* __restrict__ G, double lam, const int* __restrict__ cr,
-                          const int* __restrict__ cm, const int* __restrict__ onsite, int ntot, double* __restrict__ chi) {
+// (b, j): bubble delta_{mu nu} (local) and the product-trapezoid vertex term.  T: double, or
+// the dual numbers of a tangent flow.
+template <typename T>
+__global__ void k_chi_tri(Geo g, Tabs tb, TabsT tt, const double* __restrict__ w, const T* __restrict__ gam,
+                          const T* __restrict__ G, double lam, const int* __restrict__ cr,
+                          const int* __restrict__ cm, const int* __restrict__ onsite, int ntot, T* __restrict__ chi) {
     __shared__ double y[kMaxFreq + 1];
-    __shared__ double Wn[kMaxFreq + 1];
-    __shared__ double red[16 * 32];
+    __shared__ __align__(16) unsigned char wn_raw[sizeof(T) * (kMaxFreq + 1)];
+    __shared__ double red[16 * 32 * (sizeof(T) / sizeof(double))];
     __shared__ int Ksh;
+    T* Wn = reinterpret_cast<T*>(wn_raw);
     const int pidx = blockIdx.x;      // b * ntot + j
     const int b = pidx / ntot;
     const int on = onsite[pidx];
@@ -477,11 +513,11 @@ __global__ void k_chi_tri(Geo g, Tabs tb, TabsT tt, const double* __restrict__ w
         int K = 0;
         y[K++] = lam;
         for (int i = 0; i < N; ++i) if (w[i] > lam) y[K++] = w[i];
-        for (int k = 0; k < K; ++k) Wn[k] = 0.0;
+        for (int k = 0; k < K; ++k) Wn[k] = T(0.0);
         for (int k = 0; k + 1 < K; ++k) {
-            const double ya = y[k] + interp_odd(w, tb.invh, N, gam, y[k]);
-            const double yb = y[k + 1] + interp_odd(w, tb.invh, N, gam, y[k + 1]);
-            const double seg = (y[k + 1] - y[k]) / (ya * yb);
+            const T ya = y[k] + interp_odd(w, tb.invh, N, gam, y[k]);
+            const T yb = y[k + 1] + interp_odd(w, tb.invh, N, gam, y[k + 1]);
+            const T seg = (y[k + 1] - y[k]) / (ya * yb);
             Wn[k] += 0.5 * seg;
             Wn[k + 1] += 0.5 * seg;
         }
@@ -490,22 +526,22 @@ __global__ void k_chi_tri(Geo g, Tabs tb, TabsT tt, const double* __restrict__ w
     }
     __syncthreads();
     const int K = Ksh, M = 2 * K;
-    double acc[16];
+    T acc[16];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+    for (int c = 0; c < 16; ++c) acc[c] = T(0.0);
     for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
         const int pi = idx / M, qi = idx % M;
         const double xp = pi < K ? y[pi] : -y[pi - K];
         const double xq = qi < K ? y[qi] : -y[qi - K];
-        const double wpq = Wn[pi % K] * Wn[qi % K];
+        const T wpq = Wn[pi % K] * Wn[qi % K];
         Desc<double> d;
         make_desc(xp + xq, 0.0, xp - xq, 1, 0, tb, g, d);
         const bool mn = (xp - xq) < 0.0;
-        double v[16], e[16];
+        T v[16], e[16];
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
             const int mc = m[c];
-            const double x = tri_value(G, d, mn, tb, tt, g, r, mc & 15);
+            const T x = tri_value(G, d, mn, tb, tt, g, r, mc & 15);
             v[c] = (mc & 16) ? -x : x;
         }
         if (on) {
@@ -514,7 +550,7 @@ __global__ void k_chi_tri(Geo g, Tabs tb, TabsT tt, const double* __restrict__ w
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
                 const int mc = m0[c];
-                const double x = tri_value(G, d, me, tb, tt, g, r0, mc & 15);
+                const T x = tri_value(G, d, me, tb, tt, g, r0, mc & 15);
                 e[c] = (mc & 16) ? -x : x;
             }
         }
@@ -522,38 +558,39 @@ __global__ void k_chi_tri(Geo g, Tabs tb, TabsT tt, const double* __restrict__ w
         for (int mu = 0; mu < 4; ++mu)
 #pragma unroll
             for (int nu = 0; nu < 4; ++nu) {
-                double F = 4.0 * v[mu * 4 + nu];
+                T F = 4.0 * v[mu * 4 + nu];
                 if (on) {
-                    double x = 0.0;
+                    T x = T(0.0);
 #pragma unroll
                     for (int l = 0; l < 4; ++l) {
-                        const double ev = e[(mu ^ nu ^ l) * 4 + l];
-                        x += sr::tri::coef_x(mu, nu, l) > 0 ? 2.0 * ev : -2.0 * ev;
+                        const T ev = e[(mu ^ nu ^ l) * 4 + l];
+                        x += sr::tri::coef_x(mu, nu, l) > 0 ? T(2.0 * ev) : T(-2.0 * ev);
                     }
                     F -= x;
                 }
                 acc[mu * 4 + nu] += wpq * F;
             }
     }
-    block_sum<double, 16>(acc, red);
+    block_sum<T, 16>(acc, red);
     if (threadIdx.x == 0) {
-        double bub = 0.0;
+        T bub = T(0.0);
         for (int k = 0; k < K; ++k) bub += Wn[k];
         bub = bub / (2.0 * kPi);
         for (int c = 0; c < 16; ++c)
-            chi[(size_t)pidx * 16 + c] = ((on && (c >> 2) == (c & 3)) ? bub : 0.0) - acc[c] / (16.0 * kPi * kPi);
+            chi[(size_t)pidx * 16 + c] = ((on && (c >> 2) == (c & 3)) ? bub : T(0.0)) - acc[c] / (16.0 * kPi * kPi);
     }
 }
 
 // chi(k) = (1/N_b) sum_{b, j} cos(k (r_b - r_j)) (chi^xx + chi^yy + chi^zz)_{b j}.
-__global__ void k_chi_k_tri(int nk, const double* __restrict__ kp, const double* __restrict__ chi,
-                            const double* __restrict__ dr, int npairs, int nb, double* __restrict__ out) {
+template <typename T>
+__global__ void k_chi_k_tri(int nk, const double* __restrict__ kp, const T* __restrict__ chi,
+                            const double* __restrict__ dr, int npairs, int nb, T* __restrict__ out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nk) return;
     const double kx = kp[3 * i], ky = kp[3 * i + 1], kz = kp[3 * i + 2];
-    double acc = 0.0;
+    T acc = T(0.0);
     for (int p = 0; p < npairs; ++p) {
-        const double sp = chi[(size_t)p * 16 + 5] + chi[(size_t)p * 16 + 10] + chi[(size_t)p * 16 + 15];
+        const T sp = chi[(size_t)p * 16 + 5] + chi[(size_t)p * 16 + 10] + chi[(size_t)p * 16 + 15];
         acc += cos(kx * dr[3 * p] + ky * dr[3 * p + 1] + kz * dr[3 * p + 2]) * sp;
     }
     out[i] = acc / (double)nb;

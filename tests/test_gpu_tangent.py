@@ -88,3 +88,68 @@ def test_symmetry_breaking_direction_is_rejected():
     with pytest.raises(sr.SrError) as e:
         sr.Flow(lat, MESH, LAMS[0], sr.SR_FP64, tangents=bad)
     assert e.value.status == 4
+
+
+# ---- TRI core: the kagome DM model as a function of theta = (J, D) ----
+
+TRI_MESH = O.mesh_exponential(5, 0.05, 10.0)
+TRI_LAMS = W.lambda_list(6.0, 1.0, 6)
+TRI_THETA = np.array([1.0, 0.5])
+TRI_KPTS = np.array([[0.0, 0.0, 0.0], [1.3, -0.4, 0.0], [math.pi, math.pi / math.sqrt(3), 0.0]])
+
+
+def _chi_tri_gpu(theta, tangent=False):
+    cell, sites, B = W.kagome_dm_linear()
+    model = W.linear_model(cell, sites, B, theta, "TRI")
+    lat = sr.Lattice.from_model(model, 2, backend=sr.SR_TRI)
+    fl = sr.Flow(lat, TRI_MESH, TRI_LAMS[0], sr.SR_FP64, tangents=B if tangent else None)
+    for lam in TRI_LAMS[1:]:
+        fl.step(lam, sr.SR_EULER)
+    if tangent:
+        out = fl.measure_tangent(TRI_KPTS)
+    else:
+        out, _ = fl.measure(TRI_KPTS, want_ij=False)
+    fl.close()
+    return out
+
+
+def _chi_tri_oracle(theta):
+    cell, sites, B = W.kagome_dm_linear()
+    model = W.linear_model(cell, sites, B, theta, "TRI")
+    of = O.OracleFlowTRI(model, 2, TRI_MESH)
+    for a, b in zip(TRI_LAMS[:-1], TRI_LAMS[1:]):
+        of.euler(a, b)
+    return of.chi_k(TRI_LAMS[-1], TRI_KPTS)
+
+
+def test_tri_tangent_value_matches_plain_flow():
+    """The value part of the TRI tangent flow is the plain FP64 TRI flow."""
+    chi, _ = _chi_tri_gpu(TRI_THETA, tangent=True)
+    np.testing.assert_allclose(chi, _chi_tri_gpu(TRI_THETA), rtol=1e-12)
+
+
+def test_tri_tangent_matches_finite_differences():
+    """d chi(k) / d(J, D) of the kagome DM model on the TRI core (dual numbers through the TRI
+    self-energy flow, vertex flow, node weights and chi) against central differences of the
+    GPU flow and of the oracle's TRI flow."""
+    chi, dchi = _chi_tri_gpu(TRI_THETA, tangent=True)
+    h = 1e-5
+    for p in range(2):
+        e = np.zeros(2)
+        e[p] = h
+        fd_gpu = (_chi_tri_gpu(TRI_THETA + e) - _chi_tri_gpu(TRI_THETA - e)) / (2 * h)
+        fd_orc = (_chi_tri_oracle(TRI_THETA + e) - _chi_tri_oracle(TRI_THETA - e)) / (2 * h)
+        scale = np.abs(dchi[:, p]).max()
+        assert scale > 0
+        assert np.abs(dchi[:, p] - fd_gpu).max() <= 1e-5 * scale
+        assert np.abs(dchi[:, p] - fd_orc).max() <= 1e-5 * scale
+
+
+def test_tri_symmetry_breaking_direction_is_rejected():
+    cell, sites, B = W.kagome_dm_linear()
+    lat = sr.Lattice.from_model(W.linear_model(cell, sites, B, TRI_THETA, "TRI"), 2, backend=sr.SR_TRI)
+    bad = B.copy()
+    bad[1, 0] = 0.0          # the DM term on one bond only breaks the lattice symmetry
+    with pytest.raises(sr.SrError) as e:
+        sr.Flow(lat, TRI_MESH, TRI_LAMS[0], sr.SR_FP64, tangents=bad)
+    assert e.value.status == 4

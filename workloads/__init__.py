@@ -194,6 +194,21 @@ def honeycomb_kitaev_linear():
     return c, sites, B
 
 
+def kagome_dm_linear():
+    """The kagome DM model as a linear function of theta = (J, D): the unit cell, the six
+    directed bonds of kagome_dm and the basis matrices B (2, 6, 3, 3) with M_c = J B[0, c] +
+    D B[1, c] (Heisenberg and out-of-plane DM parts)."""
+    c = kagome()
+    sites = [((0, 0, 0, 1), (0, 0, 0, 0)), ((0, 0, 0, 0), (0, 0, 0, 2)),
+             ((-1, 0, 0, 1), (0, 0, 0, 0)), ((0, 0, 0, 0), (0, -1, 0, 2)),
+             ((0, 0, 0, 2), (0, 0, 0, 1)), ((0, -1, 0, 2), (-1, 0, 0, 1))]
+    B = np.zeros((2, len(sites), 3, 3))
+    for i in range(len(sites)):
+        B[0, i] = I3
+        B[1, i] = dm_matrix((0.0, 0.0, 1.0))
+    return c, sites, B
+
+
 def linear_model(cell, sites, B, theta, backend="XYZ") -> Model:
     M = np.einsum("p,pcij->cij", np.asarray(theta, dtype=np.float64), B)
     return Model(cell, [Coupling(f, t, M[k]) for k, (f, t) in enumerate(sites)], backend)
