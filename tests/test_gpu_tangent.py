@@ -153,3 +153,14 @@ def test_tri_symmetry_breaking_direction_is_rejected():
     with pytest.raises(sr.SrError) as e:
         sr.Flow(lat, TRI_MESH, TRI_LAMS[0], sr.SR_FP64, tangents=bad)
     assert e.value.status == 4
+
+
+def test_tri_autograd_function():
+    """The torch.autograd.Function over the tangent flow on the TRI core."""
+    cell, sites, B = W.kagome_dm_linear()
+    theta = torch.tensor(TRI_THETA, dtype=torch.float64, requires_grad=True)
+    chi = susceptibility(theta, cell, sites, B, 2, TRI_MESH, TRI_LAMS, TRI_KPTS, backend=sr.SR_TRI)
+    w = torch.tensor([1.0, -0.5, 2.0], dtype=torch.float64)
+    (chi * w).sum().backward()
+    _, dchi = _chi_tri_gpu(TRI_THETA, tangent=True)
+    np.testing.assert_allclose(theta.grad.numpy(), w.numpy() @ dchi, rtol=1e-12)
