@@ -162,11 +162,16 @@ __device__ __forceinline__ void axis_weights(const Tabs& tb, const Geo& g, doubl
     const int N = g.N;
     if constexpr (sizeof(T) == 8) {
         const double* w = tb.w;
-        if (x <= w[0]) { n = 1; ix[0] = 0; wx[0] = (T)1; return; }
-        if (x >= w[N - 1]) { n = 1; ix[0] = N - 1; wx[0] = (T)1; return; }
+        // x >= 0 (make_desc folds the signs) and the mesh is positive, so the comparisons run
+        // on the bit patterns, which order like the values (a -0 orders below every mesh
+        // point, as 0 does), on the integer pipe instead of the FP64 pipe
+        const long long xb = __double_as_longlong(x);
+        auto below = [&](int i) { return xb < __double_as_longlong(w[i]); };   // x < w[i]
+        if (below(0) || xb == __double_as_longlong(w[0])) { n = 1; ix[0] = 0; wx[0] = (T)1; return; }   // x <= w[0]
+        if (!below(N - 1)) { n = 1; ix[0] = N - 1; wx[0] = (T)1; return; }                            // x >= w[N-1]
         int k = interval_guess(g, (float)x);
-        while (k > 0 && x < w[k]) --k;
-        while (k < N - 2 && x >= w[k + 1]) ++k;
+        while (k > 0 && below(k)) --k;
+        while (k < N - 2 && !below(k + 1)) ++k;
         const double w1 = (x - w[k]) * tb.invh[k];
         if (w1 == 0.0) { n = 1; ix[0] = k; wx[0] = (T)1; return; }
         n = 2; ix[0] = k; ix[1] = k + 1;
