@@ -445,14 +445,12 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, double>::value ? 6 :
                 node_args(ch, rw, x, s, t, u, w1p, w2p, w1, w2, a, b, c);
                 const int exs = ch == 0 ? 0 : (ch == 2 ? 2 : (rw < 2 ? 1 : 2));
                 Desc<typename WeightOf<T>::type>& d = sh.desc[q * 4 + rw];
-                make_desc(a, b, c, exs, vi, tb, g, d);
                 if (rw == 0) sh.wq[q] = Wp[q0 + q];
                 if constexpr (std::is_same<T, double>::value) {
                     // FP64: the node weight goes into the corner weights of its rows
-                    if (rw == 0 || rw == 3) {
-                        const double wn = Wp[q0 + q];
-                        for (int k = 0; k < d.n; ++k) { d.wd[k] *= wn; d.ws[k] *= wn; }
-                    }
+                    make_desc<double, true>(a, b, c, exs, vi, tb, g, d, (rw == 0 || rw == 3) ? Wp[q0 + q] : 1.0);
+                } else {
+                    make_desc(a, b, c, exs, vi, tb, g, d);
                 }
             }
             __syncthreads();

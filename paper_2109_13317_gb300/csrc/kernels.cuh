@@ -173,7 +173,7 @@ __device__ __forceinline__ void axis_weights(const Tabs& tb, const Geo& g, doubl
         while (k > 0 && below(k)) --k;
         while (k < N - 2 && !below(k + 1)) ++k;
         const double w1 = (x - w[k]) * tb.invh[k];
-        if (w1 == 0.0) { n = 1; ix[0] = k; wx[0] = (T)1; return; }
+        if ((__double_as_longlong(w1) & 0x7fffffffffffffffLL) == 0) { n = 1; ix[0] = k; wx[0] = (T)1; return; }   // w1 == 0
         n = 2; ix[0] = k; ix[1] = k + 1;
         wx[0] = (T)((w[k + 1] - x) * tb.invh[k]);
         wx[1] = (T)w1;
@@ -212,15 +212,19 @@ __device__ __forceinline__ void axis_weights_f(const Tabs& tb, const Geo& g, flo
 // Corners of a descriptor whose exact axis EA (0 s, 1 t, 2 u) is known at compile time, so
 // that every per-axis index is static (the descriptor arithmetic stays in registers).
 // Corners are enumerated with the s axis outermost and the u axis innermost.
-template <int EA, typename T>
+template <int EA, bool SCALE, typename T>
 __device__ __forceinline__ void desc_corners(double s, double t, double u, int ex_idx, bool flip, const Tabs& tb,
-                                             const Geo& g, Desc<T>& d) {
+                                             const Geo& g, Desc<T>& d, T scale) {
     constexpr int A0 = EA == 0 ? 1 : 0, A1 = EA == 2 ? 1 : 2;
     const double x0 = A0 == 0 ? s : t, x1 = A1 == 1 ? t : u;
     int i0[2], i1[2], n0, n1;
     T v0[2], v1[2];
     axis_weights<T>(tb, g, x0, n0, i0, v0);
     axis_weights<T>(tb, g, x1, n1, i1, v1);
+    if constexpr (SCALE) {   // a factor of every corner weight (a node weight), on one axis
+        v0[0] *= scale;
+        if (n0 > 1) v0[1] *= scale;
+    }
     const int row = g.nc * g.Ns;
     int k = 0;
 #pragma unroll
@@ -247,19 +251,27 @@ __device__ __forceinline__ void desc_corners(double s, double t, double u, int e
 }
 
 // Descriptor of Gamma(s, t, u).  ex_slot (0 s, 1 t, 2 u) names an argument known to be the
-// mesh frequency w[ex_idx] (or 0, clamped to w[0]), which needs no interval search.
-template <typename T>
+// mesh frequency w[ex_idx] (or 0, clamped to w[0]), which needs no interval search.  SCALE:
+// every corner weight carries the factor `scale` (the node weight of an integration row).
+template <typename T, bool SCALE = false>
 __device__ __forceinline__ void make_desc(double s, double t, double u, int ex_slot, int ex_idx, const Tabs& tb,
-                                          const Geo& g, Desc<T>& d) {
+                                          const Geo& g, Desc<T>& d, T scale = T(1)) {
+    // sign tests and the s < u comparison on the bit patterns (integer pipe): x < 0 is a set
+    // sign bit on a value other than -0; after the folding both are >= 0 (or -0, compared as 0
+    // with the sign bit masked), where the bit patterns order like the values
+    constexpr long long kMag = 0x7fffffffffffffffLL;
+    auto negative = [](double x) { const long long b = __double_as_longlong(x); return b < 0 && (b & kMag) != 0; };
     int swap = 0;
-    if (t < 0.0) t = -t;
-    if (s < 0.0) { s = -s; swap ^= 1; }
-    if (u < 0.0) { u = -u; swap ^= 1; }
+    if (negative(t)) t = -t;
+    if (negative(s)) { s = -s; swap ^= 1; }
+    if (negative(u)) { u = -u; swap ^= 1; }
     bool flip = false;
-    if (s < u) { double tmp = s; s = u; u = tmp; flip = true; if (ex_slot != 1) ex_slot = 2 - ex_slot; }
-    if (ex_slot == 0) desc_corners<0, T>(s, t, u, ex_idx, flip, tb, g, d);
-    else if (ex_slot == 1) desc_corners<1, T>(s, t, u, ex_idx, flip, tb, g, d);
-    else desc_corners<2, T>(s, t, u, ex_idx, flip, tb, g, d);
+    if ((__double_as_longlong(s) & kMag) < (__double_as_longlong(u) & kMag)) {
+        double tmp = s; s = u; u = tmp; flip = true; if (ex_slot != 1) ex_slot = 2 - ex_slot;
+    }
+    if (ex_slot == 0) desc_corners<0, SCALE, T>(s, t, u, ex_idx, flip, tb, g, d, scale);
+    else if (ex_slot == 1) desc_corners<1, SCALE, T>(s, t, u, ex_idx, flip, tb, g, d, scale);
+    else desc_corners<2, SCALE, T>(s, t, u, ex_idx, flip, tb, g, d, scale);
     d.swap = swap;
 }
 

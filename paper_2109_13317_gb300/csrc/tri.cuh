@@ -320,15 +320,13 @@ __global__ void __launch_bounds__(kThreads) k_gamma_rhs_tri(Geo g, Tabs tb, Tabs
                 node_args(ch, rw, x, s, t, u, w1p, w2p, w1, w2, a, b, c);
                 const int exs = ch == 0 ? 0 : (ch == 2 ? 2 : (rw < 2 ? 1 : 2));
                 Desc<D>& d = sh.desc[q * 4 + rw];
-                make_desc(a, b, c, exs, vi, tb, g, d);
                 sh.mneg[q * 4 + rw] = (b < 0.0) != (c < 0.0);
-                if (rw == 0 || rw == 3) {
-                    if constexpr (kFold) {
-                        const R wn = (R)Wp[q0 + q];
-                        for (int k = 0; k < d.n; ++k) { d.wd[k] *= wn; d.ws[k] *= wn; }
-                    } else {
-                        sh.wq[q * 4 + rw] = Wp[q0 + q];
-                    }
+                if constexpr (kFold) {
+                    // the node weight goes into the corner weights of rows 0 and 3
+                    make_desc<D, true>(a, b, c, exs, vi, tb, g, d, (rw == 0 || rw == 3) ? (D)Wp[q0 + q] : D(1));
+                } else {
+                    make_desc(a, b, c, exs, vi, tb, g, d);
+                    if (rw == 0 || rw == 3) sh.wq[q * 4 + rw] = Wp[q0 + q];
                 }
             }
             __syncthreads();
