@@ -470,11 +470,19 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, double>::value ? 6 :
                     while (e >= row) { e -= row; if (++rw == 2) { rw = 0; ++q; } }
                 }
                 if (ch == 1) {
-                    for (int j = tid; j < qn * 2 * NC; j += blockDim.x) {
-                        const int qq = j / (2 * NC), rr = (j / NC) % 2, c = j % NC;
-                        T v = row_value(G, sh.desc[qq * 4 + 2 + rr], tb, g, 0, c);
-                        if (!kWeighted && rr == 1) v *= sh.wq[qq];
-                        sh.onrow[(qq * 2 + rr) * NC + c] = v;
+                    // on-site rows C (rr = 0) and D (rr = 1), stored as their on-site factors
+                    // F_c = sum_k s(k, c) X_k; a site whose on-site pair carries the component
+                    // permutation pi reads F_pi(c) of C (pi fixes the density component)
+                    for (int j = tid; j < qn * 2; j += blockDim.x) {
+                        const int qq = j >> 1, rr = j & 1;
+                        T v[NC];
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) {
+                            v[c] = row_value(G, sh.desc[qq * 4 + 2 + rr], tb, g, 0, c);
+                            if (!kWeighted && rr == 1) v[c] *= sh.wq[qq];
+                        }
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) sh.onrow[(qq * 2 + rr) * NC + c] = onsite_factor<T, NC>(v, c);
                     }
                 }
             }
@@ -535,14 +543,11 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, double>::value ? 6 :
                     for (int q = my_g; q < qn; q += NG) {
                         const T* A = sh.rows + (q * 2) * row + my_r * NC;
                         const T* B = sh.rows + (q * 2 + 1) * row + my_r * NC;
-                        const T* C0 = sh.onrow + (q * 2) * NC;
-                        const T* D = sh.onrow + (q * 2 + 1) * NC;
-                        T Cp[NC];
-#pragma unroll
-                        for (int k = 0; k < NC; ++k) Cp[k] = C0[perm_of(pon, k)];
+                        const T* FC = sh.onrow + (q * 2) * NC;
+                        const T* FD = sh.onrow + (q * 2 + 1) * NC;
 #pragma unroll
                         for (int c = 0; c < NC; ++c)
-                            racc[c] = fmadd(A[c], onsite_factor<T, NC>(Cp, c), fmadd(onsite_factor<T, NC>(D, c), B[c], racc[c]));
+                            racc[c] = fmadd(A[c], FC[perm_of(pon, c)], fmadd(FD[c], B[c], racc[c]));
                     }
                 }
                 for (int r = site_reg ? g.Ns : tid; r < g.Ns; r += blockDim.x) {
@@ -553,14 +558,11 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, double>::value ? 6 :
                     for (int q = 0; q < qn; ++q) {
                         const T* A = sh.rows + (q * 2) * row + r * NC;
                         const T* B = sh.rows + (q * 2 + 1) * row + r * NC;
-                        const T* C0 = sh.onrow + (q * 2) * NC;
-                        const T* D = sh.onrow + (q * 2 + 1) * NC;
-                        T Cp[NC];
-#pragma unroll
-                        for (int k = 0; k < NC; ++k) Cp[k] = C0[perm_of(pon, k)];
+                        const T* FC = sh.onrow + (q * 2) * NC;
+                        const T* FD = sh.onrow + (q * 2 + 1) * NC;
 #pragma unroll
                         for (int c = 0; c < NC; ++c)
-                            accl[c] = fmadd(A[c], onsite_factor<T, NC>(Cp, c), fmadd(onsite_factor<T, NC>(D, c), B[c], accl[c]));
+                            accl[c] = fmadd(A[c], FC[perm_of(pon, c)], fmadd(FD[c], B[c], accl[c]));
                     }
 #pragma unroll
                     for (int c = 0; c < NC; ++c) sh.acc[r * NC + c] += accl[c];
