@@ -55,7 +55,7 @@ typedef enum {
     SR_ESYMMETRY = 4,     /* not all lattice sites are equivalent under the model's symmetries */
     SR_ENONFINITE = 5,    /* the flow produced NaN / Inf */
     SR_ETIMEOUT = 6,      /* a bounded device-side wait gave up */
-    SR_EUNSUPPORTED = 7   /* valid request that this build does not implement (e.g. a TRI flow in FP32) */
+    SR_EUNSUPPORTED = 7   /* valid request that this build does not implement (e.g. tensor cores on a TRI flow) */
 } sr_status;
 
 typedef enum { SR_SU2 = 0, SR_XYZ = 1, SR_TRI = 2 } sr_backend;
@@ -254,9 +254,10 @@ sr_status sr_measure_susceptibility_tangent(sr_flow* flow, int n_k, const double
  * flow's current state (set it with sr_flow_set_state: the caller keeps or recomputes the
  * forward trajectory, e.g. from checkpoints); none changes it.  Arrays are device pointers
  * on the flow's stream: sigma parts n_freq doubles, gamma parts n_gamma doubles (state
- * layout); outputs are overwritten; asynchronous except where noted.  Errors:
- * SR_EUNSUPPORTED for FP32-mixed or tangent flows and when the lattice needs more shared
- * memory than one CTA has; SR_EINVAL for null pointers or a non-positive cutoff.
+ * layout); outputs are overwritten; asynchronous except where noted.  All three cores (SU2,
+ * XYZ, TRI).  Errors: SR_EUNSUPPORTED for FP32-mixed or tangent flows and when the lattice
+ * needs more shared memory than one CTA has; SR_EINVAL for null pointers or a non-positive
+ * cutoff.
  * Transposed lookups accumulate with atomic additions, so results are reproducible to
  * rounding, not bit for bit. */
 
@@ -285,8 +286,8 @@ sr_status sr_couplings_linear(int n_par, const double* theta, int n_couplings, c
  * d theta_p) bar_gamma, for coupling derivatives dM (host, n_par x n_couplings x 3 x 3 in the
  * order the couplings were given to sr_lattice_create; n_par <= 2) and the adjoint of the
  * initial state bar_gamma (device, state layout, e.g. from sr_flow_step_adjoint).  grad: host
- * out, n_par.  Synchronises.  Errors: SR_EINVAL; SR_EUNSUPPORTED for TRI or tangent flows and
- * for directions the core cannot represent (as sr_flow_init_tangent). */
+ * out, n_par.  Synchronises.  Errors: SR_EINVAL; SR_EUNSUPPORTED for tangent flows and for
+ * directions the core cannot represent (as sr_flow_init_tangent). */
 sr_status sr_flow_initial_vertex_adjoint(sr_flow* flow, int n_par, const double* dM, const double* d_bar_gamma, double* grad);
 
 /* ---- batched flows (many couplings / lattices of uneven size in one launch per stage) ---- */

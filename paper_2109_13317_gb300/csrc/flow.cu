@@ -1362,6 +1362,7 @@ __global__ void k_chi_k(int nk, const double* __restrict__ kp, const T* __restri
 
 #include "adjoint.cuh"
 #include "tri.cuh"
+#include "tri_adj.cuh"
 
 // ----------------------------------------------------------------------------- objects
 
@@ -2349,6 +2350,20 @@ extern "C" sr_status sr_measure_susceptibility(sr_flow* f, int n_k, const double
 static sr_status adj_prepare(sr_flow* f) {
     if (f->adj_ready) return SR_OK;
     const Geo& g = f->g;
+    if (g.nc == 16) {
+        // TRI: the vertex adjoint walks the forward lattice-sum table itself
+        CK(f->ntw.alloc((size_t)3 * g.N * g.nmax));
+        CK(f->Wbar.alloc((size_t)3 * g.N * g.nmax));
+        CK(f->dgbar.alloc((size_t)g.N));
+        CK(f->tg.alloc((size_t)g.N));
+        CK(f->tG.alloc((size_t)g.nent));
+        f->smem_adj = tri_adj_smem_bytes(g.Ns);
+        if (f->smem_adj > 227 * 1024) return fail(SR_EUNSUPPORTED, "lattice too large for the adjoint kernel (%zu bytes)", f->smem_adj);
+        CK(ensure_smem((const void*)k_gamma_adj_tri, f->smem_adj));
+        CK(cudaStreamSynchronize(f->stream));
+        f->adj_ready = true;
+        return SR_OK;
+    }
     const int row = g.Ns * g.nc, np = f->nprod;
     std::vector<int> poff(np + 1, 0), pout(f->h_gidx.size());
     for (int o = 0; o < row; ++o)
@@ -2391,7 +2406,6 @@ static sr_status adj_check(const sr_flow* f) {
     if (!f) return fail(SR_EINVAL, "null flow");
     if (f->ntan) return fail(SR_EUNSUPPORTED, "the adjoint is defined for plain flows, not tangent flows");
     if (f->prec != SR_FP64) return fail(SR_EUNSUPPORTED, "the adjoint is defined for FP64 flows");
-    if (f->g.nc == 16) return fail(SR_EUNSUPPORTED, "the adjoint is provided for the SU2 and XYZ cores");
     return SR_OK;
 }
 
@@ -2404,7 +2418,10 @@ static sr_status rhs_adjoint(sr_flow* f, double lam, const double* fbar_g, const
     AdjTabs at{f->pinv_off.p, f->pinv_out.p, f->ainv_off.p, f->ainv_idx.p, f->binv_off.p, f->binv_idx.p};
     cudaStream_t st = f->stream;
     // forward quantities the derivatives need: dgamma, the node positions and weights
-    k_sigma_rhs<double><<<g.N, 64, 0, st>>>(g, tb, f->w.p, f->gam.p, f->G.p, lam, f->dgam.p);
+    if (g.nc == 16)
+        k_sigma_rhs_tri<double><<<g.N, 64, 0, st>>>(g, tb, f->tabs_tri(), f->w.p, f->gam.p, f->G.p, lam, f->dgam.p);
+    else
+        k_sigma_rhs<double><<<g.N, 64, 0, st>>>(g, tb, f->w.p, f->gam.p, f->G.p, lam, f->dgam.p);
     k_channel_nodes<double><<<3 * g.N, 128, 0, st>>>(g, f->w.p, f->invh.p, f->gam.p, f->dgam.p, lam, f->nx.p, f->nW.p,
                                                      nullptr, f->ncount.p, nullptr, f->ntw.p);
     CK(cudaMemsetAsync(gbar_o, 0, sizeof(double) * g.N, st));
@@ -2412,7 +2429,10 @@ static sr_status rhs_adjoint(sr_flow* f, double lam, const double* fbar_g, const
     CK(cudaMemsetAsync(f->Wbar.p, 0, sizeof(double) * 3 * g.N * g.nmax, st));
     CK(cudaMemsetAsync(f->dgbar.p, 0, sizeof(double) * g.N, st));
     const int blocks = g.npair * g.N;
-    if (g.nc == 2)
+    if (g.nc == 16)
+        k_gamma_adj_tri<<<blocks, kThreads, f->smem_adj, st>>>(g, tb, f->tabs_tri(), f->w.p, f->G.p, f->nx.p, f->nW.p,
+                                                               f->ncount.p, fbar_G, Gbar_o, f->Wbar.p);
+    else if (g.nc == 2)
         k_gamma_adj<2><<<blocks, kThreads, f->smem_adj, st>>>(g, tb, at, f->w.p, f->G.p, f->nx.p, f->nW.p, f->ncount.p,
                                                               fbar_G, Gbar_o, f->Wbar.p);
     else
@@ -2421,7 +2441,10 @@ static sr_status rhs_adjoint(sr_flow* f, double lam, const double* fbar_g, const
     k_nodes_adj<<<3 * g.N, 128, 0, st>>>(g, f->w.p, f->invh.p, f->gam.p, f->dgam.p, lam, f->nx.p, f->ntw.p, f->ncount.p,
                                          f->Wbar.p, gbar_o, f->dgbar.p);
     k_axmy<<<1, 256, 0, st>>>((long)g.N, f->dgbar.p, fbar_g, -1.0, f->dgbar.p);
-    k_sigma_adj<<<g.N, 64, 0, st>>>(g, tb, f->w.p, f->gam.p, f->G.p, lam, f->dgbar.p, gbar_o, Gbar_o);
+    if (g.nc == 16)
+        k_sigma_adj_tri<<<g.N, 64, 0, st>>>(g, tb, f->tabs_tri(), f->w.p, f->gam.p, f->G.p, lam, f->dgbar.p, gbar_o, Gbar_o);
+    else
+        k_sigma_adj<<<g.N, 64, 0, st>>>(g, tb, f->w.p, f->gam.p, f->G.p, lam, f->dgbar.p, gbar_o, Gbar_o);
     CK(cudaGetLastError());
     return SR_OK;
 }
@@ -2466,15 +2489,22 @@ extern "C" sr_status sr_measure_susceptibility_adjoint(sr_flow* f, int n_k, cons
     CK(cudaMemcpyAsync(f->kbar.p + 3 * n_k, chi_bar, sizeof(double) * n_k, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(d_bar_sigma, 0, sizeof(double) * g.N, st));
     CK(cudaMemsetAsync(d_bar_gamma, 0, sizeof(double) * g.nent, st));
-    k_chik_adj<<<(npairs + 127) / 128, 128, 0, st>>>(n_k, f->kbar.p, f->kbar.p + 3 * n_k, f->chi_dr.p, npairs, lat->nb, g.nc,
-                                                     f->chibar.p);
     Tabs tb = f->tabs();
-    if (g.nc == 2)
-        k_chi_adj<2><<<npairs, 128, 0, st>>>(g, tb, f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_map.p, f->chi_onsite.p,
-                                             lat->Ntot, f->chibar.p, d_bar_sigma, d_bar_gamma);
-    else
-        k_chi_adj<4><<<npairs, 128, 0, st>>>(g, tb, f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_map.p, f->chi_onsite.p,
-                                             lat->Ntot, f->chibar.p, d_bar_sigma, d_bar_gamma);
+    if (g.nc == 16) {
+        k_chik_adj_tri<<<(npairs + 127) / 128, 128, 0, st>>>(n_k, f->kbar.p, f->kbar.p + 3 * n_k, f->chi_dr.p, npairs, lat->nb,
+                                                             f->chibar.p);
+        k_chi_adj_tri<<<npairs, 128, 0, st>>>(g, tb, f->tabs_tri(), f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_r16.p,
+                                              f->chi_m16.p, f->chi_onsite.p, lat->Ntot, f->chibar.p, d_bar_sigma, d_bar_gamma);
+    } else {
+        k_chik_adj<<<(npairs + 127) / 128, 128, 0, st>>>(n_k, f->kbar.p, f->kbar.p + 3 * n_k, f->chi_dr.p, npairs, lat->nb,
+                                                         g.nc, f->chibar.p);
+        if (g.nc == 2)
+            k_chi_adj<2><<<npairs, 128, 0, st>>>(g, tb, f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_map.p, f->chi_onsite.p,
+                                                 lat->Ntot, f->chibar.p, d_bar_sigma, d_bar_gamma);
+        else
+            k_chi_adj<4><<<npairs, 128, 0, st>>>(g, tb, f->w.p, f->gam.p, f->G.p, f->lambda, f->chi_map.p, f->chi_onsite.p,
+                                                 lat->Ntot, f->chibar.p, d_bar_sigma, d_bar_gamma);
+    }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
     return SR_OK;
@@ -2511,7 +2541,7 @@ __global__ void k_entry_column_sum(Geo g, const double* __restrict__ a, double* 
 extern "C" sr_status sr_flow_initial_vertex_adjoint(sr_flow* f, int n_par, const double* dM, const double* d_bar_gamma,
                                                    double* grad) {
     if (!f || n_par < 1 || !dM || !d_bar_gamma || !grad) return fail(SR_EINVAL, "bad arguments");
-    if (f->ntan || f->g.nc == 16) return fail(SR_EUNSUPPORTED, "plain SU2 / XYZ flows only");
+    if (f->ntan) return fail(SR_EUNSUPPORTED, "plain flows only (not tangent flows)");
     const Geo& g = f->g;
     std::vector<double> dinit;
     std::string msg;

@@ -3,7 +3,7 @@
 Pins, none of which uses the adjoint's own arithmetic:
   * dot-product identities <fbar, J ydot> = <J^T fbar, ydot> block by block (self-energy /
     vertex inputs and outputs), with J ydot from the tangent-linear flow (forward-mode dual
-    numbers through the forward kernels), for an SU2 and an XYZ lattice;
+    numbers through the forward kernels), for an SU2, an XYZ and a TRI lattice (kagome DM);
   * the same identity for chi(k) and for one Euler step;
   * the checkpointed gradient d chi(k) / d(J, K) against the tangent-linear flow, central
     finite differences of the GPU flow and of the CPU oracle, and at the full Heisenberg-
@@ -30,6 +30,7 @@ MESH = O.mesh_exponential(6, 0.05, 10.0)
 LAMS = W.lambda_list(6.0, 0.8, 8)
 KPTS = np.array([[0.0, 0.0, 0.0], [2.0, 0.5, 0.0], [math.pi / 1.5, math.pi / math.sqrt(3), 0.0]])
 THETA = np.array([0.2, -1.0])
+TRI_THETA = np.array([1.0, 0.5])     # kagome DM: (J, D)
 
 
 def _case(name):
@@ -38,8 +39,15 @@ def _case(name):
         m = W.square_j1j2(1.0, 0.5)
         B = np.stack([c.M for c in m.couplings])[None]
         return m, B
+    if name == "tri":
+        cell, sites, B = W.kagome_dm_linear()
+        return W.linear_model(cell, sites, B, TRI_THETA, "TRI"), B
     cell, sites, B = W.honeycomb_kitaev_linear()
     return W.linear_model(cell, sites, B, THETA), B
+
+
+def _lattice(name, model, L=2):
+    return sr.Lattice.from_model(model, L, backend=sr.SR_TRI) if name == "tri" else sr.Lattice.from_model(model, L)
 
 
 def _interleave(v, d1, d2=None):
@@ -49,7 +57,7 @@ def _interleave(v, d1, d2=None):
 
 def _evolved(name, steps=4):
     model, B = _case(name)
-    lat = sr.Lattice.from_model(model, 2)
+    lat = _lattice(name, model)
     fl = sr.Flow(lat, MESH, LAMS[0], sr.SR_FP64)
     for lam in LAMS[1:steps + 1]:
         fl.step(lam, sr.SR_EULER)
@@ -61,7 +69,7 @@ def _rand(n, seed):
     return (torch.rand(n, generator=g, dtype=torch.float64) * 2 - 1).cuda()
 
 
-@pytest.mark.parametrize("name", ["square_j1j2", "hk"])
+@pytest.mark.parametrize("name", ["square_j1j2", "hk", "tri"])
 @pytest.mark.parametrize("block", ["ss", "sG", "Gs", "GG"])
 def test_rhs_adjoint_dot_product(name, block):
     """<fbar, J ydot> = <J^T fbar, ydot> for each (output, input) block of the Jacobian."""
@@ -91,7 +99,7 @@ def test_rhs_adjoint_dot_product(name, block):
     fl.close()
 
 
-@pytest.mark.parametrize("name", ["square_j1j2", "hk"])
+@pytest.mark.parametrize("name", ["square_j1j2", "hk", "tri"])
 @pytest.mark.parametrize("in_blk", ["s", "G"])
 def test_chi_adjoint_dot_product(name, in_blk):
     lat, B, fl, lam = _evolved(name)
@@ -258,3 +266,30 @@ def test_adjoint_gradient_heisenberg_kitaev_full_size():
         e[p] = h
         fd = (_chi_plain(theta + e, cfg.L, mesh, lams, kmax) - _chi_plain(theta - e, cfg.L, mesh, lams, kmax)) / (2 * h)
         np.testing.assert_allclose(g[:, p], fd, rtol=1e-5)
+
+
+def test_tri_adjoint_gradient():
+    """d chi(k) / d(J, D) of the kagome DM model (TRI core) by the checkpointed adjoint against
+    the tangent-linear flow and central differences of the oracle's TRI flow."""
+    cell, sites, B = W.kagome_dm_linear()
+    th = torch.tensor(TRI_THETA, dtype=torch.float64, requires_grad=True)
+    chi = susceptibility_adjoint(th, cell, sites, B, 2, MESH, LAMS, KPTS, sr.SR_TRI, every=3)
+    g = np.array([torch.autograd.grad(chi[i], th, retain_graph=i + 1 < len(KPTS))[0].numpy() for i in range(len(KPTS))])
+    th_t = torch.tensor(TRI_THETA, dtype=torch.float64, requires_grad=True)
+    chi_t = susceptibility(th_t, cell, sites, B, 2, MESH, LAMS, KPTS, sr.SR_TRI)
+    g_t = np.array([torch.autograd.grad(chi_t[i], th_t, retain_graph=i + 1 < len(KPTS))[0].numpy() for i in range(len(KPTS))])
+    np.testing.assert_allclose(chi.detach().numpy(), chi_t.detach().numpy(), rtol=1e-12)
+    np.testing.assert_allclose(g, g_t, rtol=1e-9, atol=1e-12 * np.abs(g_t).max())
+    h = 1e-5
+
+    def chi_o(theta):
+        of = O.OracleFlowTRI(W.linear_model(cell, sites, B, theta, "TRI"), 2, MESH)
+        for a, b in zip(LAMS[:-1], LAMS[1:]):
+            of.euler(a, b)
+        return of.chi_k(LAMS[-1], KPTS)
+
+    for p in range(2):
+        e = np.zeros(2)
+        e[p] = h
+        fd = (chi_o(TRI_THETA + e) - chi_o(TRI_THETA - e)) / (2 * h)
+        np.testing.assert_allclose(g[:, p], fd, rtol=1e-5, atol=1e-5 * np.abs(fd).max())
