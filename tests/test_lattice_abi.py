@@ -207,6 +207,23 @@ def test_couplings_linear_combination():
         sr.sr_couplings_linear([1.0], B)
 
 
+def test_linear_models_reproduce_the_named_models():
+    """The parametrised models of the gradient tests are the named models at the same parameters
+    (same bonds, same coupling matrices), so their lattices, symmetry reductions and initial
+    vertices agree."""
+    for (cell, sites, B), theta, named in ((W.honeycomb_kitaev_linear(), [0.2, -1.0], W.honeycomb_kitaev(0.2, -1.0)),
+                                           (W.kagome_dm_linear(), [1.0, 0.5], W.kagome_dm(1.0, 0.5))):
+        m = W.linear_model(cell, sites, B, theta, named.backend)
+        assert len(m.couplings) == len(named.couplings)
+        for a, c in zip(m.couplings, named.couplings):
+            assert tuple(a.frm) == tuple(c.frm) and tuple(a.to) == tuple(c.to)
+            np.testing.assert_allclose(a.M, c.M, rtol=0, atol=1e-15)
+        backend = sr.SR_TRI if named.backend == "TRI" else sr.SR_XYZ
+        l1 = sr.Lattice.from_model(m, 3, backend=backend)
+        l2 = sr.Lattice.from_model(named, 3, backend=backend)
+        assert (l1.N_s, l1.N_tot, l1.P) == (l2.N_s, l2.N_tot, l2.P)
+
+
 @pytest.mark.parametrize("model,L", [(W.kagome_dm(1.0, 0.5), 4), (W.honeycomb_kitaev_gamma(0.1, -1.0, 0.5), 4),
                                      (W.rotated(W.kagome_dm(1.0, 0.3), np.eye(3)[[2, 0, 1]]), 3)])
 def test_tri_component_maps_are_signed_rotations(model, L):
